@@ -1,0 +1,478 @@
+#!/usr/bin/env python
+"""Benchmark of the tensor-path join + sort on one GB300 (or N replicas).
+
+Workload (one step): the foreign-key join of R = 10^8 unique int64 keys (a
+seeded random permutation of [0, 10^8), ids = positions) with S = 4x10^8 int64
+foreign keys drawn Zipf(s) over R's keys, for s = 0, 0.8 and 1.2 (three joins,
+each producing 4x10^8 (r_id, s_id) pairs sorted by key), plus ORDER BY key of
+a 10^8-row int64 relation (a fresh copy of R).  Inputs are generated on the
+device before timing and are far larger than L2 (129 MB), so no flush is
+needed between steps.
+
+Metric: join+sort input tuples per second = (3 (n_r + n_s) + n_sort) / step
+time, step time = the sum of the CUDA-event times of the four library calls on
+the launching stream (the untimed restore of the sort input is excluded).
+
+`--impl reference` times the CPU oracle instead (bounded sample per step).
+Under torchrun (N > 1) every rank runs an independent replica ("replicas only":
+no data-path collective); the value is the sum over ranks' units / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "join+sort input tuples/s"
+UNIT = "tuples/s"
+N_R = 100_000_000
+N_S = 400_000_000
+N_SORT = 100_000_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tj", choices=["tj", "reference"])
+    ap.add_argument("--zipf", default="0,0.8,1.2")
+    ap.add_argument("--budget-mb", type=float, default=256.0,
+                    help="mem_budget_bytes of each join in MiB (0 = unbounded)")
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    import torch.distributed as dist
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(zipfs, scale, seed_base):
+    import torch
+
+    from paper_2602_21237_gb300 import datagen
+
+    n_r = max(1000, int(N_R * scale))
+    n_s = max(1000, int(N_S * scale))
+    n_sort = max(1000, int(N_SORT * scale))
+    rels = []
+    kr = ir = None
+    for i, s in enumerate(zipfs):
+        r_k, r_i, s_k, s_i = datagen.fk_zipf(n_r, n_s, s, seed_base + 1, device="cuda")
+        if kr is None:
+            kr, ir = r_k, r_i
+        else:
+            # same R for every s (same seed), keep one copy
+            del r_k, r_i
+        rels.append((s, s_k, s_i))
+    sort_src_k = kr.clone()
+    sort_src_i = ir.clone()
+    torch.cuda.synchronize()
+    return n_r, n_s, n_sort, kr, ir, rels, sort_src_k[:n_sort], sort_src_i[:n_sort]
+
+
+def roofline_traffic(kernel: str):
+    """Bytes per algorithmic byte from the committed ncu summary of `kernel`,
+    valid only while the kernel's source is unchanged since the capture."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d[kernel]
+        src = os.path.join(ROOT, ent["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != ent["source_sha"]:
+            return None
+        return float(ent["dram_bytes_per_alg_byte"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def cpu_sample(kr, ir, rels, sort_k, sort_i, frac=1.0 / 64):
+    """Host copies of a key-range slice of the workload: R rows with key below
+    frac * n_r, the S rows (middle s) in that range, and frac of the sort input."""
+    import torch
+
+    n_r = kr.numel()
+    lim = int(n_r * frac)
+    m = kr < lim
+    r_k, r_i = kr[m].cpu().numpy(), ir[m].cpu().numpy()
+    s, s_k, s_i = rels[len(rels) // 2]
+    ms = s_k < lim
+    sk, si = s_k[ms].cpu().numpy(), s_i[ms].cpu().numpy()
+    ns = int(sort_k.numel() * frac)
+    return (r_k, r_i, sk, si, sort_k[:ns].cpu().numpy(), sort_i[:ns].cpu().numpy(), s, frac)
+
+
+def time_oracle(sample, reps=1):
+    import oracle
+
+    r_k, r_i, sk, si, so_k, so_i, s, frac = sample
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        n = oracle.join_inner(r_k, r_i, sk, si, count_only=False).shape[0]
+        oracle.sort(so_k, so_i)
+    dt = (time.perf_counter() - t0) / reps
+    tuples = len(r_k) + len(sk) + len(so_k)
+    return tuples / dt, dt, tuples, n
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    """The CPU oracle, as it stands, on a bounded sample per step."""
+    if rank != 0:
+        return
+    import torch
+
+    zipfs = [float(x) for x in args.zipf.split(",")]
+    _, _, _, kr, ir, rels, sk, si = make_workload(zipfs, args.scale, 20260221)
+    sample = cpu_sample(kr, ir, rels, sk, si)
+    del kr, ir, rels, sk, si
+    torch.cuda.empty_cache()
+    for _ in range(args.warmup):
+        time_oracle(sample)
+    times = []
+    for _ in range(args.steps):
+        v, dt, tuples, n = time_oracle(sample)
+        times.append(dt)
+    dt = statistics.mean(times)
+    value = sample_tuples(sample) / dt
+    desc = (f"key range [0, {sample[7]:g} n_r) of the workload: {len(sample[0])} R rows, "
+            f"{len(sample[2])} S rows (Zipf s={sample[6]}), sort of {len(sample[4])} rows")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": workload_config(args, zipfs),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def sample_tuples(sample):
+    return len(sample[0]) + len(sample[2]) + len(sample[4])
+
+
+def workload_config(args, zipfs):
+    return {"workload": "fk_join_1e8x4e8_int64_zipf_plus_sort_1e8",
+            "n_r": int(N_R * args.scale), "n_s": int(N_S * args.scale),
+            "n_sort": int(N_SORT * args.scale), "zipf_s": zipfs,
+            "mem_budget_bytes": int(args.budget_mb * (1 << 20)),
+            "key_dtype": "int64", "l2_flush": "inputs larger than L2 (>= 1.6 GB per array)"}
+
+
+# ---------------------------------------------------------------------------
+def run_tj(args, ws, rank, local):
+    import torch
+
+    from paper_2602_21237_gb300 import api
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    zipfs = [float(x) for x in args.zipf.split(",")]
+    budget = int(args.budget_mb * (1 << 20))
+    n_r, n_s, n_sort, kr, ir, rels, sort_src_k, sort_src_i = make_workload(
+        zipfs, args.scale, 20260221)
+    out = torch.empty((n_s, 2), dtype=torch.int64, device=dev)
+    sk = torch.empty_like(sort_src_k)
+    si = torch.empty_like(sort_src_i)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(timed):
+        rec = {}
+        for s, s_k, s_i in rels:
+            a, b = ev(), ev()
+            a.record(stream)
+            res = api.join_inner(kr, ir, s_k, s_i, mem_budget_bytes=budget, out=out,
+                                 stream=stream)
+            b.record(stream)
+            rec[f"join_s{s}"] = (a, b, res.shape[0])
+        sk.copy_(sort_src_k)
+        si.copy_(sort_src_i)
+        a, b = ev(), ev()
+        a.record(stream)
+        api.sort(sk, si, stream=stream)
+        b.record(stream)
+        rec["sort"] = (a, b, n_sort)
+        return rec
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    st0 = api.stats()
+
+    api.trace_reset()
+    api.trace_enable(True)
+    per_op = {}
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        recs = [step(True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    barrier(ws)
+    api.trace_enable(False)
+    trace = api.trace_table()
+    step_ms = []
+    for rec in recs:
+        tot = 0.0
+        for k, (a, b, n) in rec.items():
+            ms = a.elapsed_time(b)
+            per_op.setdefault(k, []).append(ms)
+            tot += ms
+        step_ms.append(tot)
+    for s, _, _ in rels:
+        assert recs[-1][f"join_s{s}"][2] == n_s, "FK join must return one pair per S row"
+    ms_step = statistics.mean(step_ms)
+    ms_step_max = allreduce_max(ms_step, ws)
+    tuples_step = len(rels) * (n_r + n_s) + n_sort
+    value = tuples_step * ws / (ms_step_max / 1e3)
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+
+    ops = {}
+    for k, xs in per_op.items():
+        n_in = (n_r + n_s) if k.startswith("join") else n_sort
+        ops[k] = {"mean_ms": statistics.mean(xs), "p50_ms": pct(xs, 0.5), "p99_ms": pct(xs, 0.99),
+                  "tuples_per_s": n_in / (statistics.mean(xs) / 1e3)}
+    peak, peak_kind = measured_peaks()
+    dom = max(trace.items(), key=lambda kv: kv[1]["ms"]) if trace else None
+    roof = None
+    launches = sum(v["launches"] for v in trace.values())
+    if dom:
+        name, d = dom
+        ach = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        ratio = roofline_traffic(name)
+        per_launch_alg = d["bytes"] / d["launches"]
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
+                "traffic": (per_launch_alg * ratio) if ratio else None,
+                "alg_bytes_per_launch": per_launch_alg,
+                "share_of_traced_ms": d["ms"] / sum(v["ms"] for v in trace.values())}
+    kernels = {k: {"launches": v["launches"], "ms": v["ms"],
+                   "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None}
+               for k, v in trace.items()}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort,
+                      ws)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        sample = cpu_sample(kr, ir, rels, sort_src_k, sort_src_i)
+        v, dt, tuples, _ = time_oracle(sample)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"key range [0, n_r/64) of the workload: {len(sample[0])} R rows, "
+                          f"{len(sample[2])} S rows (s={sample[6]}), sort of {len(sample[4])} "
+                          f"rows; {dt:.2f} s single-threaded")}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic", "config": workload_config(args, zipfs),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk.summary(), "gpu_launches": launches,
+                "wall_ms_per_step": wall * 1e3 / args.steps, "ops": ops, "kernels": kernels,
+                "join_stats": st0, "parallelism": f"replicas{ws}"}
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort, ws):
+    """Same metric through the public API with host buffers: every step copies
+    its inputs from pinned host memory and reads every result back."""
+    import torch
+
+    from paper_2602_21237_gb300 import api
+
+    dev = kr.device
+    pin = lambda t: t.cpu().pin_memory()  # noqa: E731
+    h_kr, h_ir = pin(kr), pin(ir)
+    h_s = [(s, pin(a), pin(b)) for s, a, b in rels]
+    h_sk, h_si = pin(sort_src_k), pin(sort_src_i)
+    h_out = torch.empty((n_s, 2), dtype=torch.int64).pin_memory()
+    h_sorted_k = torch.empty_like(h_sk).pin_memory()
+    h_sorted_i = torch.empty_like(h_si).pin_memory()
+    d_kr, d_ir = torch.empty_like(kr), torch.empty_like(ir)
+    d_sk = torch.empty((n_s,), dtype=torch.int64, device=dev)
+    d_si = torch.empty((n_s,), dtype=torch.int64, device=dev)
+    d_out = torch.empty((n_s, 2), dtype=torch.int64, device=dev)
+    d_ok, d_oi = torch.empty_like(sort_src_k), torch.empty_like(sort_src_i)
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        d_kr.copy_(h_kr, non_blocking=True)
+        d_ir.copy_(h_ir, non_blocking=True)
+        h2d += 2 * kr.numel() * 8
+        for s, a, b in h_s:
+            d_sk.copy_(a, non_blocking=True)
+            d_si.copy_(b, non_blocking=True)
+            h2d += 2 * a.numel() * 8
+            res = api.join_inner(d_kr, d_ir, d_sk, d_si, mem_budget_bytes=budget, out=d_out)
+            h_out[: res.shape[0]].copy_(res, non_blocking=True)
+            d2h += res.numel() * 8
+        d_ok.copy_(h_sk, non_blocking=True)
+        d_oi.copy_(h_si, non_blocking=True)
+        h2d += 2 * h_sk.numel() * 8
+        api.sort(d_ok, d_oi)
+        h_sorted_k.copy_(d_ok, non_blocking=True)
+        h_sorted_i.copy_(d_oi, non_blocking=True)
+        d2h += 2 * d_ok.numel() * 8
+        torch.cuda.synchronize()
+
+    step()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    dt = allreduce_max(dt, ws)
+    tuples_step = len(rels) * (n_r + n_s) + n_sort
+    return {"value": tuples_step * ws / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": args.e2e_steps}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_tj(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,853 @@
+// C ABI of libtj (include/tj.h): argument checks, the digit plan, scratch
+// management and the launch sequence of each operation.
+//
+// Join (paper Sec. 4.1) = sort both relations along the key axis (LSD onesweep
+// passes over the significant bits of key - min, Sec. 4.2), then align the two
+// sorted axes tile by tile and materialise the pairs once (Sec. 3.1).  Every
+// step runs in the kernels of tj_radix.cu and tj_join.cu; this file only plans
+// and launches.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "tj_internal.cuh"
+
+namespace tj {
+namespace {
+
+thread_local char g_err[512] = {0};
+thread_local tj_stats g_stats = {};
+
+tj_status set_err(tj_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define TJ_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return set_err(TJ_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                     __LINE__);                                                             \
+  } while (0)
+
+constexpr int64_t kMaxRows = (int64_t)1 << 30;
+
+// ---- kernel trace ------------------------------------------------------------------
+struct TraceRow {
+  char name[48];
+  int64_t launches;
+  double ms;
+  double bytes;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRow> g_trace;
+
+// Per call: event pairs around each launch, resolved after the call's final sync.
+class Tracer {
+ public:
+  explicit Tracer(cudaStream_t st) : st_(st) {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    on_ = g_trace_on;
+    if (on_) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        on_ = false;
+    }
+  }
+  ~Tracer() {
+    for (auto& p : pend_) {
+      cudaEventDestroy(p.e0);
+      cudaEventDestroy(p.e1);
+    }
+  }
+  void begin(const char* name, double bytes) {
+    if (!on_) return;
+    Pending p;
+    p.name = name;
+    p.bytes = bytes;
+    if (cudaEventCreate(&p.e0) != cudaSuccess) return;
+    if (cudaEventCreate(&p.e1) != cudaSuccess) {
+      cudaEventDestroy(p.e0);
+      return;
+    }
+    cudaEventRecord(p.e0, st_);
+    pend_.push_back(p);
+    open_ = true;
+  }
+  void end() {
+    if (!on_ || !open_) return;
+    cudaEventRecord(pend_.back().e1, st_);
+    open_ = false;
+  }
+  // the bytes of the last traced launch named `name` (known only afterwards)
+  void add_bytes(const char* name, double bytes) {
+    for (auto it = pend_.rbegin(); it != pend_.rend(); ++it)
+      if (strcmp(it->name, name) == 0) {
+        it->bytes += bytes;
+        return;
+      }
+  }
+  // call after the stream has been synchronised
+  void flush() {
+    if (!on_) return;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    for (auto& p : pend_) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.e0, p.e1) != cudaSuccess) continue;
+      TraceRow* row = nullptr;
+      for (auto& r : g_trace)
+        if (strcmp(r.name, p.name) == 0) row = &r;
+      if (!row) {
+        TraceRow r = {};
+        snprintf(r.name, sizeof(r.name), "%s", p.name);
+        g_trace.push_back(r);
+        row = &g_trace.back();
+      }
+      row->launches += 1;
+      row->ms += ms;
+      row->bytes += p.bytes;
+    }
+    cudaGetLastError();
+  }
+
+ private:
+  struct Pending {
+    const char* name;
+    double bytes;
+    cudaEvent_t e0, e1;
+  };
+  cudaStream_t st_;
+  bool on_ = false;
+  bool open_ = false;
+  std::vector<Pending> pend_;
+};
+
+// ---- per-device one-time setup -----------------------------------------------
+std::mutex g_init_mu;
+bool g_inited[256] = {false};
+
+tj_status ensure_device() {
+  int dev = 0;
+  TJ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return set_err(TJ_ERR_INTERNAL, "device index %d", dev);
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (g_inited[dev]) return TJ_OK;
+  cudaMemPool_t pool;
+  TJ_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = ~0ull;  // keep freed scratch in the pool between calls
+  TJ_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  TJ_CUDA(radix_init_attributes());
+  TJ_CUDA(join_init_attributes());
+  g_inited[dev] = true;
+  return TJ_OK;
+}
+
+// ---- scratch: one stream-ordered block per phase, carved in 256 B pieces ------
+struct Carve {
+  size_t off = 0;
+  template <typename T>
+  size_t add(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t at = off;
+    off += count * sizeof(T);
+    return at;
+  }
+};
+
+struct Block {
+  char* p = nullptr;
+  cudaStream_t st = nullptr;
+  ~Block() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  cudaError_t alloc(size_t n, cudaStream_t s) {
+    st = s;
+    return cudaMallocAsync((void**)&p, n ? n : 256, s);
+  }
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(p + off);
+  }
+};
+
+// ---- digit plan -----------------------------------------------------------------
+struct Plan {
+  uint64_t lo = 0;
+  int key_bits = 0;
+  int passes = 0;
+  int shift[kMaxPasses] = {0};
+  int bits[kMaxPasses] = {0};
+  int max_bits = 0;
+};
+
+int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
+
+// passes = ceil(b / kMaxDigitBits) (rounded up to even if asked), digits of
+// ceil(b / passes) bits from the least significant end.
+Plan make_plan(uint64_t lo, uint64_t range, bool even, int force_passes = -1) {
+  Plan p;
+  p.lo = lo;
+  p.key_bits = bitlen(range);
+  int P = force_passes >= 0 ? force_passes : (p.key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+  if (even && (P & 1)) ++P;
+  if (P > kMaxPasses) P = kMaxPasses;
+  p.passes = P;
+  if (P > 0) {
+    const int w = (p.key_bits + P - 1) / P;
+    for (int i = 0; i < P; ++i) {
+      p.shift[i] = std::min(i * w, 63);
+      p.bits[i] = std::max(0, std::min(w, p.key_bits - i * w));
+      p.max_bits = std::max(p.max_bits, p.bits[i]);
+    }
+  }
+  return p;
+}
+
+template <typename K>
+K key_of(unsigned long long ou);
+template <>
+int32_t key_of<int32_t>(unsigned long long ou) {
+  return (int32_t)(uint32_t)((uint32_t)ou ^ 0x80000000u);
+}
+template <>
+int64_t key_of<int64_t>(unsigned long long ou) {
+  return (int64_t)(ou ^ 0x8000000000000000ull);
+}
+
+template <typename K>
+uint64_t lo_bits(K k) {
+  return (uint64_t)(typename UnsignedOf<K>::type)k;
+}
+template <typename K>
+uint64_t range_of(K lo, K hi) {
+  using U = typename UnsignedOf<K>::type;
+  return (uint64_t)(U)((U)hi - (U)lo);
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <typename K>
+void set_job_plan(RadixJob<K>& j, const Plan& p) {
+  j.lo = p.lo;
+  j.passes = p.passes;
+  for (int i = 0; i < kMaxPasses; ++i) {
+    j.shift[i] = p.shift[i];
+    j.bits[i] = p.bits[i];
+  }
+}
+
+// Sets the ping-pong pointers of a job: pass 0 reads (in_k, in_v); pass p
+// writes buffer A when p is even, B when odd.  Returns the final location.
+template <typename K>
+void set_job_buffers(RadixJob<K>& j, const K* in_k, const K* in_v, K* ak, K* av, K* bk, K* bv,
+                     const K** res_k, const K** res_v) {
+  const K* ck = in_k;
+  const K* cv = in_v;
+  for (int p = 0; p < j.passes; ++p) {
+    K* dk = (p & 1) ? bk : ak;
+    K* dv = (p & 1) ? bv : av;
+    j.src_k[p] = ck;
+    j.src_v[p] = cv;
+    j.dst_k[p] = dk;
+    j.dst_v[p] = dv;
+    ck = dk;
+    cv = dv;
+  }
+  *res_k = ck;
+  *res_v = cv;
+}
+
+// ---- inner join -------------------------------------------------------------------
+template <typename K>
+tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is, int64_t ns,
+                    size_t budget, K* out, int64_t cap, int64_t* out_count, cudaStream_t st) {
+  tj_stats stats = {};
+  stats.groups = 1;
+  *out_count = 0;
+  if (nr == 0 || ns == 0) {
+    g_stats = stats;
+    return TJ_OK;
+  }
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+
+  const int64_t tiles_r = ceil_div(nr, kTile), tiles_s = ceil_div(ns, kTile);
+  Carve cc;
+  const size_t o_jobs = cc.add<RadixJob<K>>(2);
+  const size_t o_stats = cc.add<KeyStats>(2);
+  const size_t o_misc = cc.add<int64_t>(32);  // err, counters, total
+  const size_t o_jj = cc.add<JoinJob<K>>(1);
+  Block ctl;
+  TJ_CUDA(ctl.alloc(cc.off, st));
+  RadixJob<K>* d_jobs = ctl.at<RadixJob<K>>(o_jobs);
+  KeyStats* d_stats = ctl.at<KeyStats>(o_stats);
+  int* d_err = ctl.at<int>(o_misc);
+  uint32_t* d_counters = ctl.at<uint32_t>(o_misc + 16);  // [kMaxPasses + 1]
+  int64_t* d_total = ctl.at<int64_t>(o_misc + 128);
+  JoinJob<K>* d_jj = ctl.at<JoinJob<K>>(o_jj);
+
+  RadixJob<K> hj[2];
+  memset(hj, 0, sizeof(hj));
+  hj[0].keys = kr;
+  hj[0].n = nr;
+  hj[0].tile0 = 0;
+  hj[1].keys = ks;
+  hj[1].n = ns;
+  hj[1].tile0 = tiles_r;
+  TJ_CUDA(cudaMemsetAsync(ctl.p + o_misc, 0, 32 * sizeof(int64_t), st));
+  TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, 2 * sizeof(KeyStats), st));
+  TJ_CUDA(cudaMemcpyAsync(d_jobs, hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  Tracer tr(st);
+  const double w = (double)sizeof(K);
+  tr.begin("stats", w * (nr + ns));
+  TJ_CUDA(launch_stats<K>(d_jobs, 2, tiles_r + tiles_s, d_stats, st));
+  tr.end();
+  KeyStats hs[2];
+  TJ_CUDA(cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+
+  const K min_r = key_of<K>(hs[0].min_u), max_r = key_of<K>(~hs[0].max_u);
+  const K min_s = key_of<K>(hs[1].min_u), max_s = key_of<K>(~hs[1].max_u);
+  if (max_r < min_s || max_s < min_r) {  // key ranges do not overlap: J is empty
+    g_stats = stats;
+    return TJ_OK;
+  }
+  const K lo = std::min(min_r, min_s), hi = std::max(max_r, max_s);
+  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), false);
+  stats.key_bits = plan.key_bits;
+  stats.radix_passes = plan.passes;
+  stats.digit_bits = plan.max_bits;
+
+  const int P = plan.passes;
+  const int64_t bins_max = (int64_t)1 << plan.max_bits;
+  const int64_t jtiles = ceil_div(ns, kJTile);
+  const int nbuf = P >= 2 ? 2 : P;
+  Carve bc;
+  size_t o_r[4] = {0, 0, 0, 0}, o_s[4] = {0, 0, 0, 0};
+  for (int b = 0; b < nbuf; ++b) {
+    o_r[2 * b] = bc.add<K>(nr);
+    o_r[2 * b + 1] = bc.add<K>(nr);
+    o_s[2 * b] = bc.add<K>(ns);
+    o_s[2 * b + 1] = bc.add<K>(ns);
+  }
+  const size_t o_hist = bc.add<uint32_t>(2 * kMaxPasses * kMaxBins);
+  const size_t o_lb = bc.add<uint32_t>((size_t)(tiles_r + tiles_s) * bins_max);
+  const size_t o_ra = bc.add<int64_t>(jtiles);
+  const size_t o_rb = bc.add<int64_t>(jtiles);
+  const size_t o_jlb = bc.add<uint64_t>(jtiles);
+  const size_t need = bc.off + cc.off;
+  if (budget != 0 && need > budget)
+    return set_err(TJ_ERR_BUDGET,
+                   "join needs %zu bytes of scratch in one pass, budget is %zu", need, budget);
+  Block big;
+  TJ_CUDA(big.alloc(bc.off, st));
+  stats.scratch_peak = (int64_t)need;
+
+  const K* res_rk = kr;
+  const K* res_rv = ir;
+  const K* res_sk = ks;
+  const K* res_sv = is;
+  if (P > 0) {
+    set_job_plan(hj[0], plan);
+    set_job_plan(hj[1], plan);
+    hj[0].hist_stride = hj[1].hist_stride = kMaxBins;
+    hj[0].hist = big.at<uint32_t>(o_hist);
+    hj[1].hist = hj[0].hist + kMaxPasses * kMaxBins;
+    hj[0].lookback = big.at<uint32_t>(o_lb);
+    hj[1].lookback = hj[0].lookback + tiles_r * bins_max;
+    K* rb_k = nbuf > 1 ? big.at<K>(o_r[2]) : nullptr;
+    K* rb_v = nbuf > 1 ? big.at<K>(o_r[3]) : nullptr;
+    K* sb_k = nbuf > 1 ? big.at<K>(o_s[2]) : nullptr;
+    K* sb_v = nbuf > 1 ? big.at<K>(o_s[3]) : nullptr;
+    set_job_buffers(hj[0], kr, ir, big.at<K>(o_r[0]), big.at<K>(o_r[1]), rb_k, rb_v, &res_rk,
+                    &res_rv);
+    set_job_buffers(hj[1], ks, is, big.at<K>(o_s[0]), big.at<K>(o_s[1]), sb_k, sb_v, &res_sk,
+                    &res_sv);
+    TJ_CUDA(cudaMemcpyAsync(d_jobs, hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+    TJ_CUDA(cudaMemsetAsync(hj[0].hist, 0, 2 * kMaxPasses * kMaxBins * sizeof(uint32_t), st));
+    tr.begin("histogram", w * (nr + ns));
+    TJ_CUDA(launch_histogram<K>(d_jobs, 2, tiles_r + tiles_s, st));
+    tr.end();
+    TJ_CUDA(launch_digit_scan<K>(d_jobs, 2, P, st));
+    for (int p = 0; p < P; ++p) {
+      TJ_CUDA(cudaMemsetAsync(hj[0].lookback, 0,
+                              (size_t)(tiles_r + tiles_s) * bins_max * sizeof(uint32_t), st));
+      tr.begin("onesweep", 4.0 * w * (nr + ns));
+      TJ_CUDA(launch_onesweep<K>(d_jobs, 2, tiles_r + tiles_s, p, plan.max_bits, d_counters + p,
+                                 d_err, st));
+      tr.end();
+    }
+  }
+
+  JoinJob<K> jj;
+  jj.rk = res_rk;
+  jj.rv = res_rv;
+  jj.nr = nr;
+  jj.sk = res_sk;
+  jj.sv = res_sv;
+  jj.ns = ns;
+  jj.tile0 = 0;
+  int64_t* d_ra = big.at<int64_t>(o_ra);
+  int64_t* d_rb = big.at<int64_t>(o_rb);
+  uint64_t* d_jlb = big.at<uint64_t>(o_jlb);
+  TJ_CUDA(cudaMemcpyAsync(d_jj, &jj, sizeof(jj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(launch_tile_ranges<K>(d_jj, 1, jtiles, d_ra, d_rb, st));
+  TJ_CUDA(cudaMemsetAsync(d_jlb, 0, jtiles * sizeof(uint64_t), st));
+  tr.begin("join", 2.0 * w * (nr + ns));
+  TJ_CUDA(launch_join<K>(d_jj, 1, jtiles, d_ra, d_rb, d_jlb, d_counters + kMaxPasses, out, cap,
+                         nullptr, d_total, d_err, st));
+  tr.end();
+  int64_t h_misc[2] = {0, 0};
+  int h_err = 0;
+  TJ_CUDA(cudaMemcpyAsync(&h_misc[0], d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  if (h_misc[0] <= cap) tr.add_bytes("join", 2.0 * w * (double)h_misc[0]);
+  tr.flush();
+  if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
+  *out_count = h_misc[0];
+  stats.out_count = h_misc[0];
+  g_stats = stats;
+  if (h_misc[0] > cap)
+    return set_err(TJ_ERR_CAPACITY, "result has %lld pairs, capacity %lld",
+                   (long long)h_misc[0], (long long)cap);
+  return TJ_OK;
+}
+
+// ---- sort ---------------------------------------------------------------------------
+template <typename K>
+tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
+  tj_stats stats = {};
+  stats.groups = 1;
+  if (n <= 1) {
+    g_stats = stats;
+    return TJ_OK;
+  }
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  const int64_t tiles = ceil_div(n, kTile);
+  Carve cc;
+  const size_t o_jobs = cc.add<RadixJob<K>>(1);
+  const size_t o_stats = cc.add<KeyStats>(1);
+  const size_t o_misc = cc.add<int64_t>(32);
+  Block ctl;
+  TJ_CUDA(ctl.alloc(cc.off, st));
+  RadixJob<K>* d_jobs = ctl.at<RadixJob<K>>(o_jobs);
+  KeyStats* d_stats = ctl.at<KeyStats>(o_stats);
+  int* d_err = ctl.at<int>(o_misc);
+  uint32_t* d_counters = ctl.at<uint32_t>(o_misc + 16);
+
+  RadixJob<K> hj;
+  memset(&hj, 0, sizeof(hj));
+  hj.keys = keys;
+  hj.n = n;
+  TJ_CUDA(cudaMemsetAsync(ctl.p + o_misc, 0, 32 * sizeof(int64_t), st));
+  TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, sizeof(KeyStats), st));
+  TJ_CUDA(cudaMemcpyAsync(d_jobs, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  Tracer tr(st);
+  const double w = (double)sizeof(K);
+  tr.begin("stats", w * n);
+  TJ_CUDA(launch_stats<K>(d_jobs, 1, tiles, d_stats, st));
+  tr.end();
+  KeyStats hs;
+  TJ_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  tr.flush();
+  Tracer tr2(st);
+  const K lo = key_of<K>(hs.min_u), hi = key_of<K>(~hs.max_u);
+  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), /*even=*/true);
+  stats.key_bits = plan.key_bits;
+  stats.radix_passes = plan.passes;
+  stats.digit_bits = plan.max_bits;
+  if (plan.passes == 0) {  // all keys equal: already sorted
+    g_stats = stats;
+    return TJ_OK;
+  }
+  const int64_t bins_max = (int64_t)1 << plan.max_bits;
+  Carve bc;
+  const size_t o_bk = bc.add<K>(n);
+  const size_t o_bv = bc.add<K>(n);
+  const size_t o_hist = bc.add<uint32_t>(kMaxPasses * kMaxBins);
+  const size_t o_lb = bc.add<uint32_t>((size_t)tiles * bins_max);
+  Block big;
+  TJ_CUDA(big.alloc(bc.off, st));
+  stats.scratch_peak = (int64_t)(bc.off + cc.off);
+  set_job_plan(hj, plan);
+  hj.hist_stride = kMaxBins;
+  hj.hist = big.at<uint32_t>(o_hist);
+  hj.lookback = big.at<uint32_t>(o_lb);
+  const K* rk;
+  const K* rv;
+  // even number of passes: B, keys, B, keys, ... ends in the caller's arrays
+  set_job_buffers(hj, keys, ids, big.at<K>(o_bk), big.at<K>(o_bv), keys, ids, &rk, &rv);
+  TJ_CUDA(cudaMemcpyAsync(d_jobs, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(cudaMemsetAsync(hj.hist, 0, kMaxPasses * kMaxBins * sizeof(uint32_t), st));
+  tr2.begin("histogram", w * n);
+  TJ_CUDA(launch_histogram<K>(d_jobs, 1, tiles, st));
+  tr2.end();
+  TJ_CUDA(launch_digit_scan<K>(d_jobs, 1, plan.passes, st));
+  for (int p = 0; p < plan.passes; ++p) {
+    TJ_CUDA(cudaMemsetAsync(hj.lookback, 0, (size_t)tiles * bins_max * sizeof(uint32_t), st));
+    tr2.begin("onesweep", 4.0 * w * n);
+    TJ_CUDA(launch_onesweep<K>(d_jobs, 1, tiles, p, plan.max_bits, d_counters + p, d_err, st));
+    tr2.end();
+  }
+  int h_err = 0;
+  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  tr2.flush();
+  if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
+  if (rk != keys) return set_err(TJ_ERR_INTERNAL, "odd pass count in place");
+  g_stats = stats;
+  return TJ_OK;
+}
+
+// ---- batch of joins -------------------------------------------------------------------
+// Job j joins R rows [r_off[j], r_off[j+1]) with S rows [s_off[j], s_off[j+1]).
+// Radix jobs are laid out R_0, S_0, R_1, S_1, ...; every pair shares its own
+// (lo, bits) and all pairs use the same pass count with per-pair digit widths.
+// Everything after the statistics is captured into one CUDA graph.
+template <typename K>
+tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, const K* kr,
+                     const K* ir, const K* ks, const K* is, K* out, int64_t cap,
+                     int64_t* d_out_off, int64_t* out_count, cudaStream_t st) {
+  tj_stats stats = {};
+  stats.groups = 1;
+  *out_count = 0;
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  const int64_t R = r_off[nj], S = s_off[nj];
+  std::vector<RadixJob<K>> hj((size_t)(2 * nj));
+  memset(hj.data(), 0, hj.size() * sizeof(RadixJob<K>));
+  int64_t tiles = 0;
+  for (int64_t j = 0; j < nj; ++j) {
+    for (int side = 0; side < 2; ++side) {
+      RadixJob<K>& x = hj[(size_t)(2 * j + side)];
+      const int64_t a = side ? s_off[j] : r_off[j];
+      const int64_t n = (side ? s_off[j + 1] : r_off[j + 1]) - a;
+      x.keys = (side ? ks : kr) + a;
+      x.n = n;
+      x.tile0 = tiles;
+      tiles += ceil_div(n, kTile);
+    }
+  }
+  Carve cc;
+  const size_t o_jobs = cc.add<RadixJob<K>>((size_t)(2 * nj));
+  const size_t o_stats = cc.add<KeyStats>((size_t)(2 * nj));
+  const size_t o_misc = cc.add<int64_t>(32);
+  const size_t o_jj = cc.add<JoinJob<K>>((size_t)nj);
+  Block ctl;
+  TJ_CUDA(ctl.alloc(cc.off, st));
+  RadixJob<K>* d_jobs = ctl.at<RadixJob<K>>(o_jobs);
+  KeyStats* d_stats = ctl.at<KeyStats>(o_stats);
+  int* d_err = ctl.at<int>(o_misc);
+  uint32_t* d_counters = ctl.at<uint32_t>(o_misc + 16);
+  int64_t* d_total = ctl.at<int64_t>(o_misc + 128);
+  JoinJob<K>* d_jj = ctl.at<JoinJob<K>>(o_jj);
+  TJ_CUDA(cudaMemsetAsync(ctl.p + o_misc, 0, 32 * sizeof(int64_t), st));
+  TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, (size_t)(2 * nj) * sizeof(KeyStats), st));
+  TJ_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>),
+                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(launch_stats<K>(d_jobs, (int)(2 * nj), tiles, d_stats, st));
+  std::vector<KeyStats> hs((size_t)(2 * nj));
+  TJ_CUDA(cudaMemcpyAsync(hs.data(), d_stats, hs.size() * sizeof(KeyStats),
+                          cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+
+  // per-pair ranges; pairs that cannot match are dropped from the batch
+  std::vector<uint64_t> plo((size_t)nj, 0), prange((size_t)nj, 0);
+  std::vector<char> live((size_t)nj, 0);
+  int P = 0;
+  for (int64_t j = 0; j < nj; ++j) {
+    const RadixJob<K>& xr = hj[(size_t)(2 * j)];
+    const RadixJob<K>& xs = hj[(size_t)(2 * j + 1)];
+    if (xr.n == 0 || xs.n == 0) continue;
+    const K min_r = key_of<K>(hs[(size_t)(2 * j)].min_u), max_r = key_of<K>(~hs[(size_t)(2 * j)].max_u);
+    const K min_s = key_of<K>(hs[(size_t)(2 * j + 1)].min_u),
+            max_s = key_of<K>(~hs[(size_t)(2 * j + 1)].max_u);
+    if (max_r < min_s || max_s < min_r) continue;
+    const K lo = std::min(min_r, min_s), hi = std::max(max_r, max_s);
+    plo[(size_t)j] = lo_bits<K>(lo);
+    prange[(size_t)j] = range_of<K>(lo, hi);
+    live[(size_t)j] = 1;
+    P = std::max(P, make_plan(plo[(size_t)j], prange[(size_t)j], false).passes);
+  }
+  stats.radix_passes = P;
+  // scratch: ping-pong copies of every live pair, histograms, look-back, join state
+  const int nbuf = P >= 2 ? 2 : P;
+  std::vector<Plan> plans((size_t)nj);
+  int64_t hist_words = 0, lb_words = 0, jtiles = 0;
+  std::vector<int64_t> hist_at((size_t)(2 * nj), 0), lb_at((size_t)(2 * nj), 0);
+  tiles = 0;
+  for (int64_t j = 0; j < nj; ++j) {
+    Plan pl;
+    if (live[(size_t)j]) pl = make_plan(plo[(size_t)j], prange[(size_t)j], false, P);
+    plans[(size_t)j] = pl;
+    stats.key_bits = std::max(stats.key_bits, pl.key_bits);
+    stats.digit_bits = std::max(stats.digit_bits, pl.max_bits);
+    const int64_t bins = (int64_t)1 << pl.max_bits;
+    for (int side = 0; side < 2; ++side) {
+      RadixJob<K>& x = hj[(size_t)(2 * j + side)];
+      if (!live[(size_t)j]) x.n = 0;
+      x.tile0 = tiles;
+      const int64_t t = ceil_div(x.n, kTile);
+      tiles += t;
+      hist_at[(size_t)(2 * j + side)] = hist_words;
+      hist_words += (int64_t)std::max(P, 1) * bins;
+      lb_at[(size_t)(2 * j + side)] = lb_words;
+      lb_words += t * bins;
+    }
+    if (live[(size_t)j]) jtiles += ceil_div(s_off[j + 1] - s_off[j], kJTile);
+  }
+  Carve bc;
+  size_t o_r[4] = {0, 0, 0, 0}, o_s[4] = {0, 0, 0, 0};
+  for (int b = 0; b < nbuf; ++b) {
+    o_r[2 * b] = bc.add<K>((size_t)R);
+    o_r[2 * b + 1] = bc.add<K>((size_t)R);
+    o_s[2 * b] = bc.add<K>((size_t)S);
+    o_s[2 * b + 1] = bc.add<K>((size_t)S);
+  }
+  const size_t o_hist = bc.add<uint32_t>((size_t)std::max<int64_t>(hist_words, 1));
+  const size_t o_lb = bc.add<uint32_t>((size_t)std::max<int64_t>(lb_words, 1));
+  const size_t o_ra = bc.add<int64_t>((size_t)std::max<int64_t>(jtiles, 1));
+  const size_t o_rb = bc.add<int64_t>((size_t)std::max<int64_t>(jtiles, 1));
+  const size_t o_jlb = bc.add<uint64_t>((size_t)std::max<int64_t>(jtiles, 1));
+  Block big;
+  TJ_CUDA(big.alloc(bc.off, st));
+  stats.scratch_peak = (int64_t)(bc.off + cc.off);
+
+  std::vector<JoinJob<K>> hjj((size_t)nj);
+  int64_t jt = 0;
+  for (int64_t j = 0; j < nj; ++j) {
+    const K* res[4] = {kr + r_off[j], ir + r_off[j], ks + s_off[j], is + s_off[j]};
+    for (int side = 0; side < 2; ++side) {
+      RadixJob<K>& x = hj[(size_t)(2 * j + side)];
+      set_job_plan(x, plans[(size_t)j]);
+      x.passes = live[(size_t)j] ? P : 0;
+      x.hist_stride = 1 << plans[(size_t)j].max_bits;
+      x.hist = big.at<uint32_t>(o_hist) + hist_at[(size_t)(2 * j + side)];
+      x.lookback = big.at<uint32_t>(o_lb) + lb_at[(size_t)(2 * j + side)];
+      const int64_t a = side ? s_off[j] : r_off[j];
+      const size_t* o = side ? o_s : o_r;
+      K* ak = nbuf > 0 ? big.at<K>(o[0]) + a : nullptr;
+      K* av = nbuf > 0 ? big.at<K>(o[1]) + a : nullptr;
+      K* bk = nbuf > 1 ? big.at<K>(o[2]) + a : nullptr;
+      K* bv = nbuf > 1 ? big.at<K>(o[3]) + a : nullptr;
+      set_job_buffers(x, res[2 * side], res[2 * side + 1], ak, av, bk, bv, &res[2 * side],
+                      &res[2 * side + 1]);
+    }
+    JoinJob<K>& y = hjj[(size_t)j];
+    y.rk = res[0];
+    y.rv = res[1];
+    y.nr = r_off[j + 1] - r_off[j];
+    y.sk = res[2];
+    y.sv = res[3];
+    y.ns = live[(size_t)j] ? s_off[j + 1] - s_off[j] : 0;
+    y.tile0 = jt;
+    jt += ceil_div(y.ns, kJTile);
+  }
+  TJ_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>),
+                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(cudaMemcpyAsync(d_jj, hjj.data(), hjj.size() * sizeof(JoinJob<K>),
+                          cudaMemcpyHostToDevice, st));
+
+  // the batch's device work, captured once as a graph (plain launches on the
+  // legacy stream, which cannot be captured)
+  const bool use_graph = st != nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph) TJ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  auto step = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  if (P > 0) {
+    step(cudaMemsetAsync(big.at<uint32_t>(o_hist), 0,
+                         (size_t)std::max<int64_t>(hist_words, 1) * sizeof(uint32_t), st));
+    step(launch_histogram<K>(d_jobs, (int)(2 * nj), tiles, st));
+    step(launch_digit_scan<K>(d_jobs, (int)(2 * nj), P, st));
+    for (int p = 0; p < P; ++p) {
+      step(cudaMemsetAsync(big.at<uint32_t>(o_lb), 0,
+                           (size_t)std::max<int64_t>(lb_words, 1) * sizeof(uint32_t), st));
+      step(launch_onesweep<K>(d_jobs, (int)(2 * nj), tiles, p, stats.digit_bits, d_counters + p,
+                              d_err, st));
+    }
+  }
+  step(launch_tile_ranges<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra),
+                             big.at<int64_t>(o_rb), st));
+  step(cudaMemsetAsync(big.at<uint64_t>(o_jlb), 0,
+                       (size_t)std::max<int64_t>(jtiles, 1) * sizeof(uint64_t), st));
+  step(launch_join<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra), big.at<int64_t>(o_rb),
+                      big.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, d_out_off,
+                      d_total, d_err, st));
+  step(launch_fix_job_out<K>(d_jj, (int)nj, jtiles, d_out_off, d_total, st));
+  if (use_graph) {
+    cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+  }
+  int64_t h_total = 0;
+  int h_err = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&h_total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess)
+    return set_err(TJ_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+  if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
+  *out_count = h_total;
+  stats.out_count = h_total;
+  g_stats = stats;
+  if (h_total > cap)
+    return set_err(TJ_ERR_CAPACITY, "batch result has %lld pairs, capacity %lld",
+                   (long long)h_total, (long long)cap);
+  return TJ_OK;
+}
+
+bool bad_ptr(const void* p, int64_t n) { return n > 0 && p == nullptr; }
+
+}  // namespace
+}  // namespace tj
+
+using namespace tj;
+
+extern "C" {
+
+tj_status tj_join_inner(tj_dtype dt, const void* keys_r, const void* ids_r, int64_t n_r,
+                        const void* keys_s, const void* ids_s, int64_t n_s,
+                        size_t mem_budget_bytes, void* out_pairs, int64_t out_capacity,
+                        int64_t* out_count, void* stream) {
+  g_err[0] = 0;
+  if (!out_count) return set_err(TJ_ERR_INVALID, "out_count is NULL");
+  *out_count = 0;
+  if (n_r < 0 || n_s < 0 || out_capacity < 0)
+    return set_err(TJ_ERR_INVALID, "negative size");
+  if (n_r >= kMaxRows || n_s >= kMaxRows)
+    return set_err(TJ_ERR_INVALID, "n >= 2^30 rows per relation is not supported");
+  if (bad_ptr(keys_r, n_r) || bad_ptr(ids_r, n_r) || bad_ptr(keys_s, n_s) ||
+      bad_ptr(ids_s, n_s) || bad_ptr(out_pairs, out_capacity))
+    return set_err(TJ_ERR_INVALID, "null pointer with a non-zero size");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == TJ_I32)
+    return join_impl<int32_t>((const int32_t*)keys_r, (const int32_t*)ids_r, n_r,
+                              (const int32_t*)keys_s, (const int32_t*)ids_s, n_s,
+                              mem_budget_bytes, (int32_t*)out_pairs, out_capacity, out_count, st);
+  if (dt == TJ_I64)
+    return join_impl<int64_t>((const int64_t*)keys_r, (const int64_t*)ids_r, n_r,
+                              (const int64_t*)keys_s, (const int64_t*)ids_s, n_s,
+                              mem_budget_bytes, (int64_t*)out_pairs, out_capacity, out_count, st);
+  return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
+  g_err[0] = 0;
+  if (n < 0) return set_err(TJ_ERR_INVALID, "negative size");
+  if (n >= kMaxRows) return set_err(TJ_ERR_INVALID, "n >= 2^30 rows is not supported");
+  if (bad_ptr(keys, n) || bad_ptr(ids, n))
+    return set_err(TJ_ERR_INVALID, "null pointer with a non-zero size");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == TJ_I32) return sort_impl<int32_t>((int32_t*)keys, (int32_t*)ids, n, st);
+  if (dt == TJ_I64) return sort_impl<int64_t>((int64_t*)keys, (int64_t*)ids, n, st);
+  return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+tj_status tj_join_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off, const int64_t* s_off,
+                        const void* keys_r, const void* ids_r, const void* keys_s,
+                        const void* ids_s, void* out_pairs, int64_t out_capacity,
+                        int64_t* out_off, int64_t* out_count, void* stream) {
+  g_err[0] = 0;
+  if (!out_count) return set_err(TJ_ERR_INVALID, "out_count is NULL");
+  *out_count = 0;
+  if (n_jobs < 0 || out_capacity < 0) return set_err(TJ_ERR_INVALID, "negative size");
+  if (n_jobs >= ((int64_t)1 << 30)) return set_err(TJ_ERR_INVALID, "too many jobs");
+  if (n_jobs > 0 && (!r_off || !s_off || !out_off))
+    return set_err(TJ_ERR_INVALID, "null offsets");
+  if (n_jobs == 0) return TJ_OK;
+  if (r_off[0] != 0 || s_off[0] != 0) return set_err(TJ_ERR_INVALID, "offsets must start at 0");
+  for (int64_t j = 0; j < n_jobs; ++j) {
+    const int64_t a = r_off[j + 1] - r_off[j], b = s_off[j + 1] - s_off[j];
+    if (a < 0 || b < 0) return set_err(TJ_ERR_INVALID, "offsets of job %lld decrease", (long long)j);
+    if (a >= kMaxRows || b >= kMaxRows)
+      return set_err(TJ_ERR_INVALID, "job %lld has >= 2^30 rows", (long long)j);
+  }
+  if (bad_ptr(keys_r, r_off[n_jobs]) || bad_ptr(ids_r, r_off[n_jobs]) ||
+      bad_ptr(keys_s, s_off[n_jobs]) || bad_ptr(ids_s, s_off[n_jobs]) ||
+      bad_ptr(out_pairs, out_capacity))
+    return set_err(TJ_ERR_INVALID, "null pointer with a non-zero size");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == TJ_I32)
+    return batch_impl<int32_t>(n_jobs, r_off, s_off, (const int32_t*)keys_r,
+                               (const int32_t*)ids_r, (const int32_t*)keys_s,
+                               (const int32_t*)ids_s, (int32_t*)out_pairs, out_capacity, out_off,
+                               out_count, st);
+  if (dt == TJ_I64)
+    return batch_impl<int64_t>(n_jobs, r_off, s_off, (const int64_t*)keys_r,
+                               (const int64_t*)ids_r, (const int64_t*)keys_s,
+                               (const int64_t*)ids_s, (int64_t*)out_pairs, out_capacity, out_off,
+                               out_count, st);
+  return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+const char* tj_status_str(tj_status s) {
+  switch (s) {
+    case TJ_OK: return "TJ_OK";
+    case TJ_ERR_INVALID: return "TJ_ERR_INVALID";
+    case TJ_ERR_BUDGET: return "TJ_ERR_BUDGET";
+    case TJ_ERR_CAPACITY: return "TJ_ERR_CAPACITY";
+    case TJ_ERR_CUDA: return "TJ_ERR_CUDA";
+    case TJ_ERR_TIMEOUT: return "TJ_ERR_TIMEOUT";
+    case TJ_ERR_INTERNAL: return "TJ_ERR_INTERNAL";
+  }
+  return "TJ_ERR_UNKNOWN";
+}
+
+const char* tj_last_error(void) { return g_err; }
+
+tj_status tj_get_stats(tj_stats* out) {
+  if (!out) return TJ_ERR_INVALID;
+  *out = g_stats;
+  return TJ_OK;
+}
+
+const char* tj_version(void) { return "tj 0.1 (sm_103a)"; }
+
+void tj_trace_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace_on = on != 0;
+}
+
+void tj_trace_reset(void) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace.clear();
+}
+
+int tj_trace_count(void) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  return (int)g_trace.size();
+}
+
+tj_status tj_trace_get(int i, char* name, int name_len, int64_t* launches, double* ms,
+                       double* bytes) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  if (i < 0 || i >= (int)g_trace.size()) return TJ_ERR_INVALID;
+  const TraceRow& r = g_trace[(size_t)i];
+  if (name && name_len > 0) snprintf(name, (size_t)name_len, "%s", r.name);
+  if (launches) *launches = r.launches;
+  if (ms) *ms = r.ms;
+  if (bytes) *bytes = r.bytes;
+  return TJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Internal declarations shared by the CUDA translation units of libtj.
+//
+// Layout of a relation: two device arrays (SoA), keys[n] and ids[n], of the
+// same integer width.  Sorting moves both; joins read both and write (r_id,
+// s_id) pairs once at the end (late materialisation, paper Sec. 3.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tj.h"
+
+namespace tj {
+
+// ---- launch geometry -------------------------------------------------------
+constexpr int kThreads = 256;               // threads per CTA (8 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;                  // rows per thread in a sort tile
+constexpr int kTile = kThreads * kItems;    // 4096 rows per onesweep tile
+constexpr int kMaxDigitBits = 9;            // widest radix digit
+constexpr int kMaxBins = 1 << kMaxDigitBits;
+constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass
+constexpr int kJTile = 2048;                // S rows per join tile
+constexpr int kRCap = 2048;                 // R rows a join tile keeps on chip
+constexpr int kHTSlots = 4096;              // on-chip hash table slots (load <= 0.5)
+
+// ---- decoupled look-back words (30-bit counts) ----------------------------
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+// 64-bit words for output offsets (62-bit counts)
+constexpr uint64_t kFlagAgg64 = 1ull << 62;
+constexpr uint64_t kFlagInc64 = 2ull << 62;
+constexpr uint64_t kValMask64 = (1ull << 62) - 1ull;
+// bounded waits: iterations of a spin before the device reports TJ_ERR_TIMEOUT
+constexpr int kSpinLimit = 1 << 22;
+
+template <typename K> struct UnsignedOf;
+template <> struct UnsignedOf<int32_t> { using type = uint32_t; };
+template <> struct UnsignedOf<int64_t> { using type = uint64_t; };
+
+// ---- per-array radix job ---------------------------------------------------
+// One array being sorted by (key - lo) over `passes` LSD digits.  Pass p reads
+// src_k/src_v[p] and writes dst_k/dst_v[p] (ping-pong buffers).
+template <typename K>
+struct RadixJob {
+  const K* keys;        // keys for statistics and the digit histogram
+  int64_t n;            // rows
+  int64_t tile0;        // first global tile index (kTile rows per tile)
+  uint64_t lo;          // subtracted (bit pattern of the key type, wraps)
+  int32_t passes;
+  int32_t shift[kMaxPasses];
+  int32_t bits[kMaxPasses];
+  int32_t hist_stride;  // words between passes in `hist`
+  uint32_t* hist;       // [passes][hist_stride]: counts, then exclusive bases
+  uint32_t* lookback;   // [tiles][1 << bits[p]] words of the current pass
+  const K* src_k[kMaxPasses];
+  const K* src_v[kMaxPasses];
+  K* dst_k[kMaxPasses];
+  K* dst_v[kMaxPasses];
+};
+
+// Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).
+struct KeyStats {
+  unsigned long long min_u;
+  unsigned long long max_u;
+};
+
+// ---- join job ---------------------------------------------------------------
+// One join of key-sorted R and key-sorted S.
+template <typename K>
+struct JoinJob {
+  const K* rk;          // sorted R keys
+  const K* rv;          // R ids in the same order
+  int64_t nr;
+  const K* sk;          // sorted S keys
+  const K* sv;
+  int64_t ns;
+  int64_t tile0;        // first global join tile (kJTile S rows per tile)
+};
+
+// ---- launchers (tj_radix.cu) -----------------------------------------------
+cudaError_t radix_init_attributes();
+template <typename K>
+cudaError_t launch_stats(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                         KeyStats* d_stats, cudaStream_t st);
+template <typename K>
+cudaError_t launch_histogram(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                             cudaStream_t st);
+template <typename K>
+cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passes,
+                              cudaStream_t st);
+template <typename K>
+cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                            int pass, int max_bits, uint32_t* d_tile_counter, int* d_err,
+                            cudaStream_t st);
+
+// ---- launchers (tj_join.cu) -------------------------------------------------
+cudaError_t join_init_attributes();
+template <typename K>
+cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st);
+template <typename K>
+cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                        const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
+                        uint32_t* d_tile_counter, K* out, int64_t capacity,
+                        int64_t* d_job_out, int64_t* d_total, int* d_err, cudaStream_t st);
+template <typename K>
+cudaError_t launch_fix_job_out(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                               int64_t* d_job_out, const int64_t* d_total, cudaStream_t st);
+
+}  // namespace tj

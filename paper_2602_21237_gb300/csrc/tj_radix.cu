@@ -1,0 +1,437 @@
+// LSD radix machinery for the tensor-path sort (paper Sec. 4.2: the sort is a
+// relocation of rows along the key axis, digit by digit) on sm_103a.
+//
+//   k_stats      : min / max of the keys of every array (one read of the keys);
+//                  the planner turns them into (lo, significant bits).
+//   k_histogram  : the counts of every digit of every pass, in one read of the
+//                  keys (per-CTA shared-memory histograms merged into global).
+//   k_digit_scan : exclusive scan of each pass's digit counts (digit bases).
+//   k_onesweep   : one digit pass: a tile of 4096 rows is ranked stably inside
+//                  the CTA (warp __match_any_sync groups + per-warp counters),
+//                  its per-digit counts are published to a decoupled look-back
+//                  chain, and the rows are scattered through shared memory so
+//                  that each digit's run is written contiguously.
+//
+// Every kernel takes an array of jobs so that one launch serves any number of
+// arrays (both sides of a join, or thousands of joins of a batch).
+#include "tj_internal.cuh"
+
+namespace tj {
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+template <typename Job>
+__device__ __forceinline__ int find_job(const Job* jobs, int num_jobs, int64_t t) {
+  int lo = 0, hi = num_jobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile0 <= t)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_volatile_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.volatile.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long order_u(int32_t k) {
+  return (unsigned long long)((uint32_t)k ^ 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long order_u(int64_t k) {
+  return (unsigned long long)k ^ 0x8000000000000000ull;
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, typename UnsignedOf<K>::type lo, int shift,
+                                             uint32_t mask) {
+  using U = typename UnsignedOf<K>::type;
+  return (uint32_t)((((U)key) - lo) >> shift) & mask;
+}
+
+// Exclusive scan of in[0, bins) into out[0, bins) by the whole CTA
+// (bins <= 2 * kThreads).  Ends with a barrier.
+__device__ __forceinline__ void block_excl_scan_bins(const uint32_t* in, uint32_t* out, int bins,
+                                                     uint32_t* s_warp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int d0 = tid * 2;
+  const uint32_t a = d0 < bins ? in[d0] : 0u;
+  const uint32_t b = d0 + 1 < bins ? in[d0 + 1] : 0u;
+  const uint32_t s = a + b;
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w)
+    if (w < warp) wpre += s_warp[w];
+  const uint32_t excl = wpre + x - s;
+  if (d0 < bins) out[d0] = excl;
+  if (d0 + 1 < bins) out[d0 + 1] = excl + a;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// K1: min / max of every array's keys
+// ---------------------------------------------------------------------------
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restrict__ jobs,
+                                                    int num_jobs, int64_t total_tiles,
+                                                    KeyStats* __restrict__ stats) {
+  __shared__ unsigned long long s_mn[kWarps], s_mx[kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const int j = find_job(jobs, num_jobs, t);
+    const K* __restrict__ keys = jobs[j].keys;
+    const int64_t row0 = (t - jobs[j].tile0) * kTile;
+    const int64_t row1 = min(jobs[j].n, row0 + kTile);
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (int64_t r = row0 + threadIdx.x; r < row1; r += kThreads) {
+      const unsigned long long u = order_u(keys[r]);
+      mn = u < mn ? u : mn;
+      mx = u > mx ? u : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, mn, o);
+      unsigned long long b = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+      mn = a < mn ? a : mn;
+      mx = b > mx ? b : mx;
+    }
+    if (lane == 0) {
+      s_mn[warp] = mn;
+      s_mx[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kWarps; ++w) {
+        mn = s_mn[w] < mn ? s_mn[w] : mn;
+        mx = s_mx[w] > mx ? s_mx[w] : mx;
+      }
+      atomicMin(&stats[j].min_u, mn);
+      atomicMin(&stats[j].max_u, ~mx);  // stored inverted so both fields use atomicMin
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: digit histograms of every pass in one read of the keys
+// ---------------------------------------------------------------------------
+constexpr int kHistTilesPerCta = 4;
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __restrict__ jobs,
+                                                        int num_jobs, int64_t total_tiles) {
+  using U = typename UnsignedOf<K>::type;
+  __shared__ uint32_t s_h[kMaxPasses * kMaxBins];
+  __shared__ int s_shift[kMaxPasses];
+  __shared__ uint32_t s_mask[kMaxPasses];
+  const int64_t t_begin = (int64_t)blockIdx.x * kHistTilesPerCta;
+  const int64_t t_end = min(total_tiles, t_begin + kHistTilesPerCta);
+  int cur = -1, passes = 0;
+  U lo = 0;
+  for (int64_t t = t_begin; t < t_end; ++t) {
+    const int j = find_job(jobs, num_jobs, t);
+    if (j != cur) {
+      if (cur >= 0) {
+        __syncthreads();
+        for (int p = 0; p < passes; ++p)
+          for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) {
+            const uint32_t c = s_h[p * kMaxBins + d];
+            if (c) atomicAdd(&jobs[cur].hist[p * jobs[cur].hist_stride + d], c);
+          }
+      }
+      __syncthreads();
+      cur = j;
+      passes = jobs[j].passes;
+      lo = (U)jobs[j].lo;
+      if (threadIdx.x < kMaxPasses) {
+        s_shift[threadIdx.x] = jobs[j].shift[threadIdx.x];
+        s_mask[threadIdx.x] =
+            threadIdx.x < passes ? (1u << jobs[j].bits[threadIdx.x]) - 1u : 0u;
+      }
+      for (int i = threadIdx.x; i < kMaxPasses * kMaxBins; i += kThreads) s_h[i] = 0;
+      __syncthreads();
+    }
+    const K* __restrict__ keys = jobs[j].keys;
+    const int64_t row0 = (t - jobs[j].tile0) * kTile;
+    const int64_t row1 = min(jobs[j].n, row0 + kTile);
+    for (int64_t r = row0 + threadIdx.x; r < row1; r += kThreads) {
+      const U u = (U)keys[r] - lo;
+      for (int p = 0; p < passes; ++p)
+        atomicAdd(&s_h[p * kMaxBins + ((uint32_t)(u >> s_shift[p]) & s_mask[p])], 1u);
+    }
+  }
+  if (cur >= 0) {
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+      for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) {
+        const uint32_t c = s_h[p * kMaxBins + d];
+        if (c) atomicAdd(&jobs[cur].hist[p * jobs[cur].hist_stride + d], c);
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: exclusive scan of each (job, pass) digit histogram, in place
+// ---------------------------------------------------------------------------
+template <typename K>
+__global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs, int passes) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (int64_t)num_jobs * passes) return;
+  const int j = (int)(gw / passes), p = (int)(gw % passes);
+  if (p >= jobs[j].passes) return;
+  const int bins = 1 << jobs[j].bits[p];
+  uint32_t* h = jobs[j].hist + p * jobs[j].hist_stride;
+  uint32_t carry = 0;
+  for (int base = 0; base < bins; base += 32) {
+    const uint32_t v = (base + lane < bins) ? h[base + lane] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (base + lane < bins) h[base + lane] = carry + x - v;
+    carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: one onesweep digit pass
+// ---------------------------------------------------------------------------
+template <typename K>
+constexpr size_t onesweep_smem_bytes() {
+  return 2 * sizeof(K) * kTile                 // staged keys, staged ids
+         + sizeof(uint32_t) * kWarps * kMaxBins  // per-warp digit counters
+         + sizeof(uint32_t) * kMaxBins * 2       // tile counts, tile exclusive
+         + sizeof(long long) * kMaxBins;         // global base per digit
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_onesweep(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles, int pass,
+               uint32_t* __restrict__ tile_counter, int* __restrict__ err) {
+  using U = typename UnsignedOf<K>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  K* s_keys = reinterpret_cast<K*>(smem);
+  K* s_vals = s_keys + kTile;
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + kTile);
+  uint32_t* s_count = s_whist + kWarps * kMaxBins;
+  uint32_t* s_excl = s_count + kMaxBins;
+  long long* s_gbase = reinterpret_cast<long long*>(s_excl + kMaxBins);
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_t;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_t = atomicAdd(tile_counter, 1u);
+  __syncthreads();
+  const int64_t t = s_t;
+  if (t >= total_tiles) return;
+  const int j = find_job(jobs, num_jobs, t);
+  const RadixJob<K>* J = jobs + j;
+  const int64_t lt = t - J->tile0;
+  const int64_t row0 = lt * kTile;
+  const int nvalid = (int)min((int64_t)kTile, J->n - row0);
+  const int shift = J->shift[pass];
+  const int bins = 1 << J->bits[pass];
+  const uint32_t mask = (uint32_t)bins - 1u;
+  const U lo = (U)J->lo;
+  const K* __restrict__ src_k = J->src_k[pass] + row0;
+  const K* __restrict__ src_v = J->src_v[pass] + row0;
+  K* __restrict__ dst_k = J->dst_k[pass];
+  K* __restrict__ dst_v = J->dst_v[pass];
+  uint32_t* lb_base = J->lookback;
+  uint32_t* lb_mine = lb_base + lt * bins;
+  const uint32_t* hist = J->hist + pass * J->hist_stride;
+
+  for (int i = tid; i < kWarps * bins; i += kThreads) s_whist[i] = 0u;
+
+  // Warp-striped rows: warp w owns rows [w*32*kItems, (w+1)*32*kItems) of the
+  // tile; iteration i covers 32 consecutive rows, so ranks follow row order.
+  const int wbase = warp * 32 * kItems;
+  K key[kItems];
+  K val[kItems];
+  uint32_t rk[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int r = wbase + i * 32 + lane;
+    key[i] = r < nvalid ? src_k[r] : K(0);
+  }
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int r = wbase + i * 32 + lane;
+    val[i] = r < nvalid ? src_v[r] : K(0);
+  }
+  __syncthreads();
+
+  uint32_t* wh = s_whist + warp * bins;
+  const uint32_t ltm = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int r = wbase + i * 32 + lane;
+    const bool valid = r < nvalid;
+    const uint32_t d = valid ? digit_of<K>(key[i], lo, shift, mask) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    const uint32_t base = valid ? wh[d] : 0u;
+    __syncwarp();
+    if (valid && (peers >> lane) == 1u) wh[d] = base + __popc(peers);
+    __syncwarp();
+    rk[i] = base + __popc(peers & ltm);
+  }
+  __syncthreads();
+
+  // per digit: exclusive prefix over warps and the tile's count; publish it
+  for (int d = tid; d < bins; d += kThreads) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = s_whist[w * bins + d];
+      s_whist[w * bins + d] = run;
+      run += c;
+    }
+    s_count[d] = run;
+    st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | run);
+  }
+  __syncthreads();
+  block_excl_scan_bins(s_count, s_excl, bins, s_warp);
+
+  // decoupled look-back: sum predecessors' counts of this digit until an
+  // inclusive prefix is found.  Bounded wait; on timeout report and go on.
+  for (int d = tid; d < bins; d += kThreads) {
+    uint32_t prefix = 0;
+    if (lt > 0) {
+      const uint32_t* p = lb_mine - bins + d;
+      int64_t k = lt - 1;
+      int spins = 0;
+      while (true) {
+        const uint32_t v = ld_volatile_u32(p);
+        const uint32_t f = v & ~kValMask;
+        if (f == 0u) {
+          if (++spins > kSpinLimit) {
+            atomicExch(err, (int)TJ_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+          continue;
+        }
+        prefix += v & kValMask;
+        if (f == kFlagInc || k == 0) break;
+        --k;
+        p -= bins;
+        spins = 0;
+      }
+      st_volatile_u32(lb_mine + d, kFlagInc | ((prefix + s_count[d]) & kValMask));
+    }
+    s_gbase[d] = (long long)hist[d] + (long long)prefix - (long long)s_excl[d];
+  }
+  __syncthreads();
+
+  // place rows at their tile-sorted position in shared memory
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int r = wbase + i * 32 + lane;
+    if (r < nvalid) {
+      const uint32_t d = digit_of<K>(key[i], lo, shift, mask);
+      const uint32_t pos = s_excl[d] + s_whist[warp * bins + d] + rk[i];
+      s_keys[pos] = key[i];
+      s_vals[pos] = val[i];
+    }
+  }
+  __syncthreads();
+
+  // scatter: consecutive staged rows of one digit go to consecutive addresses
+  for (int q = tid; q < nvalid; q += kThreads) {
+    const K k = s_keys[q];
+    const uint32_t d = digit_of<K>(k, lo, shift, mask);
+    const long long g = s_gbase[d] + q;
+    dst_k[g] = k;
+    dst_v[g] = s_vals[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+cudaError_t launch_stats(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                         KeyStats* d_stats, cudaStream_t st) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const int64_t grid = total_tiles < 152 * 8 ? total_tiles : 152 * 8;
+  k_stats<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_stats);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_histogram(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                             cudaStream_t st) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const int64_t grid = (total_tiles + kHistTilesPerCta - 1) / kHistTilesPerCta;
+  k_histogram<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passes,
+                              cudaStream_t st) {
+  if (passes <= 0 || num_jobs <= 0) return cudaSuccess;
+  const int64_t warps = (int64_t)num_jobs * passes;
+  const int64_t grid = (warps * 32 + kThreads - 1) / kThreads;
+  k_digit_scan<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, passes);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                            int pass, int max_bits, uint32_t* d_tile_counter, int* d_err,
+                            cudaStream_t st) {
+  (void)max_bits;
+  if (total_tiles <= 0) return cudaSuccess;
+  const size_t smem = onesweep_smem_bytes<K>();
+  k_onesweep<K><<<(unsigned)total_tiles, kThreads, smem, st>>>(d_jobs, num_jobs, total_tiles, pass,
+                                                               d_tile_counter, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t radix_init_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_onesweep<int32_t>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)onesweep_smem_bytes<int32_t>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_onesweep<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)onesweep_smem_bytes<int64_t>());
+}
+
+#define TJ_INSTANTIATE_RADIX(K)                                                                 \
+  template cudaError_t launch_stats<K>(const RadixJob<K>*, int, int64_t, KeyStats*,             \
+                                       cudaStream_t);                                           \
+  template cudaError_t launch_histogram<K>(const RadixJob<K>*, int, int64_t, cudaStream_t);     \
+  template cudaError_t launch_digit_scan<K>(const RadixJob<K>*, int, int, cudaStream_t);        \
+  template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, uint32_t*, \
+                                          int*, cudaStream_t);
+TJ_INSTANTIATE_RADIX(int32_t)
+TJ_INSTANTIATE_RADIX(int64_t)
+
+}  // namespace tj
