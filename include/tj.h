@@ -53,15 +53,43 @@ typedef enum { TJ_I32 = 0, TJ_I64 = 1 } tj_dtype;
 /* Per-call counters of the calling thread's last successful call. */
 typedef struct {
   int32_t key_bits;        /* significant bits of (key - min) over both inputs */
-  int32_t radix_passes;    /* digit passes per sorted array */
+  int32_t radix_passes;    /* digit passes per sorted array (max over batches) */
   int32_t digit_bits;      /* widest digit used */
-  int32_t groups;          /* key-range groups processed (1 = single pass) */
-  int64_t scratch_peak;    /* peak bytes of library scratch live at once */
-  int64_t staging_bytes;   /* bytes of partitioned relation copies (batches) */
+  int32_t groups;          /* passes over groups of batches (1 = single pass) */
+  int64_t scratch_peak;    /* peak bytes of library working set live at once */
+  int64_t staging_bytes;   /* bytes of the key-range batches (partitioned copies) */
   int64_t out_count;       /* pairs produced (join) */
   int32_t used_hbm_table;  /* 1 if the HBM hash table path ran */
-  int32_t learned;         /* 1 if learned routing ran, 2 if it fell back to radix */
+  int32_t learned;         /* router used: tj_router value; +100 if it fell back to radix */
+  int32_t partitions;      /* key-range batches of the route pass (0 = single pass) */
+  int32_t heavy_keys;      /* keys that got a batch of their own */
+  int64_t max_partition;   /* rows (R + S) of the largest batch */
+  double balance;          /* largest batch / mean batch (1 = perfect) */
+  double radix_balance;    /* the same for equal-width key ranges, from the sample */
 } tj_stats;
+
+/*
+ * How the join partitions its inputs (no counterpart in the paper, which
+ * leaves the execution design open).
+ */
+typedef enum {
+  TJ_ROUTE_AUTO = 0,   /* single pass if its scratch fits the budget, else TJ_ROUTE_PLA */
+  TJ_ROUTE_SINGLE = 1, /* sort both relations whole, then align (TJ_ERR_BUDGET if too big) */
+  TJ_ROUTE_RADIX = 2,  /* key-range batches of equal width (top bits of key - min) */
+  TJ_ROUTE_PLA = 3,    /* batches from a piecewise-linear CDF on a sample's quantiles */
+  TJ_ROUTE_MLP = 4     /* batches from a 1-32-32-1 MLP CDF trained on the device */
+} tj_router;
+
+typedef struct {
+  int32_t router;        /* tj_router */
+  int32_t partitions;    /* key-range batches requested, 2..1024 (0 = 1024) */
+  int32_t sample_stride; /* sample one row in this many (0 = 100, a 1% sample) */
+  int32_t pla_segments;  /* segments of the piecewise-linear CDF (0 = 4096) */
+  int32_t mlp_steps;     /* Adam steps of the MLP (0 = 600) */
+  int32_t mlp_batch;     /* sample rows per step (0 = 512) */
+  float mlp_lr;          /* Adam learning rate (0 = 3e-3) */
+  uint64_t seed;         /* sample offsets, MLP initialisation and batches (0 = 20260221) */
+} tj_join_opts;
 
 /*
  * Inner equi-join (Sec. 4.1): J = { (r.id, s.id) : r.key == s.key }.
@@ -89,6 +117,19 @@ tj_status tj_join_inner(tj_dtype dt, const void* keys_r, const void* ids_r, int6
                         int64_t* out_count, void* stream);
 
 /*
+ * tj_join_inner with an explicit partitioning choice (opts may be NULL for the
+ * defaults).  Partitioned joins route both relations to key-range batches in
+ * one pass, then sort and align groups of batches whose working set fits
+ * mem_budget_bytes, one group after another; a key heavy enough to hold a
+ * whole batch's share of rows gets a batch of its own and needs no sort.
+ * The result is the same for every router.
+ */
+tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, int64_t n_r,
+                           const void* keys_s, const void* ids_s, int64_t n_s,
+                           size_t mem_budget_bytes, const tj_join_opts* opts, void* out_pairs,
+                           int64_t out_capacity, int64_t* out_count, void* stream);
+
+/*
  * ORDER BY key (Sec. 4.2): stable sort of the rows (keys[i], ids[i]) by key
  * ascending, in place.  n rows; keys and ids are device arrays (read-write).
  * Synchronises `stream` once (key statistics for the digit plan).
@@ -110,6 +151,85 @@ tj_status tj_join_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off, const
                         const void* keys_r, const void* ids_r, const void* keys_s,
                         const void* ids_s, void* out_pairs, int64_t out_capacity,
                         int64_t* out_off, int64_t* out_count, void* stream);
+
+/*
+ * Checks of the learned partitioner's network (no counterpart in the paper).
+ * tj_mlp_grad: gradient of the mean squared error of the 1-32-32-1 ReLU
+ * network with parameters theta (1153 fp32, layout
+ * [b3 | w1(32) | b1(32) | W2(32x32, row i from hidden-1 unit i) | b2(32) | w3(32)])
+ * on the batch (x[i], y[i]), i < n, 1 <= n <= 256, written to grad (1153).
+ * tj_mlp_adam: one Adam step t >= 1 (beta 0.9 / 0.999, eps 1e-8, learning
+ * rate lr) on n parameters, updating theta, m and v in place.  All pointers
+ * are device arrays; both calls synchronise `stream`.
+ */
+tj_status tj_mlp_grad(const float* theta, const float* x, const float* y, int n, float* grad,
+                      void* stream);
+tj_status tj_mlp_adam(float* theta, float* m, float* v, const float* grad, int n, int t,
+                      float lr, void* stream);
+
+/*
+ * Serving loop (no counterpart in the paper; it measures the P50/P99 latency
+ * the paper reports, Sec. 5.2 and Sec. 6, for a stream of requests).
+ *
+ * A server owns `workers` host threads, each with its own CUDA stream on the
+ * device that was current at tj_server_create.  Submitted requests wait in
+ * one FIFO queue; the head is admitted as soon as a worker is free and its
+ * footprint fits in what mem_budget_bytes has left (footprint = the scratch
+ * its library call may hold + its output buffer, out_capacity pairs).  Admitted
+ * requests run concurrently on their workers' streams; a completion releases
+ * its reservation and admits the next request (continuous batching).  A
+ * request whose footprint exceeds the whole budget completes at once with
+ * TJ_ERR_BUDGET.  Inputs and outputs are caller-owned device arrays that must
+ * stay valid until the request completes; results are the same as those of
+ * the direct calls.
+ */
+typedef enum { TJ_OP_JOIN = 0, TJ_OP_SORT = 1 } tj_op;
+
+typedef struct {
+  int32_t op;            /* tj_op */
+  int32_t dt;            /* tj_dtype */
+  void* keys_r;          /* join: R columns; sort: the relation sorted in place */
+  void* ids_r;
+  int64_t n_r;
+  const void* keys_s;    /* join only */
+  const void* ids_s;
+  int64_t n_s;
+  void* out_pairs;       /* join only: out_capacity pairs */
+  int64_t out_capacity;
+} tj_request;
+
+typedef struct {
+  int32_t status;        /* tj_status of the call */
+  int64_t out_count;     /* join: pairs (or required count on TJ_ERR_CAPACITY) */
+  double latency_ms;     /* completion - arrival (submission) */
+} tj_result;
+
+typedef struct {
+  int64_t completed;
+  double p50_ms, p99_ms, max_ms, mean_ms;  /* request latency */
+  int64_t tuples;                          /* input rows of completed requests */
+  double makespan_s;                       /* first arrival -> last completion */
+  int64_t peak_reserved;                   /* bytes reserved at once, <= budget */
+  int32_t peak_inflight;                   /* requests running at once */
+} tj_server_stats;
+
+typedef struct tj_server tj_server;
+
+tj_status tj_server_create(size_t mem_budget_bytes, int workers, tj_server** out);
+/* Queue a request; *ticket identifies it.  Never blocks on admission. */
+tj_status tj_server_submit(tj_server* s, const tj_request* req, int64_t* ticket);
+/* Submit reqs[i] at arrival_s[i] seconds after the call starts (non-decreasing),
+ * from the calling thread; returns once all are submitted. */
+tj_status tj_server_replay(tj_server* s, const tj_request* reqs, const double* arrival_s,
+                           int64_t n, int64_t* tickets);
+/* Block until the request completes; *res receives its outcome. */
+tj_status tj_server_wait(tj_server* s, int64_t ticket, tj_result* res);
+/* Block until nothing is queued or running. */
+tj_status tj_server_drain(tj_server* s);
+tj_status tj_server_report(tj_server* s, tj_server_stats* out);
+tj_status tj_server_reset_stats(tj_server* s);
+/* Drains, stops the workers and frees the server. */
+void tj_server_destroy(tj_server* s);
 
 /* Text of a status code (static storage). */
 const char* tj_status_str(tj_status s);

@@ -36,7 +36,19 @@ class _Stats(ctypes.Structure):
                 ("digit_bits", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("scratch_peak", ctypes.c_int64), ("staging_bytes", ctypes.c_int64),
                 ("out_count", ctypes.c_int64), ("used_hbm_table", ctypes.c_int32),
-                ("learned", ctypes.c_int32)]
+                ("learned", ctypes.c_int32), ("partitions", ctypes.c_int32),
+                ("heavy_keys", ctypes.c_int32), ("max_partition", ctypes.c_int64),
+                ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("router", ctypes.c_int32), ("partitions", ctypes.c_int32),
+                ("sample_stride", ctypes.c_int32), ("pla_segments", ctypes.c_int32),
+                ("mlp_steps", ctypes.c_int32), ("mlp_batch", ctypes.c_int32),
+                ("mlp_lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+ROUTERS = {"auto": 0, "single": 1, "radix": 2, "pla": 3, "mlp": 4}
 
 
 def lib_path() -> str:
@@ -55,6 +67,9 @@ def _load():
         p64 = ctypes.POINTER(ctypes.c_int64)
         lib.tj_join_inner.argtypes = [ci, vp, vp, i64, vp, vp, i64, sz, vp, i64, p64, vp]
         lib.tj_join_inner.restype = ci
+        lib.tj_join_inner_ex.argtypes = [ci, vp, vp, i64, vp, vp, i64, sz,
+                                         ctypes.POINTER(_Opts), vp, i64, p64, vp]
+        lib.tj_join_inner_ex.restype = ci
         lib.tj_sort.argtypes = [ci, vp, vp, i64, vp]
         lib.tj_sort.restype = ci
         lib.tj_join_batch.argtypes = [ci, i64, p64, p64, vp, vp, vp, vp, vp, i64, vp, p64, vp]
@@ -67,6 +82,10 @@ def _load():
         lib.tj_get_stats.restype = ci
         lib.tj_version.argtypes = []
         lib.tj_version.restype = ctypes.c_char_p
+        lib.tj_mlp_grad.argtypes = [vp, vp, vp, ci, vp, vp]
+        lib.tj_mlp_grad.restype = ci
+        lib.tj_mlp_adam.argtypes = [vp, vp, vp, vp, ci, ci, ctypes.c_float, vp]
+        lib.tj_mlp_adam.restype = ci
         lib.tj_trace_enable.argtypes = [ci]
         lib.tj_trace_enable.restype = None
         lib.tj_trace_reset.argtypes = []
@@ -139,18 +158,50 @@ def trace_table() -> dict:
     return out
 
 
+def mlp_grad(theta, x, y, stream=None):
+    """Gradient (1153 fp32) of the learned partitioner's network on a batch
+    (tj_mlp_grad); theta, x, y are CUDA float32 tensors."""
+    lib = _load()
+    for t in (theta, x, y):
+        if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError("theta, x, y must be contiguous CUDA float32 tensors")
+    g = torch.empty_like(theta)
+    with torch.cuda.device(theta.device):
+        _check(lib, lib.tj_mlp_grad(theta.data_ptr(), x.data_ptr(), y.data_ptr(), x.numel(),
+                                    g.data_ptr(), _stream(stream)))
+    return g
+
+
+def mlp_adam(theta, m, v, g, t: int, lr: float, stream=None):
+    """One Adam step in place on CUDA float32 tensors (tj_mlp_adam)."""
+    lib = _load()
+    with torch.cuda.device(theta.device):
+        _check(lib, lib.tj_mlp_adam(theta.data_ptr(), m.data_ptr(), v.data_ptr(), g.data_ptr(),
+                                    theta.numel(), int(t), float(lr), _stream(stream)))
+    return theta, m, v
+
+
 def version() -> str:
     return _load().tj_version().decode()
 
 
 def join_inner(keys_r, ids_r, keys_s, ids_s, mem_budget_bytes: int = 0, out=None,
-               stream=None):
+               stream=None, router: str | None = None, partitions: int = 0,
+               sample_stride: int = 0, pla_segments: int = 0, mlp_steps: int = 0,
+               mlp_batch: int = 0, mlp_lr: float = 0.0, seed: int = 0):
     """Inner equi-join (paper Sec. 4.1) -> (count, 2) tensor of (r_id, s_id)
     ordered by key, then S position, then R position.
 
     `out`, if given, is a (capacity, 2) tensor of the id dtype that receives the
     pairs; otherwise one of n_s rows is tried first and, if the result is
-    larger, the join is run again into a buffer of the exact size."""
+    larger, the join is run again into a buffer of the exact size.  `router`
+    ('auto', 'single', 'radix', 'pla', 'mlp') and the other keywords fill
+    tj_join_opts (0 = library default)."""
+    opts = None
+    if router is not None or partitions or sample_stride or pla_segments or mlp_steps or \
+            mlp_batch or mlp_lr or seed:
+        opts = _Opts(ROUTERS[router or "auto"], int(partitions), int(sample_stride),
+                     int(pla_segments), int(mlp_steps), int(mlp_batch), float(mlp_lr), int(seed))
     lib = _load()
     dev = keys_r.device
     dt = _dt(keys_r)
@@ -164,10 +215,12 @@ def join_inner(keys_r, ids_r, keys_s, ids_s, mem_budget_bytes: int = 0, out=None
 
         def run(buf):
             cap = 0 if buf is None else buf.shape[0]
-            return lib.tj_join_inner(dt, keys_r.data_ptr(), ids_r.data_ptr(), keys_r.numel(),
-                                     keys_s.data_ptr(), ids_s.data_ptr(), keys_s.numel(),
-                                     int(mem_budget_bytes), 0 if buf is None else buf.data_ptr(),
-                                     cap, ctypes.byref(cnt), sp)
+            return lib.tj_join_inner_ex(dt, keys_r.data_ptr(), ids_r.data_ptr(), keys_r.numel(),
+                                        keys_s.data_ptr(), ids_s.data_ptr(), keys_s.numel(),
+                                        int(mem_budget_bytes),
+                                        ctypes.byref(opts) if opts is not None else None,
+                                        0 if buf is None else buf.data_ptr(),
+                                        cap, ctypes.byref(cnt), sp)
 
         if out is not None:
             if out.dim() != 2 or out.shape[1] != 2 or out.dtype != keys_r.dtype or \
@@ -236,3 +289,128 @@ def join_batch(r_off, s_off, keys_r, ids_r, keys_s, ids_s, out=None, stream=None
             st = run(buf)
         _check(lib, st)
         return buf[: cnt.value], out_off
+
+
+# ---------------------------------------------------------------------------
+# serving loop (tj_server_*)
+# ---------------------------------------------------------------------------
+class _Req(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("dt", ctypes.c_int32), ("keys_r", ctypes.c_void_p),
+                ("ids_r", ctypes.c_void_p), ("n_r", ctypes.c_int64),
+                ("keys_s", ctypes.c_void_p), ("ids_s", ctypes.c_void_p),
+                ("n_s", ctypes.c_int64), ("out_pairs", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_int64)]
+
+
+class _Res(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("out_count", ctypes.c_int64),
+                ("latency_ms", ctypes.c_double)]
+
+
+class _SStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("tuples", ctypes.c_int64),
+                ("makespan_s", ctypes.c_double), ("peak_reserved", ctypes.c_int64),
+                ("peak_inflight", ctypes.c_int32)]
+
+
+def _server_lib():
+    lib = _load()
+    if not getattr(lib, "_srv_ready", False):
+        vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        p64 = ctypes.POINTER(ctypes.c_int64)
+        lib.tj_server_create.argtypes = [ctypes.c_size_t, ci, ctypes.POINTER(vp)]
+        lib.tj_server_create.restype = ci
+        lib.tj_server_submit.argtypes = [vp, ctypes.POINTER(_Req), p64]
+        lib.tj_server_submit.restype = ci
+        lib.tj_server_replay.argtypes = [vp, ctypes.POINTER(_Req),
+                                         ctypes.POINTER(ctypes.c_double), i64, p64]
+        lib.tj_server_replay.restype = ci
+        lib.tj_server_wait.argtypes = [vp, i64, ctypes.POINTER(_Res)]
+        lib.tj_server_wait.restype = ci
+        lib.tj_server_drain.argtypes = [vp]
+        lib.tj_server_drain.restype = ci
+        lib.tj_server_report.argtypes = [vp, ctypes.POINTER(_SStats)]
+        lib.tj_server_report.restype = ci
+        lib.tj_server_reset_stats.argtypes = [vp]
+        lib.tj_server_reset_stats.restype = ci
+        lib.tj_server_destroy.argtypes = [vp]
+        lib.tj_server_destroy.restype = None
+        lib._srv_ready = True
+    return lib
+
+
+class Server:
+    """Continuous-batching server over the C ABI (tj_server_*): requests are
+    admitted FIFO as workers and device memory (mem_budget_bytes) free up and
+    run concurrently on the workers' streams."""
+
+    def __init__(self, mem_budget_bytes: int, workers: int = 4):
+        self._lib = _server_lib()
+        h = ctypes.c_void_p()
+        _check(self._lib, self._lib.tj_server_create(int(mem_budget_bytes), int(workers),
+                                                     ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    @staticmethod
+    def join_request(keys_r, ids_r, keys_s, ids_s, out):
+        r = _Req(0, _dt(keys_r), keys_r.data_ptr(), ids_r.data_ptr(), keys_r.numel(),
+                 keys_s.data_ptr(), ids_s.data_ptr(), keys_s.numel(), out.data_ptr(),
+                 out.shape[0])
+        r._tensors = (keys_r, ids_r, keys_s, ids_s, out)
+        return r
+
+    @staticmethod
+    def sort_request(keys, ids):
+        r = _Req(1, _dt(keys), keys.data_ptr(), ids.data_ptr(), keys.numel(), None, None, 0,
+                 None, 0)
+        r._tensors = (keys, ids)
+        return r
+
+    def submit(self, req) -> int:
+        t = ctypes.c_int64(0)
+        _check(self._lib, self._lib.tj_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = req
+        return t.value
+
+    def replay(self, reqs, arrival_s):
+        n = len(reqs)
+        arr = (_Req * n)(*reqs)
+        ts = (ctypes.c_double * n)(*[float(x) for x in arrival_s])
+        tk = (ctypes.c_int64 * n)()
+        _check(self._lib, self._lib.tj_server_replay(self._h, arr, ts, n, tk))
+        out = list(tk)
+        for t, r in zip(out, reqs):
+            self._keep[t] = r
+        return out
+
+    def wait(self, ticket: int) -> dict:
+        r = _Res()
+        _check(self._lib, self._lib.tj_server_wait(self._h, int(ticket), ctypes.byref(r)))
+        self._keep.pop(ticket, None)
+        return {"status": r.status, "out_count": r.out_count, "latency_ms": r.latency_ms}
+
+    def drain(self):
+        _check(self._lib, self._lib.tj_server_drain(self._h))
+
+    def report(self) -> dict:
+        s = _SStats()
+        _check(self._lib, self._lib.tj_server_report(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _SStats._fields_}
+
+    def reset_stats(self):
+        _check(self._lib, self._lib.tj_server_reset_stats(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.tj_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,6 +54,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     nvcc = _nvcc()
     os.makedirs(OBJ, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_v else []
+    extra += os.environ.get("TJ_NVCC_EXTRA", "").split()
 
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")

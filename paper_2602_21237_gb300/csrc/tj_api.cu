@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <limits>
 #include <mutex>
 #include <vector>
 
@@ -39,6 +40,7 @@ tj_status set_err(tj_status s, const char* fmt, ...) {
   } while (0)
 
 constexpr int64_t kMaxRows = (int64_t)1 << 30;
+constexpr int kMlpTable = 4096;  // grid of the MLP's monotone tabulation
 
 // ---- kernel trace ------------------------------------------------------------------
 struct TraceRow {
@@ -147,6 +149,7 @@ tj_status ensure_device() {
   TJ_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
   TJ_CUDA(radix_init_attributes());
   TJ_CUDA(join_init_attributes());
+  TJ_CUDA(mlp_init_attributes());
   g_inited[dev] = true;
   return TJ_OK;
 }
@@ -191,13 +194,20 @@ struct Plan {
 
 int bitlen(uint64_t x) { return x ? 64 - __builtin_clzll(x) : 0; }
 
-// passes = ceil(b / kMaxDigitBits) (rounded up to even if asked), digits of
-// ceil(b / passes) bits from the least significant end.
-Plan make_plan(uint64_t lo, uint64_t range, bool even, int force_passes = -1) {
+// passes = ceil(b / max_digit) (rounded up to even if asked), digits of
+// ceil(b / passes) bits from the least significant end.  The widest digit is
+// 10 bits for int32 rows and 9 bits for int64 rows, the widest that keeps two
+// onesweep CTAs resident per SM.
+template <typename K>
+constexpr int max_digit_bits() {
+  return sizeof(K) == 4 ? 10 : 9;
+}
+
+Plan make_plan(uint64_t lo, uint64_t range, bool even, int max_digit, int force_passes = -1) {
   Plan p;
   p.lo = lo;
   p.key_bits = bitlen(range);
-  int P = force_passes >= 0 ? force_passes : (p.key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+  int P = force_passes >= 0 ? force_passes : (p.key_bits + max_digit - 1) / max_digit;
   if (even && (P & 1)) ++P;
   if (P > kMaxPasses) P = kMaxPasses;
   p.passes = P;
@@ -267,9 +277,43 @@ void set_job_buffers(RadixJob<K>& j, const K* in_k, const K* in_v, K* ak, K* av,
 }
 
 // ---- inner join -------------------------------------------------------------------
+struct Opts {
+  int router = TJ_ROUTE_AUTO;
+  int partitions = 1024;
+  int stride = 100;
+  int segments = 4096;
+  int mlp_steps = 600;
+  int mlp_batch = 512;
+  float mlp_lr = 3e-3f;
+  uint64_t seed = 20260221ull;
+};
+
+Opts make_opts(const tj_join_opts* o) {
+  Opts x;
+  if (!o) return x;
+  x.router = o->router;
+  if (o->partitions > 0) x.partitions = o->partitions;
+  if (o->sample_stride > 0) x.stride = o->sample_stride;
+  if (o->pla_segments > 0) x.segments = o->pla_segments;
+  if (o->mlp_steps > 0) x.mlp_steps = o->mlp_steps;
+  if (o->mlp_batch > 0) x.mlp_batch = o->mlp_batch;
+  if (o->mlp_lr > 0.f) x.mlp_lr = o->mlp_lr;
+  if (o->seed) x.seed = o->seed;
+  return x;
+}
+
+template <typename K>
+tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is,
+                         int64_t ns, K lo, K hi, size_t budget, const Opts& o, K* out,
+                         int64_t cap, int64_t* out_count, tj_stats& stats, Tracer& tr,
+                         cudaStream_t st);
+template <typename K>
+tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st);
+
 template <typename K>
 tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is, int64_t ns,
-                    size_t budget, K* out, int64_t cap, int64_t* out_count, cudaStream_t st) {
+                    size_t budget, const Opts& opts, K* out, int64_t cap, int64_t* out_count,
+                    cudaStream_t st) {
   tj_stats stats = {};
   stats.groups = 1;
   *out_count = 0;
@@ -322,7 +366,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
     return TJ_OK;
   }
   const K lo = std::min(min_r, min_s), hi = std::max(max_r, max_s);
-  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), false);
+  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), false, max_digit_bits<K>());
   stats.key_bits = plan.key_bits;
   stats.radix_passes = plan.passes;
   stats.digit_bits = plan.max_bits;
@@ -345,6 +389,21 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   const size_t o_rb = bc.add<int64_t>(jtiles);
   const size_t o_jlb = bc.add<uint64_t>(jtiles);
   const size_t need = bc.off + cc.off;
+  int router = opts.router;
+  if (router == TJ_ROUTE_AUTO)
+    router = (budget == 0 || need <= budget) ? TJ_ROUTE_SINGLE : TJ_ROUTE_PLA;
+  if (router != TJ_ROUTE_SINGLE) {
+    stats.learned = router;
+    Opts po = opts;
+    po.router = router;
+    tj_status ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, budget, po, out, cap,
+                                     out_count, stats, tr, st);
+    if (ps == TJ_OK || ps == TJ_ERR_CAPACITY) {
+      stats.out_count = *out_count;
+      g_stats = stats;
+    }
+    return ps;
+  }
   if (budget != 0 && need > budget)
     return set_err(TJ_ERR_BUDGET,
                    "join needs %zu bytes of scratch in one pass, budget is %zu", need, budget);
@@ -382,7 +441,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
       TJ_CUDA(cudaMemsetAsync(hj[0].lookback, 0,
                               (size_t)(tiles_r + tiles_s) * bins_max * sizeof(uint32_t), st));
       tr.begin("onesweep", 4.0 * w * (nr + ns));
-      TJ_CUDA(launch_onesweep<K>(d_jobs, 2, tiles_r + tiles_s, p, plan.max_bits, d_counters + p,
+      TJ_CUDA(launch_onesweep<K>(d_jobs, 2, tiles_r + tiles_s, p, plan.max_bits, false, d_counters + p,
                                  d_err, st));
       tr.end();
     }
@@ -404,7 +463,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   TJ_CUDA(cudaMemsetAsync(d_jlb, 0, jtiles * sizeof(uint64_t), st));
   tr.begin("join", 2.0 * w * (nr + ns));
   TJ_CUDA(launch_join<K>(d_jj, 1, jtiles, d_ra, d_rb, d_jlb, d_counters + kMaxPasses, out, cap,
-                         nullptr, d_total, d_err, st));
+                         nullptr, nullptr, d_total, d_err, st));
   tr.end();
   int64_t h_misc[2] = {0, 0};
   int h_err = 0;
@@ -420,6 +479,401 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   if (h_misc[0] > cap)
     return set_err(TJ_ERR_CAPACITY, "result has %lld pairs, capacity %lld",
                    (long long)h_misc[0], (long long)cap);
+  return TJ_OK;
+}
+
+
+// ---- partitioned (multi-pass) join --------------------------------------------------
+// 1. cut keys from the router (equal-width ranges, or sample quantiles);
+// 2. one route pass moves R and S into key-range batches (staging);
+// 3. batches are grouped in key order so that each group's working set (sort
+//    buffers, histograms, look-back, join state) fits the budget, and every
+//    group is sorted and aligned by one batched launch sequence, its output
+//    written after the previous group's (device-side running offset).
+template <typename K>
+std::vector<K> make_cuts(const std::vector<K>& b) {
+  std::vector<K> v(b);
+  std::sort(v.begin(), v.end());
+  std::vector<K> out;
+  for (size_t i = 0; i < v.size();) {
+    size_t j = i;
+    while (j < v.size() && v[j] == v[i]) ++j;
+    out.push_back(v[i]);
+    // a boundary that repeats holds at least one batch's worth of rows: give
+    // it a batch of its own by also cutting right after it
+    if (j - i >= 2 && v[i] < std::numeric_limits<K>::max()) out.push_back((K)(v[i] + 1));
+    i = j;
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+  return out;
+}
+
+template <typename K>
+tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is,
+                         int64_t ns, K lo, K hi, size_t budget, const Opts& o, K* out,
+                         int64_t cap, int64_t* out_count, tj_stats& stats, Tracer& tr,
+                         cudaStream_t st) {
+  const double w = (double)sizeof(K);
+  const int maxd = max_digit_bits<K>();
+  int parts = std::max(2, std::min(o.partitions, kMaxCuts));
+  std::vector<K> cuts;
+  int router = o.router;
+  // ---- 1. cut keys ----
+  if (router == TJ_ROUTE_PLA || router == TJ_ROUTE_MLP) {
+    const int stride = o.stride;
+    const int64_t off_r = (int64_t)((o.seed * 0x9E3779B97F4A7C15ull) >> 33) % std::min<int64_t>(stride, nr);
+    const int64_t off_s = (int64_t)((o.seed * 0xBF58476D1CE4E5B9ull) >> 33) % std::min<int64_t>(stride, ns);
+    const int64_t m_r = (nr - off_r + stride - 1) / stride, m_s = (ns - off_s + stride - 1) / stride;
+    const int64_t m = m_r + m_s;
+    int G = std::max(o.segments, parts);
+    G = (G / parts) * parts;  // boundaries fall on knots
+    Carve c;
+    const size_t o_k = c.add<K>((size_t)m), o_v = c.add<K>((size_t)m), o_b = c.add<K>((size_t)parts);
+    const size_t o_th = c.add<float>(kMlpParams), o_tab = c.add<float>(kMlpTable + 1);
+    Block sb;
+    TJ_CUDA(sb.alloc(c.off, st));
+    TJ_CUDA(launch_sample_gather<K>(kr, m_r, off_r, ks, m_s, off_s, stride, sb.at<K>(o_k),
+                                    sb.at<K>(o_v), st));
+    const tj_stats keep = g_stats;
+    tj_status ss = sort_impl<K>(sb.at<K>(o_k), sb.at<K>(o_v), m, st);
+    g_stats = keep;
+    if (ss != TJ_OK) return ss;
+    std::vector<K> bnd((size_t)(parts - 1));
+    if (router == TJ_ROUTE_PLA) {
+      // boundaries of the piecewise-linear CDF: knots t_{(G / parts) p}
+      const int step = G / parts;
+      tr.begin("pla_fit", w * (double)m);
+      TJ_CUDA(launch_quantiles<K>(sb.at<K>(o_k), m, G, step, step * (parts - 1), step,
+                                  sb.at<K>(o_b), st));
+      tr.end();
+    } else {
+      // MLP: seeded uniform initialisation on the host, training and the
+      // monotone tabulation on the device
+      std::vector<float> th(kMlpParams, 0.f);
+      uint64_t z = o.seed;
+      auto uni = [&](float a) {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        return a * (2.f * (float)((x >> 40) * (1.0 / 16777216.0)) - 1.f);
+      };
+      for (int i = 0; i < 32; ++i) th[1 + i] = uni(2.45f);          // w1
+      for (int i = 0; i < 32; ++i) th[33 + i] = uni(1.0f);          // b1
+      for (int i = 0; i < 1024; ++i) th[65 + i] = uni(0.433f);      // W2
+      for (int i = 0; i < 32; ++i) th[1121 + i] = uni(0.433f);      // w3
+      TJ_CUDA(cudaMemcpyAsync(sb.at<float>(o_th), th.data(), th.size() * 4,
+                              cudaMemcpyHostToDevice, st));
+      tr.begin("mlp_train", 0.0);
+      TJ_CUDA(launch_mlp_train<K>(sb.at<K>(o_k), m, sb.at<float>(o_th), o.mlp_steps, o.mlp_lr,
+                                  o.seed, st));
+      tr.end();
+      tr.begin("mlp_route_table", 0.0);
+      TJ_CUDA(launch_mlp_boundaries<K>(sb.at<float>(o_th), kMlpTable, sb.at<float>(o_tab), parts,
+                                       sb.at<K>(o_k), m, sb.at<K>(o_b), st));
+      tr.end();
+    }
+    TJ_CUDA(cudaMemcpyAsync(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K),
+                            cudaMemcpyDeviceToHost, st));
+    // radix judge on the sample: balance of equal-width ranges of the same count
+    std::vector<K> samp((size_t)m);
+    TJ_CUDA(cudaMemcpyAsync(samp.data(), sb.at<K>(o_k), samp.size() * sizeof(K),
+                            cudaMemcpyDeviceToHost, st));
+    TJ_CUDA(cudaStreamSynchronize(st));
+    {
+      const int b = bitlen(range_of<K>(lo, hi));
+      int plog = 0;
+      while ((2 << plog) <= parts) ++plog;
+      const int sh = std::max(0, b - plog);
+      std::vector<int64_t> cnt((size_t)1 << plog, 0);
+      for (K x : samp) {
+        uint64_t d = range_of<K>(lo, x) >> sh;
+        if (d >= cnt.size()) d = cnt.size() - 1;
+        ++cnt[(size_t)d];
+      }
+      const int64_t mx = *std::max_element(cnt.begin(), cnt.end());
+      stats.radix_balance = (double)mx * (double)cnt.size() / (double)std::max<int64_t>(1, m);
+    }
+    cuts = make_cuts<K>(bnd);
+  } else {  // TJ_ROUTE_RADIX
+    router = TJ_ROUTE_RADIX;
+    const int b = bitlen(range_of<K>(lo, hi));
+    int plog = 0;
+    while ((2 << plog) <= parts) ++plog;
+    if (b <= plog) {
+      for (uint64_t x = 1; x <= range_of<K>(lo, hi); ++x)
+        cuts.push_back((K)(lo_bits<K>(lo) + x));
+    } else {
+      for (int64_t p = 1; p < ((int64_t)1 << plog); ++p)
+        cuts.push_back((K)(lo_bits<K>(lo) + ((uint64_t)p << (b - plog))));
+    }
+  }
+  while ((int)cuts.size() > kMaxCuts - 1) cuts.pop_back();  // cannot happen for parts <= 1024
+  const int ncuts = (int)cuts.size();
+  const int nparts = ncuts + 1;
+  int rbits = bitlen((uint64_t)ncuts);
+  if (rbits == 0) rbits = 1;
+  stats.partitions = nparts;
+  {
+    int heavy = 0;
+    for (int i = 0; i + 1 < ncuts; ++i)
+      if ((uint64_t)cuts[(size_t)i + 1] - (uint64_t)cuts[(size_t)i] == 1) ++heavy;
+    stats.heavy_keys = heavy;
+  }
+
+  // ---- 2. route pass into staging ----
+  const int64_t tiles_r = ceil_div(nr, kTile), tiles_s = ceil_div(ns, kTile);
+  Carve cc;
+  const size_t o_rk = cc.add<K>((size_t)nr), o_rv = cc.add<K>((size_t)nr);
+  const size_t o_sk = cc.add<K>((size_t)ns), o_sv = cc.add<K>((size_t)ns);
+  const size_t staging = cc.off;
+  const size_t o_cuts = cc.add<K>(kMaxCuts);
+  const size_t o_hist = cc.add<uint32_t>(2 * kMaxBins);
+  const size_t o_lb = cc.add<uint32_t>((size_t)(tiles_r + tiles_s) << rbits);
+  const size_t o_jobs = cc.add<RadixJob<K>>(2);
+  const size_t o_misc = cc.add<int64_t>(32);
+  Block stg;
+  TJ_CUDA(stg.alloc(cc.off, st));
+  stats.staging_bytes = (int64_t)staging;
+  int* d_err = stg.at<int>(o_misc);
+  uint32_t* d_counters = stg.at<uint32_t>(o_misc + 16);
+  int64_t* d_total = stg.at<int64_t>(o_misc + 128);
+  int64_t* d_base = stg.at<int64_t>(o_misc + 136);
+  std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
+  std::copy(cuts.begin(), cuts.end(), hc.begin());
+  TJ_CUDA(cudaMemcpyAsync(stg.at<K>(o_cuts), hc.data(), kMaxCuts * sizeof(K),
+                          cudaMemcpyHostToDevice, st));
+  RadixJob<K> hj[2];
+  memset(hj, 0, sizeof(hj));
+  for (int side = 0; side < 2; ++side) {
+    RadixJob<K>& x = hj[side];
+    x.keys = side ? ks : kr;
+    x.n = side ? ns : nr;
+    x.tile0 = side ? tiles_r : 0;
+    x.passes = 1;
+    x.bits[0] = rbits;
+    x.hist_stride = kMaxBins;
+    x.hist = stg.at<uint32_t>(o_hist) + side * kMaxBins;
+    x.lookback = stg.at<uint32_t>(o_lb) + (side ? (tiles_r << rbits) : 0);
+    x.src_k[0] = side ? ks : kr;
+    x.src_v[0] = side ? is : ir;
+    x.dst_k[0] = side ? stg.at<K>(o_sk) : stg.at<K>(o_rk);
+    x.dst_v[0] = side ? stg.at<K>(o_sv) : stg.at<K>(o_rv);
+    x.cuts = stg.at<K>(o_cuts);
+    x.ncuts = ncuts;
+  }
+  RadixJob<K>* d_rj = stg.at<RadixJob<K>>(o_jobs);
+  TJ_CUDA(cudaMemsetAsync(stg.p + o_misc, 0, 32 * sizeof(int64_t), st));
+  TJ_CUDA(cudaMemcpyAsync(d_rj, hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_hist), 0, 2 * kMaxBins * sizeof(uint32_t), st));
+  tr.begin("histogram", w * (nr + ns));
+  TJ_CUDA(launch_histogram<K>(d_rj, 2, tiles_r + tiles_s, st));
+  tr.end();
+  std::vector<uint32_t> hcount(2 * (size_t)kMaxBins);
+  TJ_CUDA(cudaMemcpyAsync(hcount.data(), stg.at<uint32_t>(o_hist), hcount.size() * 4,
+                          cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(launch_digit_scan<K>(d_rj, 2, 1, st));
+  TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_lb), 0,
+                          ((size_t)(tiles_r + tiles_s) << rbits) * sizeof(uint32_t), st));
+  tr.begin("route", 4.0 * w * (nr + ns));
+  TJ_CUDA(launch_onesweep<K>(d_rj, 2, tiles_r + tiles_s, 0, rbits, true, d_counters + kMaxPasses,
+                             d_err, st));
+  tr.end();
+  TJ_CUDA(cudaStreamSynchronize(st));  // partition sizes for the grouping
+
+  // ---- 3. batches and groups ----
+  struct Part {
+    int64_t r0, nr, s0, ns;
+    K lo, hi;
+    Plan plan;
+    int64_t ws;
+  };
+  std::vector<Part> P;
+  int64_t r_at = 0, s_at = 0, maxrows = 0, live_rows = 0;
+  for (int j = 0; j < nparts; ++j) {
+    Part q;
+    q.nr = hcount[(size_t)j];
+    q.ns = hcount[(size_t)kMaxBins + j];
+    q.r0 = r_at;
+    q.s0 = s_at;
+    r_at += q.nr;
+    s_at += q.ns;
+    maxrows = std::max<int64_t>(maxrows, q.nr + q.ns);
+    if (q.nr == 0 || q.ns == 0) continue;
+    q.lo = j == 0 ? lo : std::max(lo, cuts[(size_t)j - 1]);
+    q.hi = j == ncuts ? hi : std::min(hi, (K)(cuts[(size_t)j] - 1));
+    q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd);
+    const int nb = std::min(q.plan.passes, 2);
+    const int64_t bins = (int64_t)1 << q.plan.max_bits;
+    q.ws = (int64_t)nb * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
+           (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * bins * 4 +
+           ceil_div(q.ns, kJTile) * 24 + 2 * (int64_t)sizeof(RadixJob<K>) +
+           (int64_t)sizeof(JoinJob<K>) + 2 * (int64_t)std::max(1, q.plan.passes) * bins * 4 + 4096;
+    live_rows += q.nr + q.ns;
+    P.push_back(q);
+  }
+  if (r_at != nr || s_at != ns) return set_err(TJ_ERR_INTERNAL, "route counts do not add up");
+  stats.max_partition = maxrows;
+  stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
+  const int64_t fixed = (int64_t)(cc.off - staging) + 4096;
+  const int64_t room = budget ? (int64_t)budget - fixed : INT64_MAX;
+  if (room <= 0) return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes",
+                                budget, (long long)fixed);
+  std::vector<std::pair<size_t, size_t>> groups;  // [first, last) into P
+  int64_t ws_max = 0;
+  for (size_t i = 0; i < P.size();) {
+    if (P[i].ws > room)
+      return set_err(TJ_ERR_BUDGET,
+                     "batch of keys [%lld, %lld] needs %lld bytes of working set, budget "
+                     "leaves %lld (raise the budget or the number of batches)",
+                     (long long)P[i].lo, (long long)P[i].hi, (long long)P[i].ws,
+                     (long long)room);
+    size_t j = i;
+    int64_t acc = 0;
+    while (j < P.size() && acc + P[j].ws <= room) acc += P[j].ws, ++j;
+    groups.push_back({i, j});
+    ws_max = std::max(ws_max, acc);
+    i = j;
+  }
+  stats.groups = (int)groups.size();
+  stats.scratch_peak = (int64_t)(cc.off - staging) + ws_max;
+
+  // ---- 4. one batched sort + align per group ----
+  // Group layout in the working block: job tables | sort buffers of every batch
+  // | histograms of every batch | look-back words of every batch | join state.
+  Block wk;
+  TJ_CUDA(wk.alloc((size_t)std::max<int64_t>(ws_max, 256), st));
+  int maxp = 0;
+  for (auto& g : groups) {
+    const size_t nj = g.second - g.first;
+    Carve gc;
+    const size_t o_gj = gc.add<RadixJob<K>>(2 * nj), o_gjj = gc.add<JoinJob<K>>(nj);
+    std::vector<size_t> o_buf(nj * 8, 0);
+    for (size_t i = 0; i < nj; ++i) {
+      const Part& q = P[g.first + i];
+      for (int b2 = 0; b2 < std::min(q.plan.passes, 2); ++b2) {
+        o_buf[i * 8 + 4 * b2 + 0] = gc.add<K>((size_t)q.nr);
+        o_buf[i * 8 + 4 * b2 + 1] = gc.add<K>((size_t)q.nr);
+        o_buf[i * 8 + 4 * b2 + 2] = gc.add<K>((size_t)q.ns);
+        o_buf[i * 8 + 4 * b2 + 3] = gc.add<K>((size_t)q.ns);
+      }
+    }
+    int P_g = 0, maxbits = 0;
+    size_t hist_words = 0, lb_words = 0;
+    std::vector<size_t> hist_at(nj * 2), lb_at(nj * 2);
+    for (size_t i = 0; i < nj; ++i) {
+      const Part& q = P[g.first + i];
+      const size_t bins = (size_t)1 << q.plan.max_bits;
+      for (int side = 0; side < 2; ++side) {
+        hist_at[i * 2 + side] = hist_words;
+        hist_words += (size_t)std::max(1, q.plan.passes) * bins;
+        lb_at[i * 2 + side] = lb_words;
+        lb_words += (size_t)ceil_div(side ? q.ns : q.nr, kTile) * bins;
+      }
+      P_g = std::max(P_g, q.plan.passes);
+      maxbits = std::max(maxbits, q.plan.max_bits);
+    }
+    const size_t o_hist_g = gc.add<uint32_t>(std::max<size_t>(hist_words, 1));
+    const size_t o_lb_g = gc.add<uint32_t>(std::max<size_t>(lb_words, 1));
+    std::vector<RadixJob<K>> rj;
+    std::vector<JoinJob<K>> jj;
+    int64_t tiles = 0, jtiles = 0;
+    double rows = 0;
+    for (size_t i = 0; i < nj; ++i) {
+      const Part& q = P[g.first + i];
+      rows += (double)(q.nr + q.ns);
+      const K* res[4];
+      for (int side = 0; side < 2; ++side) {
+        RadixJob<K> x;
+        memset(&x, 0, sizeof(x));
+        const int64_t n = side ? q.ns : q.nr;
+        const K* k0 = side ? stg.at<K>(o_sk) + q.s0 : stg.at<K>(o_rk) + q.r0;
+        const K* v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
+        x.keys = k0;
+        x.n = n;
+        x.tile0 = tiles;
+        tiles += ceil_div(n, kTile);
+        set_job_plan(x, q.plan);
+        x.hist_stride = 1 << q.plan.max_bits;
+        x.hist = wk.at<uint32_t>(o_hist_g) + hist_at[i * 2 + side];
+        x.lookback = wk.at<uint32_t>(o_lb_g) + lb_at[i * 2 + side];
+        const int nb = std::min(q.plan.passes, 2);
+        K* ak = nb > 0 ? wk.at<K>(o_buf[i * 8 + 2 * side]) : nullptr;
+        K* av = nb > 0 ? wk.at<K>(o_buf[i * 8 + 2 * side + 1]) : nullptr;
+        K* bk = nb > 1 ? wk.at<K>(o_buf[i * 8 + 4 + 2 * side]) : nullptr;
+        K* bv = nb > 1 ? wk.at<K>(o_buf[i * 8 + 4 + 2 * side + 1]) : nullptr;
+        set_job_buffers(x, k0, v0, ak, av, bk, bv, &res[2 * side], &res[2 * side + 1]);
+        rj.push_back(x);
+      }
+      JoinJob<K> y;
+      y.rk = res[0];
+      y.rv = res[1];
+      y.nr = q.nr;
+      y.sk = res[2];
+      y.sv = res[3];
+      y.ns = q.ns;
+      y.tile0 = jtiles;
+      jtiles += ceil_div(q.ns, kJTile);
+      jj.push_back(y);
+    }
+    const size_t o_ra = gc.add<int64_t>((size_t)jtiles), o_rb = gc.add<int64_t>((size_t)jtiles);
+    const size_t o_jlb = gc.add<uint64_t>((size_t)jtiles);
+    if ((int64_t)gc.off > std::max<int64_t>(ws_max, 256))
+      return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, working block has %lld", gc.off,
+                     (long long)ws_max);
+    maxp = std::max(maxp, P_g);
+    RadixJob<K>* d_gj = wk.at<RadixJob<K>>(o_gj);
+    JoinJob<K>* d_gjj = wk.at<JoinJob<K>>(o_gjj);
+    TJ_CUDA(cudaMemcpyAsync(d_gj, rj.data(), rj.size() * sizeof(RadixJob<K>),
+                            cudaMemcpyHostToDevice, st));
+    TJ_CUDA(cudaMemcpyAsync(d_gjj, jj.data(), jj.size() * sizeof(JoinJob<K>),
+                            cudaMemcpyHostToDevice, st));
+    TJ_CUDA(cudaMemsetAsync(d_counters, 0, (kMaxPasses + 1) * sizeof(uint32_t), st));
+    if (P_g > 0) {
+      TJ_CUDA(cudaMemsetAsync(wk.p + o_hist_g, 0, hist_words * sizeof(uint32_t), st));
+      tr.begin("histogram", w * rows);
+      TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), tiles, st));
+      tr.end();
+      TJ_CUDA(launch_digit_scan<K>(d_gj, (int)(2 * nj), P_g, st));
+      for (int p = 0; p < P_g; ++p) {
+        double prow = 0;
+        for (size_t i = 0; i < nj; ++i)
+          if (P[g.first + i].plan.passes > p)
+            prow += (double)(P[g.first + i].nr + P[g.first + i].ns);
+        TJ_CUDA(cudaMemsetAsync(wk.p + o_lb_g, 0, lb_words * sizeof(uint32_t), st));
+        tr.begin("onesweep", 4.0 * w * prow);
+        TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), tiles, p, maxbits, false, d_counters + p,
+                                   d_err, st));
+        tr.end();
+      }
+    }
+    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, jtiles, wk.at<int64_t>(o_ra),
+                                  wk.at<int64_t>(o_rb), st));
+    TJ_CUDA(cudaMemsetAsync(wk.at<uint64_t>(o_jlb), 0, (size_t)std::max<int64_t>(jtiles, 1) * 8,
+                            st));
+    tr.begin("join", 2.0 * w * rows);
+    TJ_CUDA(launch_join<K>(d_gjj, (int)nj, jtiles, wk.at<int64_t>(o_ra), wk.at<int64_t>(o_rb),
+                           wk.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, d_base,
+                           nullptr, d_total, d_err, st));
+    tr.end();
+    TJ_CUDA(launch_add_base(d_base, d_total, st));
+  }
+  stats.radix_passes = maxp;
+  int64_t h_total = 0;
+  int h_err = 0;
+  TJ_CUDA(cudaMemcpyAsync(&h_total, d_base, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  if (h_total <= cap) tr.add_bytes("join", 2.0 * w * (double)h_total);
+  tr.flush();
+  if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
+  *out_count = h_total;
+  stats.learned = router;
+  if (h_total > cap)
+    return set_err(TJ_ERR_CAPACITY, "result has %lld pairs, capacity %lld", (long long)h_total,
+                   (long long)cap);
   return TJ_OK;
 }
 
@@ -464,7 +918,7 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   tr.flush();
   Tracer tr2(st);
   const K lo = key_of<K>(hs.min_u), hi = key_of<K>(~hs.max_u);
-  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), /*even=*/true);
+  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), /*even=*/true, max_digit_bits<K>());
   stats.key_bits = plan.key_bits;
   stats.radix_passes = plan.passes;
   stats.digit_bits = plan.max_bits;
@@ -498,7 +952,7 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   for (int p = 0; p < plan.passes; ++p) {
     TJ_CUDA(cudaMemsetAsync(hj.lookback, 0, (size_t)tiles * bins_max * sizeof(uint32_t), st));
     tr2.begin("onesweep", 4.0 * w * n);
-    TJ_CUDA(launch_onesweep<K>(d_jobs, 1, tiles, p, plan.max_bits, d_counters + p, d_err, st));
+    TJ_CUDA(launch_onesweep<K>(d_jobs, 1, tiles, p, plan.max_bits, false, d_counters + p, d_err, st));
     tr2.end();
   }
   int h_err = 0;
@@ -579,7 +1033,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
     plo[(size_t)j] = lo_bits<K>(lo);
     prange[(size_t)j] = range_of<K>(lo, hi);
     live[(size_t)j] = 1;
-    P = std::max(P, make_plan(plo[(size_t)j], prange[(size_t)j], false).passes);
+    P = std::max(P, make_plan(plo[(size_t)j], prange[(size_t)j], false, max_digit_bits<K>()).passes);
   }
   stats.radix_passes = P;
   // scratch: ping-pong copies of every live pair, histograms, look-back, join state
@@ -590,7 +1044,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   tiles = 0;
   for (int64_t j = 0; j < nj; ++j) {
     Plan pl;
-    if (live[(size_t)j]) pl = make_plan(plo[(size_t)j], prange[(size_t)j], false, P);
+    if (live[(size_t)j]) pl = make_plan(plo[(size_t)j], prange[(size_t)j], false, max_digit_bits<K>(), P);
     plans[(size_t)j] = pl;
     stats.key_bits = std::max(stats.key_bits, pl.key_bits);
     stats.digit_bits = std::max(stats.digit_bits, pl.max_bits);
@@ -678,7 +1132,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
     for (int p = 0; p < P; ++p) {
       step(cudaMemsetAsync(big.at<uint32_t>(o_lb), 0,
                            (size_t)std::max<int64_t>(lb_words, 1) * sizeof(uint32_t), st));
-      step(launch_onesweep<K>(d_jobs, (int)(2 * nj), tiles, p, stats.digit_bits, d_counters + p,
+      step(launch_onesweep<K>(d_jobs, (int)(2 * nj), tiles, p, stats.digit_bits, false, d_counters + p,
                               d_err, st));
     }
   }
@@ -687,8 +1141,8 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   step(cudaMemsetAsync(big.at<uint64_t>(o_jlb), 0,
                        (size_t)std::max<int64_t>(jtiles, 1) * sizeof(uint64_t), st));
   step(launch_join<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra), big.at<int64_t>(o_rb),
-                      big.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, d_out_off,
-                      d_total, d_err, st));
+                      big.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, nullptr,
+                      d_out_off, d_total, d_err, st));
   step(launch_fix_job_out<K>(d_jj, (int)nj, jtiles, d_out_off, d_total, st));
   if (use_graph) {
     cudaError_t e2 = cudaStreamEndCapture(st, &graph);
@@ -729,6 +1183,14 @@ tj_status tj_join_inner(tj_dtype dt, const void* keys_r, const void* ids_r, int6
                         const void* keys_s, const void* ids_s, int64_t n_s,
                         size_t mem_budget_bytes, void* out_pairs, int64_t out_capacity,
                         int64_t* out_count, void* stream) {
+  return tj_join_inner_ex(dt, keys_r, ids_r, n_r, keys_s, ids_s, n_s, mem_budget_bytes, nullptr,
+                          out_pairs, out_capacity, out_count, stream);
+}
+
+tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, int64_t n_r,
+                           const void* keys_s, const void* ids_s, int64_t n_s,
+                           size_t mem_budget_bytes, const tj_join_opts* opts, void* out_pairs,
+                           int64_t out_capacity, int64_t* out_count, void* stream) {
   g_err[0] = 0;
   if (!out_count) return set_err(TJ_ERR_INVALID, "out_count is NULL");
   *out_count = 0;
@@ -739,15 +1201,21 @@ tj_status tj_join_inner(tj_dtype dt, const void* keys_r, const void* ids_r, int6
   if (bad_ptr(keys_r, n_r) || bad_ptr(ids_r, n_r) || bad_ptr(keys_s, n_s) ||
       bad_ptr(ids_s, n_s) || bad_ptr(out_pairs, out_capacity))
     return set_err(TJ_ERR_INVALID, "null pointer with a non-zero size");
+  if (opts && (opts->router < TJ_ROUTE_AUTO || opts->router > TJ_ROUTE_MLP ||
+               opts->partitions < 0 || opts->partitions > kMaxCuts || opts->sample_stride < 0))
+    return set_err(TJ_ERR_INVALID, "bad tj_join_opts");
+  const Opts o = make_opts(opts);
   cudaStream_t st = (cudaStream_t)stream;
   if (dt == TJ_I32)
     return join_impl<int32_t>((const int32_t*)keys_r, (const int32_t*)ids_r, n_r,
                               (const int32_t*)keys_s, (const int32_t*)ids_s, n_s,
-                              mem_budget_bytes, (int32_t*)out_pairs, out_capacity, out_count, st);
+                              mem_budget_bytes, o, (int32_t*)out_pairs, out_capacity, out_count,
+                              st);
   if (dt == TJ_I64)
     return join_impl<int64_t>((const int64_t*)keys_r, (const int64_t*)ids_r, n_r,
                               (const int64_t*)keys_s, (const int64_t*)ids_s, n_s,
-                              mem_budget_bytes, (int64_t*)out_pairs, out_capacity, out_count, st);
+                              mem_budget_bytes, o, (int64_t*)out_pairs, out_capacity, out_count,
+                              st);
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
 }
 
@@ -798,6 +1266,32 @@ tj_status tj_join_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off, const
                                (const int64_t*)ids_s, (int64_t*)out_pairs, out_capacity, out_off,
                                out_count, st);
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+tj_status tj_mlp_grad(const float* theta, const float* x, const float* y, int n, float* grad,
+                      void* stream) {
+  g_err[0] = 0;
+  if (n < 1 || n > 256) return set_err(TJ_ERR_INVALID, "batch must have 1..256 rows");
+  if (!theta || !x || !y || !grad) return set_err(TJ_ERR_INVALID, "null pointer");
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  TJ_CUDA(launch_mlp_grad(theta, x, y, n, grad, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  return TJ_OK;
+}
+
+tj_status tj_mlp_adam(float* theta, float* m, float* v, const float* grad, int n, int t,
+                      float lr, void* stream) {
+  g_err[0] = 0;
+  if (n < 0 || t < 1) return set_err(TJ_ERR_INVALID, "bad size or step");
+  if (n > 0 && (!theta || !m || !v || !grad)) return set_err(TJ_ERR_INVALID, "null pointer");
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0) TJ_CUDA(launch_adam(theta, m, v, grad, n, t, lr, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  return TJ_OK;
 }
 
 const char* tj_status_str(tj_status s) {

@@ -13,11 +13,22 @@
 namespace tj {
 
 // ---- launch geometry -------------------------------------------------------
-constexpr int kThreads = 256;               // threads per CTA (8 warps)
+constexpr int kThreads = 256;               // threads per CTA of most kernels (8 warps)
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;                  // rows per thread in a sort tile
-constexpr int kTile = kThreads * kItems;    // 4096 rows per onesweep tile
-constexpr int kMaxDigitBits = 9;            // widest radix digit
+#ifndef TJ_SORT_THREADS
+#define TJ_SORT_THREADS 512
+#endif
+#ifndef TJ_SORT_MINB
+#define TJ_SORT_MINB 2
+#endif
+#ifndef TJ_SORT_ITEMS
+#define TJ_SORT_ITEMS 8
+#endif
+constexpr int kSortThreads = TJ_SORT_THREADS;  // threads per onesweep CTA
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kItems = TJ_SORT_ITEMS;          // rows per thread in a sort tile
+constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (4096)
+constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass
 constexpr int kJTile = 2048;                // S rows per join tile
@@ -34,6 +45,10 @@ constexpr uint64_t kFlagInc64 = 2ull << 62;
 constexpr uint64_t kValMask64 = (1ull << 62) - 1ull;
 // bounded waits: iterations of a spin before the device reports TJ_ERR_TIMEOUT
 constexpr int kSpinLimit = 1 << 22;
+// key-range partitions of one route pass: cuts <= 1023 -> digits of <= 10 bits
+constexpr int kMaxCuts = 1024;
+// predecessors read per look-back round trip
+constexpr int kLookWindow = 8;
 
 template <typename K> struct UnsignedOf;
 template <> struct UnsignedOf<int32_t> { using type = uint32_t; };
@@ -58,6 +73,10 @@ struct RadixJob {
   const K* src_v[kMaxPasses];
   K* dst_k[kMaxPasses];
   K* dst_v[kMaxPasses];
+  // Route digit (pass 0 only, when cuts != nullptr): the digit of a key is the
+  // number of cut keys <= key, i.e. the index of its key-range partition.
+  const K* cuts;        // sorted cut keys, padded to kMaxCuts with the key type's max
+  int32_t ncuts;        // real cuts (<= kMaxCuts - 1); partitions = ncuts + 1
 };
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).
@@ -92,8 +111,8 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
                               cudaStream_t st);
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                            int pass, int max_bits, uint32_t* d_tile_counter, int* d_err,
-                            cudaStream_t st);
+                            int pass, int max_bits, bool route, uint32_t* d_tile_counter,
+                            int* d_err, cudaStream_t st);
 
 // ---- launchers (tj_join.cu) -------------------------------------------------
 cudaError_t join_init_attributes();
@@ -104,9 +123,33 @@ template <typename K>
 cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                         const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
-                        int64_t* d_job_out, int64_t* d_total, int* d_err, cudaStream_t st);
+                        const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
+                        int* d_err, cudaStream_t st);
+cudaError_t launch_add_base(int64_t* d_base, int64_t* d_total, cudaStream_t st);
+
+// ---- launchers (tj_learned.cu) ----------------------------------------------
+template <typename K>
+cudaError_t launch_sample_gather(const K* a, int64_t ma, int64_t off_a, const K* b, int64_t mb,
+                                 int64_t off_b, int stride, K* out_k, K* out_v, cudaStream_t st);
+template <typename K>
+cudaError_t launch_quantiles(const K* sorted, int64_t m, int G, int first, int last, int step,
+                             K* out, cudaStream_t st);
 template <typename K>
 cudaError_t launch_fix_job_out(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                                int64_t* d_job_out, const int64_t* d_total, cudaStream_t st);
+
+// ---- launchers (tj_mlp.cu) ---------------------------------------------------
+constexpr int kMlpParams = 1153;
+cudaError_t mlp_init_attributes();
+template <typename K>
+cudaError_t launch_mlp_train(const K* sorted, int64_t m, float* theta, int steps, float lr,
+                             uint64_t seed, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* theta, const float* x, const float* y, int n,
+                            float* grad, cudaStream_t st);
+cudaError_t launch_adam(float* theta, float* m, float* v, const float* g, int n, int t, float lr,
+                        cudaStream_t st);
+template <typename K>
+cudaError_t launch_mlp_boundaries(const float* theta, int T, float* table, int parts,
+                                  const K* sorted, int64_t m, K* out, cudaStream_t st);
 
 }  // namespace tj

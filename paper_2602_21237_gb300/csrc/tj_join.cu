@@ -101,26 +101,24 @@ __global__ void k_tile_ranges(const JoinJob<K>* __restrict__ jobs, int num_jobs,
 // ---------------------------------------------------------------------------
 template <typename K>
 constexpr size_t join_smem_bytes() {
-  return sizeof(K) * kJTile * 2          // S keys, S ids
-         + sizeof(K) * kRCap * 2         // R keys, R ids
-         + sizeof(uint32_t) * kHTSlots   // hash table: packed (first, end)
-         + sizeof(uint64_t) * kJTile     // per-row counts -> exclusive offsets
-         + sizeof(uint32_t) * kJTile;    // per-row run start (relative to a)
+  return sizeof(K) * kJTile             // S keys of the tile
+         + sizeof(K) * kRCap            // R keys of the tile's R range
+         + sizeof(uint32_t) * kHTSlots  // hash table: packed (first, end) of a run
+         + sizeof(uint64_t) * kJTile    // per-row counts -> exclusive offsets
+         + sizeof(uint32_t) * kJTile;   // per-row run start (relative to a)
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     k_join(const JoinJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles,
            const int64_t* __restrict__ ra, const int64_t* __restrict__ rb,
            uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter,
-           K* __restrict__ out, int64_t capacity, int64_t* __restrict__ job_out,
-           int64_t* __restrict__ total, int* __restrict__ err) {
+           K* __restrict__ out, int64_t capacity, const int64_t* __restrict__ out_base,
+           int64_t* __restrict__ job_out, int64_t* __restrict__ total, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
   K* s_sk = reinterpret_cast<K*>(smem);
-  K* s_sv = s_sk + kJTile;
-  K* s_rk = s_sv + kJTile;
-  K* s_rv = s_rk + kRCap;
-  uint32_t* s_ht = reinterpret_cast<uint32_t*>(s_rv + kRCap);
+  K* s_rk = s_sk + kJTile;
+  uint32_t* s_ht = reinterpret_cast<uint32_t*>(s_rk + kRCap);
   uint64_t* s_off = reinterpret_cast<uint64_t*>(s_ht + kHTSlots);
   uint32_t* s_rs = reinterpret_cast<uint32_t*>(s_off + kJTile);
   __shared__ uint64_t s_wsum[kWarps];
@@ -137,25 +135,29 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int64_t t = s_t;
   if (t >= total_tiles) return;
   const int j = find_job_j(jobs, num_jobs, t);
-  const JoinJob<K>* J = jobs + j;
-  const int64_t lt = t - J->tile0;
-  const int64_t row0 = lt * kJTile;
-  const int nv = (int)min((int64_t)kJTile, J->ns - row0);
+  const JoinJob<K> J = jobs[j];
   const int64_t a = ra[t];
   const int64_t nrr = rb[t] - a;
+  const int64_t lt = t - J.tile0;
+  const int64_t row0 = lt * kJTile;
+  const int nv = (int)min((int64_t)kJTile, J.ns - row0);
   const bool small = nrr <= kRCap;
-  const K* __restrict__ rk_g = J->rk + a;
-  const K* __restrict__ rv_g = J->rv + a;
+  const K* __restrict__ sk_g = J.sk + row0;
+  const K* __restrict__ sv_g = J.sv + row0;
+  const K* __restrict__ rk_g = J.rk + a;
+  const K* __restrict__ rv_g = J.rv + a;
 
-  for (int q = tid; q < nv; q += kThreads) {
-    s_sk[q] = J->sk[row0 + q];
-    s_sv[q] = J->sv[row0 + q];
+  // S ids of this thread's rows, loaded now and used only when writing
+  constexpr int kRows = kJTile / kThreads;
+  K sid[kRows];
+#pragma unroll
+  for (int u = 0; u < kRows; ++u) {
+    const int q = tid + u * kThreads;
+    sid[u] = q < nv ? sv_g[q] : K(0);
   }
+  for (int q = tid; q < nv; q += kThreads) s_sk[q] = sk_g[q];
   if (small) {
-    for (int i = tid; i < (int)nrr; i += kThreads) {
-      s_rk[i] = rk_g[i];
-      s_rv[i] = rv_g[i];
-    }
+    for (int i = tid; i < (int)nrr; i += kThreads) s_rk[i] = rk_g[i];
     for (int i = tid; i < kHTSlots; i += kThreads) s_ht[i] = kHTEmpty;
   }
   __syncthreads();
@@ -189,9 +191,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
   }
 
-  // probe: match count and run start of every S row of the tile
+  // probe: match count and run start of every S row of the tile; the R id of
+  // the first match is gathered right away (used when writing)
   int mymax = 0;
-  for (int q = tid; q < nv; q += kThreads) {
+  K rid[kRows];
+#pragma unroll
+  for (int u = 0; u < kRows; ++u) {
+    const int q = tid + u * kThreads;
+    rid[u] = K(0);
+    if (q >= nv) continue;
     const K key = s_sk[q];
     uint32_t cnt = 0, start = 0;
     if (small) {
@@ -215,6 +223,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     s_off[q] = cnt;
     s_rs[q] = start;
+    if (cnt) rid[u] = rv_g[start];
     mymax = max(mymax, (int)cnt);
   }
   if (mymax > 1) atomicMax(&s_maxcnt, mymax);
@@ -265,25 +274,40 @@ __global__ void __launch_bounds__(kThreads, 2)
       st_volatile_u64(mine, kFlagInc64 | (C & kValMask64));
     } else {
       st_volatile_u64(mine, kFlagAgg64 | (C & kValMask64));
-      const uint64_t* p = mine - 1;
-      int64_t k = t - 1;
+      int64_t k = t - 1;  // newest predecessor not yet summed
       int spins = 0;
-      while (true) {
-        const uint64_t w = ld_volatile_u64(p);
-        const uint64_t f = w & ~kValMask64;
-        if (f == 0ull) {
+      bool done = false;
+      while (!done) {
+        uint64_t v[kLookWindow];
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w)
+          v[w] = (k - w >= 0) ? ld_volatile_u64(lookback + (k - w)) : kFlagInc64;
+        int used = 0;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w) {
+          if (used != w) break;
+          const uint64_t f = v[w] & ~kValMask64;
+          if (f == 0ull) break;
+          acc += v[w] & kValMask64;
+          ++used;
+          if (f == kFlagInc64) {
+            done = true;
+            break;
+          }
+        }
+        prefix += acc;
+        k -= used;
+        if (done || k < 0) break;
+        if (used == 0) {
           if (++spins > kSpinLimit) {
             atomicExch(err, (int)TJ_ERR_TIMEOUT);
             break;
           }
-          __nanosleep(64);
-          continue;
+          __nanosleep(32);
+        } else {
+          spins = 0;
         }
-        prefix += w & kValMask64;
-        if (f == kFlagInc64 || k == 0) break;
-        --k;
-        --p;
-        spins = 0;
       }
       st_volatile_u64(mine, kFlagInc64 | ((prefix + C) & kValMask64));
     }
@@ -292,19 +316,23 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (t == total_tiles - 1) *total = (int64_t)(prefix + C);
   }
   __syncthreads();
-  const uint64_t E = s_base;
+  // output index of this tile's first pair: the group's base (the partitioned
+  // join writes several groups one after another) plus the chained prefix
+  const uint64_t E = s_base + (out_base ? (uint64_t)*out_base : 0ull);
   if (E + C > (uint64_t)capacity) return;  // the host reports TJ_ERR_CAPACITY
 
   K* __restrict__ o = out + 2 * E;
   if (s_maxcnt <= 1) {
     // at most one match per S row (e.g. a foreign-key join): row-wise writes
-    for (int q = tid; q < nv; q += kThreads) {
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int q = tid + u * kThreads;
+      if (q >= nv) break;
       const uint64_t off = s_off[q];
       const bool hit = (q + 1 < nv ? s_off[q + 1] : C) > off;
       if (hit) {
-        const uint32_t r = s_rs[q];
-        o[2 * off] = small ? s_rv[r] : rv_g[r];
-        o[2 * off + 1] = s_sv[q];
+        o[2 * off] = rid[u];
+        o[2 * off + 1] = sid[u];
       }
     }
   } else {
@@ -319,8 +347,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           hi = mid - 1;
       }
       const uint64_t r = s_rs[lo] + (x - s_off[lo]);
-      o[2 * x] = small ? s_rv[r] : rv_g[r];
-      o[2 * x + 1] = s_sv[lo];
+      o[2 * x] = rv_g[r];
+      o[2 * x + 1] = sv_g[lo];
     }
   }
 }
@@ -338,13 +366,25 @@ cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t t
 template <typename K>
 cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                         const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
-                        uint32_t* d_tile_counter, K* out, int64_t capacity, int64_t* d_job_out,
-                        int64_t* d_total, int* d_err, cudaStream_t st) {
+                        uint32_t* d_tile_counter, K* out, int64_t capacity,
+                        const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
+                        int* d_err, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
   const size_t smem = join_smem_bytes<K>();
-  k_join<K><<<(unsigned)total_tiles, kThreads, smem, st>>>(d_jobs, num_jobs, total_tiles, d_ra,
-                                                           d_rb, d_lookback, d_tile_counter, out,
-                                                           capacity, d_job_out, d_total, d_err);
+  k_join<K><<<(unsigned)total_tiles, kThreads, smem, st>>>(
+      d_jobs, num_jobs, total_tiles, d_ra, d_rb, d_lookback, d_tile_counter, out, capacity,
+      d_out_base, d_job_out, d_total, d_err);
+  return cudaGetLastError();
+}
+
+// base += group total (stream-ordered between the groups of a partitioned join)
+__global__ void k_add_base(int64_t* base, int64_t* total) {
+  *base += *total;
+  *total = 0;
+}
+
+cudaError_t launch_add_base(int64_t* d_base, int64_t* d_total, cudaStream_t st) {
+  k_add_base<<<1, 1, 0, st>>>(d_base, d_total);
   return cudaGetLastError();
 }
 
@@ -392,7 +432,7 @@ cudaError_t join_init_attributes() {
                                              cudaStream_t);                                     \
   template cudaError_t launch_join<K>(const JoinJob<K>*, int, int64_t, const int64_t*,           \
                                       const int64_t*, uint64_t*, uint32_t*, K*, int64_t,          \
-                                      int64_t*, int64_t*, int*, cudaStream_t);                    \
+                                      const int64_t*, int64_t*, int64_t*, int*, cudaStream_t);    \
   template cudaError_t launch_fix_job_out<K>(const JoinJob<K>*, int, int64_t, int64_t*,          \
                                              const int64_t*, cudaStream_t);
 TJ_INSTANTIATE_JOIN(int32_t)

@@ -1,0 +1,68 @@
+// Learned key-range partitioner (no counterpart in the paper; it chooses the
+// key-range batches of the partitioned join, the device analogue of the
+// relational path's work_mem batches of Sec. 6).
+//
+//   k_sample_gather : every `stride`-th row of R and of S from seeded offsets,
+//                     pooled (a 1% sample for stride 100).
+//   k_quantiles     : knots / boundaries at sample quantiles of the sorted
+//                     sample, q_i = s[floor(i (m - 1) / G)] (the piecewise-
+//                     linear CDF model; its partition boundaries for P | G are
+//                     the knots t_{(G/P) p}).
+//   MLP kernels     : see tj_mlp.cu.
+#include "tj_internal.cuh"
+
+namespace tj {
+
+template <typename K>
+__global__ void k_sample_gather(const K* __restrict__ a, int64_t ma, int64_t off_a,
+                                const K* __restrict__ b, int64_t mb, int64_t off_b, int stride,
+                                K* __restrict__ out_k, K* __restrict__ out_v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ma) {
+    out_k[i] = a[off_a + i * stride];
+    out_v[i] = (K)i;
+  } else if (i < ma + mb) {
+    out_k[i] = b[off_b + (i - ma) * stride];
+    out_v[i] = (K)i;
+  }
+}
+
+// out[i] = sorted[floor(i * (m - 1) / G) ] for i in [first, last]
+template <typename K>
+__global__ void k_quantiles(const K* __restrict__ sorted, int64_t m, int G, int first, int last,
+                            int step, K* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = first + i * step;
+  if (q > last) return;
+  const int64_t idx = ((int64_t)q * (m - 1)) / G;
+  out[i] = sorted[idx];
+}
+
+template <typename K>
+cudaError_t launch_sample_gather(const K* a, int64_t ma, int64_t off_a, const K* b, int64_t mb,
+                                 int64_t off_b, int stride, K* out_k, K* out_v, cudaStream_t st) {
+  const int64_t n = ma + mb;
+  if (n <= 0) return cudaSuccess;
+  k_sample_gather<K><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+      a, ma, off_a, b, mb, off_b, stride, out_k, out_v);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_quantiles(const K* sorted, int64_t m, int G, int first, int last, int step,
+                             K* out, cudaStream_t st) {
+  const int n = (last - first) / step + 1;
+  if (n <= 0) return cudaSuccess;
+  k_quantiles<K><<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(sorted, m, G, first, last,
+                                                                      step, out);
+  return cudaGetLastError();
+}
+
+#define TJ_INSTANTIATE_LEARNED(K)                                                                \
+  template cudaError_t launch_sample_gather<K>(const K*, int64_t, int64_t, const K*, int64_t,    \
+                                               int64_t, int, K*, K*, cudaStream_t);              \
+  template cudaError_t launch_quantiles<K>(const K*, int64_t, int, int, int, int, K*, cudaStream_t);
+TJ_INSTANTIATE_LEARNED(int32_t)
+TJ_INSTANTIATE_LEARNED(int64_t)
+
+}  // namespace tj

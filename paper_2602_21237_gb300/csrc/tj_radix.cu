@@ -64,6 +64,18 @@ __device__ __forceinline__ uint32_t digit_of(K key, typename UnsignedOf<K>::type
   return (uint32_t)((((U)key) - lo) >> shift) & mask;
 }
 
+// Number of cut keys <= key in a sorted table padded to kMaxCuts entries with
+// the key type's maximum (branch-free binary search; pads only count for the
+// maximum key and are clipped by ncuts).
+template <typename K>
+__device__ __forceinline__ uint32_t route_of(K key, const K* s_cuts, int ncuts) {
+  int pos = 0;
+#pragma unroll
+  for (int step = kMaxCuts / 2; step >= 1; step >>= 1)
+    if (s_cuts[pos + step - 1] <= key) pos += step;
+  return (uint32_t)min(pos, ncuts);
+}
+
 // Exclusive scan of in[0, bins) into out[0, bins) by the whole CTA
 // (bins <= 2 * kThreads).  Ends with a barrier.
 __device__ __forceinline__ void block_excl_scan_bins(const uint32_t* in, uint32_t* out, int bins,
@@ -138,8 +150,6 @@ __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restric
 // ---------------------------------------------------------------------------
 // K2: digit histograms of every pass in one read of the keys
 // ---------------------------------------------------------------------------
-constexpr int kHistTilesPerCta = 4;
-
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __restrict__ jobs,
                                                         int num_jobs, int64_t total_tiles) {
@@ -147,50 +157,65 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __res
   __shared__ uint32_t s_h[kMaxPasses * kMaxBins];
   __shared__ int s_shift[kMaxPasses];
   __shared__ uint32_t s_mask[kMaxPasses];
-  const int64_t t_begin = (int64_t)blockIdx.x * kHistTilesPerCta;
-  const int64_t t_end = min(total_tiles, t_begin + kHistTilesPerCta);
-  int cur = -1, passes = 0;
+  __shared__ K s_cuts[kMaxCuts];
+  int cur = -1, passes = 0, ncuts = -1;
   U lo = 0;
-  for (int64_t t = t_begin; t < t_end; ++t) {
+  auto flush = [&](int job) {
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+      for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) {
+        const uint32_t c = s_h[p * kMaxBins + d];
+        if (c) atomicAdd(&jobs[job].hist[p * jobs[job].hist_stride + d], c);
+      }
+  };
+  // grid-stride over tiles: one flush per job a CTA touched
+  for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
     const int j = find_job(jobs, num_jobs, t);
     if (j != cur) {
-      if (cur >= 0) {
-        __syncthreads();
-        for (int p = 0; p < passes; ++p)
-          for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) {
-            const uint32_t c = s_h[p * kMaxBins + d];
-            if (c) atomicAdd(&jobs[cur].hist[p * jobs[cur].hist_stride + d], c);
-          }
-      }
+      if (cur >= 0) flush(cur);
       __syncthreads();
       cur = j;
       passes = jobs[j].passes;
       lo = (U)jobs[j].lo;
+      ncuts = jobs[j].cuts ? jobs[j].ncuts : -1;
+      if (ncuts >= 0)
+        for (int i = threadIdx.x; i < kMaxCuts; i += kThreads) s_cuts[i] = jobs[j].cuts[i];
       if (threadIdx.x < kMaxPasses) {
         s_shift[threadIdx.x] = jobs[j].shift[threadIdx.x];
         s_mask[threadIdx.x] =
             threadIdx.x < passes ? (1u << jobs[j].bits[threadIdx.x]) - 1u : 0u;
       }
-      for (int i = threadIdx.x; i < kMaxPasses * kMaxBins; i += kThreads) s_h[i] = 0;
+      __syncthreads();
+      for (int p = 0; p < passes; ++p)
+        for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) s_h[p * kMaxBins + d] = 0;
       __syncthreads();
     }
     const K* __restrict__ keys = jobs[j].keys;
     const int64_t row0 = (t - jobs[j].tile0) * kTile;
-    const int64_t row1 = min(jobs[j].n, row0 + kTile);
-    for (int64_t r = row0 + threadIdx.x; r < row1; r += kThreads) {
-      const U u = (U)keys[r] - lo;
-      for (int p = 0; p < passes; ++p)
-        atomicAdd(&s_h[p * kMaxBins + ((uint32_t)(u >> s_shift[p]) & s_mask[p])], 1u);
+    const int row1 = (int)min((int64_t)kTile, jobs[j].n - row0);
+    const K* __restrict__ kp = keys + row0;
+    constexpr int kU = kTile / kThreads;  // 16 rows per thread, loads issued together
+    K kv[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int r = threadIdx.x + u * kThreads;
+      kv[u] = r < row1 ? kp[r] : K(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int r = threadIdx.x + u * kThreads;
+      if (r < row1) {
+        if (ncuts >= 0) {
+          atomicAdd(&s_h[route_of<K>(kv[u], s_cuts, ncuts)], 1u);
+        } else {
+          const U x = (U)kv[u] - lo;
+          for (int p = 0; p < passes; ++p)
+            atomicAdd(&s_h[p * kMaxBins + ((uint32_t)(x >> s_shift[p]) & s_mask[p])], 1u);
+        }
+      }
     }
   }
-  if (cur >= 0) {
-    __syncthreads();
-    for (int p = 0; p < passes; ++p)
-      for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) {
-        const uint32_t c = s_h[p * kMaxBins + d];
-        if (c) atomicAdd(&jobs[cur].hist[p * jobs[cur].hist_stride + d], c);
-      }
-  }
+  if (cur >= 0) flush(cur);
 }
 
 // ---------------------------------------------------------------------------
@@ -222,27 +247,49 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 // ---------------------------------------------------------------------------
 // K4: one onesweep digit pass
 // ---------------------------------------------------------------------------
+// Shared memory (bins = 2^bits of this pass, set at launch):
+//   keys[kTile] K | ids[kTile] K | warp counters[kSortWarps][bins] u32 |
+//   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
+//   [cut keys[kMaxCuts] K, when the pass routes by a cut table]
 template <typename K>
-constexpr size_t onesweep_smem_bytes() {
-  return 2 * sizeof(K) * kTile                 // staged keys, staged ids
-         + sizeof(uint32_t) * kWarps * kMaxBins  // per-warp digit counters
-         + sizeof(uint32_t) * kMaxBins * 2       // tile counts, tile exclusive
-         + sizeof(long long) * kMaxBins;         // global base per digit
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route) {
+  return 2 * sizeof(K) * kTile + sizeof(uint32_t) * (size_t)(kSortWarps + 2) * bins +
+         sizeof(long long) * (size_t)bins + (route ? sizeof(K) * kMaxCuts : 0);
+}
+
+// Exclusive scan of in[0, bins) by a CTA of kSortThreads (bins <= 2 * kSortThreads).
+__device__ __forceinline__ void sort_block_excl_scan(const uint32_t* in, uint32_t* out, int bins,
+                                                     uint32_t* s_warp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int d0 = tid * 2;
+  const uint32_t a = d0 < bins ? in[d0] : 0u;
+  const uint32_t b = d0 + 1 < bins ? in[d0 + 1] : 0u;
+  const uint32_t s = a + b;
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w)
+    if (w < warp) wpre += s_warp[w];
+  const uint32_t excl = wpre + x - s;
+  if (d0 < bins) out[d0] = excl;
+  if (d0 + 1 < bins) out[d0 + 1] = excl + a;
+  __syncthreads();
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     k_onesweep(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles, int pass,
                uint32_t* __restrict__ tile_counter, int* __restrict__ err) {
   using U = typename UnsignedOf<K>::type;
   extern __shared__ __align__(16) unsigned char smem[];
-  K* s_keys = reinterpret_cast<K*>(smem);
-  K* s_vals = s_keys + kTile;
-  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + kTile);
-  uint32_t* s_count = s_whist + kWarps * kMaxBins;
-  uint32_t* s_excl = s_count + kMaxBins;
-  long long* s_gbase = reinterpret_cast<long long*>(s_excl + kMaxBins);
-  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_warp[kSortWarps];
   __shared__ uint32_t s_t;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -252,6 +299,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (t >= total_tiles) return;
   const int j = find_job(jobs, num_jobs, t);
   const RadixJob<K>* J = jobs + j;
+  if (pass >= J->passes) return;  // this array needs fewer passes than the batch
   const int64_t lt = t - J->tile0;
   const int64_t row0 = lt * kTile;
   const int nvalid = (int)min((int64_t)kTile, J->n - row0);
@@ -267,14 +315,26 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint32_t* lb_mine = lb_base + lt * bins;
   const uint32_t* hist = J->hist + pass * J->hist_stride;
 
-  for (int i = tid; i < kWarps * bins; i += kThreads) s_whist[i] = 0u;
+  K* s_keys = reinterpret_cast<K*>(smem);
+  K* s_vals = s_keys + kTile;
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + kTile);
+  uint32_t* s_count = s_whist + kSortWarps * bins;
+  uint32_t* s_excl = s_count + bins;
+  long long* s_gbase = reinterpret_cast<long long*>(s_excl + bins);
+  K* s_cuts = reinterpret_cast<K*>(s_gbase + bins);
+  const int ncuts = J->cuts ? J->ncuts : -1;
+  if (ncuts >= 0)
+    for (int i = tid; i < kMaxCuts; i += kSortThreads) s_cuts[i] = J->cuts[i];
+  // the digit of a row in this pass: a radix digit of key - lo, or its route
+  auto dig = [&](K k) -> uint32_t {
+    return ncuts >= 0 ? route_of<K>(k, s_cuts, ncuts) : digit_of<K>(k, lo, shift, mask);
+  };
 
   // Warp-striped rows: warp w owns rows [w*32*kItems, (w+1)*32*kItems) of the
-  // tile; iteration i covers 32 consecutive rows, so ranks follow row order.
+  // tile; item i covers 32 consecutive rows, so ranks follow row order.
   const int wbase = warp * 32 * kItems;
   K key[kItems];
   K val[kItems];
-  uint32_t rk[kItems];
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const int r = wbase + i * 32 + lane;
@@ -285,29 +345,43 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int r = wbase + i * 32 + lane;
     val[i] = r < nvalid ? src_v[r] : K(0);
   }
+  for (int i = tid; i < kSortWarps * bins; i += kSortThreads) s_whist[i] = 0u;
   __syncthreads();
 
-  uint32_t* wh = s_whist + warp * bins;
-  const uint32_t ltm = lanemask_lt();
+  // 1. peer groups of equal digits for every item (independent -> pipelined)
+  uint32_t peers[kItems];
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const int r = wbase + i * 32 + lane;
-    const bool valid = r < nvalid;
-    const uint32_t d = valid ? digit_of<K>(key[i], lo, shift, mask) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-    const uint32_t base = valid ? wh[d] : 0u;
-    __syncwarp();
-    if (valid && (peers >> lane) == 1u) wh[d] = base + __popc(peers);
-    __syncwarp();
-    rk[i] = base + __popc(peers & ltm);
+    const uint32_t d = r < nvalid ? dig(key[i]) : 0xFFFFFFFFu;
+    peers[i] = __match_any_sync(0xFFFFFFFFu, d);
+  }
+  // 2. one shared-memory atomicAdd per group, issued by the group's highest
+  //    lane; it returns the warp's running count of that digit (items in order)
+  uint32_t* wh = s_whist + warp * bins;
+  uint32_t rk[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int r = wbase + i * 32 + lane;
+    rk[i] = 0u;
+    if (r < nvalid && (peers[i] >> lane) == 1u)
+      rk[i] = atomicAdd(&wh[dig(key[i])], (uint32_t)__popc(peers[i]));
+  }
+  // 3. broadcast the group's base and add the rank inside the group
+  const uint32_t ltm = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int leader = 31 - __clz(peers[i]);
+    const uint32_t base = __shfl_sync(0xFFFFFFFFu, rk[i], leader);
+    rk[i] = base + __popc(peers[i] & ltm);
   }
   __syncthreads();
 
   // per digit: exclusive prefix over warps and the tile's count; publish it
-  for (int d = tid; d < bins; d += kThreads) {
+  for (int d = tid; d < bins; d += kSortThreads) {
     uint32_t run = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < kSortWarps; ++w) {
       const uint32_t c = s_whist[w * bins + d];
       s_whist[w * bins + d] = run;
       run += c;
@@ -316,32 +390,77 @@ __global__ void __launch_bounds__(kThreads, 2)
     st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | run);
   }
   __syncthreads();
-  block_excl_scan_bins(s_count, s_excl, bins, s_warp);
+  sort_block_excl_scan(s_count, s_excl, bins, s_warp);
 
-  // decoupled look-back: sum predecessors' counts of this digit until an
-  // inclusive prefix is found.  Bounded wait; on timeout report and go on.
-  for (int d = tid; d < bins; d += kThreads) {
+  // Look-back and placement overlap: each digit thread first issues the loads
+  // of its first look-back window, then every thread places its rows at their
+  // tile-sorted position in shared memory, then the digit threads finish the
+  // decoupled look-back (summing predecessors' counts of their digit until an
+  // inclusive prefix, kLookWindow words per round trip; bounded wait, on
+  // timeout report and go on).
+  constexpr int kDPer = (kMaxBins + kSortThreads - 1) / kSortThreads;
+  uint32_t win[kLookWindow];  // first window of this thread's first digit
+#pragma unroll
+  for (int w = 0; w < kLookWindow; ++w)
+    win[w] = (tid < bins && lt - 1 - w >= 0) ? ld_volatile_u32(lb_base + (lt - 1 - w) * bins + tid)
+                                             : 0u;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const int r = wbase + i * 32 + lane;
+    if (r < nvalid) {
+      const uint32_t d = dig(key[i]);
+      const uint32_t pos = s_excl[d] + s_whist[warp * bins + d] + rk[i];
+      s_keys[pos] = key[i];
+      s_vals[pos] = val[i];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < kDPer; ++e) {
+    const int d = tid + e * kSortThreads;
+    if (d >= bins) break;
     uint32_t prefix = 0;
     if (lt > 0) {
-      const uint32_t* p = lb_mine - bins + d;
-      int64_t k = lt - 1;
+      int64_t k = lt - 1;  // newest predecessor not yet summed
       int spins = 0;
-      while (true) {
-        const uint32_t v = ld_volatile_u32(p);
-        const uint32_t f = v & ~kValMask;
-        if (f == 0u) {
+      bool done = false;
+      bool first = (e == 0);
+      while (!done) {
+        uint32_t v[kLookWindow];
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w)
+          v[w] = first ? win[w]
+                       : ((k - w >= 0) ? ld_volatile_u32(lb_base + (k - w) * bins + d) : kFlagInc);
+        if (first)
+#pragma unroll
+          for (int w = 0; w < kLookWindow; ++w)
+            if (k - w < 0) v[w] = kFlagInc;
+        first = false;
+        int used = 0;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w) {
+          if (used != w) break;
+          const uint32_t f = v[w] & ~kValMask;
+          if (f == 0u) break;
+          acc += v[w] & kValMask;
+          ++used;
+          if (f == kFlagInc) {
+            done = true;
+            break;
+          }
+        }
+        prefix += acc;
+        k -= used;
+        if (done || k < 0) break;
+        if (used == 0) {
           if (++spins > kSpinLimit) {
             atomicExch(err, (int)TJ_ERR_TIMEOUT);
             break;
           }
-          __nanosleep(64);
-          continue;
+          __nanosleep(32);
+        } else {
+          spins = 0;
         }
-        prefix += v & kValMask;
-        if (f == kFlagInc || k == 0) break;
-        --k;
-        p -= bins;
-        spins = 0;
       }
       st_volatile_u32(lb_mine + d, kFlagInc | ((prefix + s_count[d]) & kValMask));
     }
@@ -349,23 +468,11 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   __syncthreads();
 
-  // place rows at their tile-sorted position in shared memory
-#pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    const int r = wbase + i * 32 + lane;
-    if (r < nvalid) {
-      const uint32_t d = digit_of<K>(key[i], lo, shift, mask);
-      const uint32_t pos = s_excl[d] + s_whist[warp * bins + d] + rk[i];
-      s_keys[pos] = key[i];
-      s_vals[pos] = val[i];
-    }
-  }
-  __syncthreads();
-
   // scatter: consecutive staged rows of one digit go to consecutive addresses
-  for (int q = tid; q < nvalid; q += kThreads) {
+#pragma unroll 4
+  for (int q = tid; q < nvalid; q += kSortThreads) {
     const K k = s_keys[q];
-    const uint32_t d = digit_of<K>(k, lo, shift, mask);
+    const uint32_t d = dig(k);
     const long long g = s_gbase[d] + q;
     dst_k[g] = k;
     dst_v[g] = s_vals[q];
@@ -388,7 +495,7 @@ template <typename K>
 cudaError_t launch_histogram(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                              cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
-  const int64_t grid = (total_tiles + kHistTilesPerCta - 1) / kHistTilesPerCta;
+  const int64_t grid = total_tiles < 152 * 6 ? total_tiles : 152 * 6;
   k_histogram<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles);
   return cudaGetLastError();
 }
@@ -405,23 +512,22 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
 
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                            int pass, int max_bits, uint32_t* d_tile_counter, int* d_err,
-                            cudaStream_t st) {
-  (void)max_bits;
+                            int pass, int max_bits, bool route, uint32_t* d_tile_counter,
+                            int* d_err, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
-  const size_t smem = onesweep_smem_bytes<K>();
-  k_onesweep<K><<<(unsigned)total_tiles, kThreads, smem, st>>>(d_jobs, num_jobs, total_tiles, pass,
-                                                               d_tile_counter, d_err);
+  const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route);
+  k_onesweep<K><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(d_jobs, num_jobs, total_tiles,
+                                                                   pass, d_tile_counter, d_err);
   return cudaGetLastError();
 }
 
 cudaError_t radix_init_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_onesweep<int32_t>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)onesweep_smem_bytes<int32_t>());
+                                       (int)onesweep_smem_bytes<int32_t>(kMaxBins, true));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_onesweep<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)onesweep_smem_bytes<int64_t>());
+                              (int)onesweep_smem_bytes<int64_t>(kMaxBins, true));
 }
 
 #define TJ_INSTANTIATE_RADIX(K)                                                                 \
@@ -429,8 +535,8 @@ cudaError_t radix_init_attributes() {
                                        cudaStream_t);                                           \
   template cudaError_t launch_histogram<K>(const RadixJob<K>*, int, int64_t, cudaStream_t);     \
   template cudaError_t launch_digit_scan<K>(const RadixJob<K>*, int, int, cudaStream_t);        \
-  template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, uint32_t*, \
-                                          int*, cudaStream_t);
+  template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, bool,    \
+                                          uint32_t*, int*, cudaStream_t);
 TJ_INSTANTIATE_RADIX(int32_t)
 TJ_INSTANTIATE_RADIX(int64_t)
 

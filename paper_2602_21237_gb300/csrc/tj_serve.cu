@@ -1,0 +1,244 @@
+// Serving loop (no counterpart in the paper, whose P99 framing of Sec. 5.2 /
+// Sec. 6 it measures): continuous batching of join and sort requests under a
+// device-memory budget.
+//
+// Requests wait in one FIFO queue.  A request is admitted as soon as a worker
+// is free and its footprint (the library scratch its call may hold plus its
+// output buffer) fits in what the budget has left; it then runs on its
+// worker's own CUDA stream, so admitted requests overlap on the device.  When
+// it completes, its reservation is released and the next queued request is
+// admitted immediately -- requests that arrive while others run join the mix
+// as slots and memory free up.  Latency = completion - arrival.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tj_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Pending {
+  int64_t ticket;
+  tj_request req;
+  size_t footprint;
+  Clock::time_point arrival;
+};
+
+}  // namespace
+
+struct tj_server {
+  size_t budget = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;  // queue / completion changes
+  std::deque<Pending> queue;
+  std::unordered_map<int64_t, tj_result> done;
+  std::vector<double> lat_ms;
+  size_t reserved = 0;
+  size_t peak_reserved = 0;
+  int inflight = 0;
+  int peak_inflight = 0;
+  int64_t next = 0;
+  int64_t tuples = 0;
+  bool stop = false;
+  Clock::time_point first_arrival{}, last_done{};
+  bool any = false;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+size_t rows_bytes(tj_dtype dt) { return dt == TJ_I32 ? 4 : 8; }
+
+// What the library may hold for the call (single-pass sort buffers, look-back,
+// join state) plus the output buffer the request pins.
+size_t footprint_of(const tj_request& r) {
+  const size_t w = rows_bytes((tj_dtype)r.dt);
+  if (r.op == TJ_OP_SORT) return (size_t)r.n_r * (2 * w + 2) + (2u << 20);
+  const size_t rows = (size_t)(r.n_r + r.n_s);
+  return rows * (4 * w + 2) + (size_t)r.out_capacity * 2 * w + (2u << 20);
+}
+
+void worker_main(tj_server* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st = nullptr;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  while (true) {
+    Pending p;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] {
+        return S->stop ||
+               (!S->queue.empty() && S->reserved + S->queue.front().footprint <= S->budget);
+      });
+      if (S->stop && S->queue.empty()) break;
+      if (S->queue.empty() || S->reserved + S->queue.front().footprint > S->budget) continue;
+      p = S->queue.front();
+      S->queue.pop_front();
+      S->reserved += p.footprint;
+      S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+      S->inflight += 1;
+      S->peak_inflight = std::max(S->peak_inflight, S->inflight);
+    }
+    tj_result res = {};
+    const tj_request& r = p.req;
+    const size_t w = rows_bytes((tj_dtype)r.dt);
+    if (r.op == TJ_OP_SORT) {
+      res.status = tj_sort((tj_dtype)r.dt, r.keys_r, r.ids_r, r.n_r, st);
+    } else {
+      // the call's working set stays inside the reservation minus its output
+      const size_t lib = p.footprint - (size_t)r.out_capacity * 2 * w;
+      res.status = tj_join_inner((tj_dtype)r.dt, r.keys_r, r.ids_r, r.n_r, r.keys_s, r.ids_s,
+                                 r.n_s, lib, r.out_pairs, r.out_capacity, &res.out_count, st);
+    }
+    const Clock::time_point t1 = Clock::now();
+    res.latency_ms = std::chrono::duration<double, std::milli>(t1 - p.arrival).count();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->reserved -= p.footprint;
+      S->inflight -= 1;
+      S->done[p.ticket] = res;
+      S->lat_ms.push_back(res.latency_ms);
+      S->tuples += r.op == TJ_OP_SORT ? r.n_r : r.n_r + r.n_s;
+      if (t1 > S->last_done) S->last_done = t1;
+    }
+    S->cv.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+double pct(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t i = (size_t)pos;
+  const double f = pos - (double)i;
+  return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+tj_status tj_server_create(size_t mem_budget_bytes, int workers, tj_server** out) {
+  if (!out || workers < 1 || workers > 64 || mem_budget_bytes == 0) return TJ_ERR_INVALID;
+  tj_server* S = new tj_server();
+  S->budget = mem_budget_bytes;
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    delete S;
+    return TJ_ERR_CUDA;
+  }
+  for (int i = 0; i < workers; ++i) S->workers.emplace_back(worker_main, S);
+  *out = S;
+  return TJ_OK;
+}
+
+tj_status tj_server_submit(tj_server* S, const tj_request* r, int64_t* ticket) {
+  if (!S || !r || !ticket) return TJ_ERR_INVALID;
+  if (r->op != TJ_OP_JOIN && r->op != TJ_OP_SORT) return TJ_ERR_INVALID;
+  Pending p;
+  p.req = *r;
+  p.footprint = footprint_of(*r);
+  p.arrival = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    p.ticket = S->next++;
+    *ticket = p.ticket;
+    if (!S->any) {
+      S->first_arrival = p.arrival;
+      S->any = true;
+    }
+    if (p.footprint > S->budget) {  // can never be admitted
+      tj_result res = {};
+      res.status = TJ_ERR_BUDGET;
+      S->done[p.ticket] = res;
+      S->cv.notify_all();
+      return TJ_OK;
+    }
+    S->queue.push_back(p);
+  }
+  S->cv.notify_all();
+  return TJ_OK;
+}
+
+tj_status tj_server_wait(tj_server* S, int64_t ticket, tj_result* res) {
+  if (!S || !res) return TJ_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (ticket < 0 || ticket >= S->next) return TJ_ERR_INVALID;
+  S->cv.wait(lk, [&] { return S->done.count(ticket) > 0; });
+  *res = S->done[ticket];
+  return TJ_OK;
+}
+
+tj_status tj_server_replay(tj_server* S, const tj_request* reqs, const double* arrival_s,
+                           int64_t n, int64_t* tickets) {
+  if (!S || (n > 0 && (!reqs || !arrival_s || !tickets))) return TJ_ERR_INVALID;
+  const Clock::time_point t0 = Clock::now();
+  for (int64_t i = 0; i < n; ++i) {
+    const auto due = t0 + std::chrono::duration_cast<Clock::duration>(
+                              std::chrono::duration<double>(arrival_s[i]));
+    std::this_thread::sleep_until(due);
+    tj_status st = tj_server_submit(S, &reqs[i], &tickets[i]);
+    if (st != TJ_OK) return st;
+  }
+  return TJ_OK;
+}
+
+tj_status tj_server_drain(tj_server* S) {
+  if (!S) return TJ_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(S->mu);
+  S->cv.wait(lk, [&] { return S->queue.empty() && S->inflight == 0; });
+  return TJ_OK;
+}
+
+tj_status tj_server_report(tj_server* S, tj_server_stats* out) {
+  if (!S || !out) return TJ_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(S->mu);
+  tj_server_stats r = {};
+  r.completed = (int64_t)S->lat_ms.size();
+  r.p50_ms = pct(S->lat_ms, 0.50);
+  r.p99_ms = pct(S->lat_ms, 0.99);
+  r.max_ms = S->lat_ms.empty() ? 0.0 : *std::max_element(S->lat_ms.begin(), S->lat_ms.end());
+  double sum = 0;
+  for (double x : S->lat_ms) sum += x;
+  r.mean_ms = S->lat_ms.empty() ? 0.0 : sum / (double)S->lat_ms.size();
+  r.tuples = S->tuples;
+  r.makespan_s = S->any ? std::chrono::duration<double>(S->last_done - S->first_arrival).count()
+                        : 0.0;
+  r.peak_reserved = (int64_t)S->peak_reserved;
+  r.peak_inflight = S->peak_inflight;
+  *out = r;
+  return TJ_OK;
+}
+
+tj_status tj_server_reset_stats(tj_server* S) {
+  if (!S) return TJ_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->lat_ms.clear();
+  S->tuples = 0;
+  S->any = false;
+  S->peak_reserved = S->reserved;
+  S->peak_inflight = S->inflight;
+  return TJ_OK;
+}
+
+void tj_server_destroy(tj_server* S) {
+  if (!S) return;
+  tj_server_drain(S);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  for (auto& t : S->workers) t.join();
+  delete S;
+}
+
+}  // extern "C"

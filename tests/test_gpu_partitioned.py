@@ -1,0 +1,86 @@
+"""GPU parity of the partitioned (multi-pass) join: key-range batches from
+equal-width ranges (radix) or sample quantiles (PLA), grouped under a device
+memory budget.  Whatever the router and the budget, the result must equal the
+oracle's byte for byte; the working set must stay within the budget."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_21237_gb300 import api, datagen
+from gpu_util import DEV, assert_pairs_equal
+
+pytestmark = pytest.mark.gpu
+
+
+def check(kr, ir, ks, is_, **kw):
+    got = api.join_inner(kr.to(DEV), ir.to(DEV), ks.to(DEV), is_.to(DEV), **kw)
+    exp = oracle.join_inner(kr.numpy(), ir.numpy(), ks.numpy(), is_.numpy())
+    assert_pairs_equal(got, exp)
+    return api.stats()
+
+
+@pytest.mark.parametrize("router", ["radix", "pla"])
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
+def test_router_unbounded(router, dtype):
+    kr, ir, ks, is_ = datagen.uniform_pair(200_000, 300_003, -50_000, 150_000, 31, dtype)
+    st = check(kr, ir, ks, is_, router=router)
+    assert st["partitions"] > 1 and st["groups"] == 1
+    assert st["learned"] == api.ROUTERS[router]
+
+
+@pytest.mark.parametrize("s", [0.0, 1.2])
+def test_pla_budgeted_fk_zipf(s):
+    kr, ir, ks, is_ = datagen.fk_zipf(200_000, 800_000, s, 41)
+    budget = 6 << 20
+    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256)
+    assert st["groups"] > 1
+    assert st["scratch_peak"] <= budget
+    if s > 1.0:
+        assert st["heavy_keys"] >= 1  # the hottest keys get batches of their own
+
+
+def test_auto_switches_to_partitioned_under_budget():
+    kr, ir, ks, is_ = datagen.fk_zipf(300_000, 900_000, 0.8, 43)
+    st = check(kr, ir, ks, is_, mem_budget_bytes=8 << 20)
+    assert st["learned"] == api.ROUTERS["pla"] and st["groups"] > 1
+    assert st["scratch_peak"] <= 8 << 20
+    st = check(kr, ir, ks, is_)  # unbounded: single pass
+    assert st["partitions"] == 0
+
+
+def test_pla_many_to_many_and_wide_keys():
+    g = torch.Generator().manual_seed(12)
+    base = torch.randint(-(1 << 62), 1 << 62, (3000,), generator=g, dtype=torch.int64)
+    kr = base[torch.randint(0, 3000, (60000,), generator=g)]
+    ks = base[torch.randint(0, 3000, (40000,), generator=g)]
+    ir = torch.arange(60000, dtype=torch.int64)
+    is_ = torch.arange(40000, dtype=torch.int64) * 7
+    check(kr, ir, ks, is_, router="pla", partitions=64)
+    check(kr, ir, ks, is_, router="radix", partitions=64)
+
+
+def test_lognormal_pla_balances_better_than_radix():
+    kr, ir = datagen.lognormal_mix(1 << 18, 51)
+    ks, is_ = datagen.lognormal_mix(1 << 18, 52)
+    sp = check(kr, ir, ks, is_, router="pla", partitions=256)
+    sr = check(kr, ir, ks, is_, router="radix", partitions=256)
+    assert sp["balance"] < 2.5
+    assert sr["balance"] > 3 * sp["balance"]
+    assert sp["radix_balance"] > 3 * sp["balance"]
+
+
+def test_budget_too_small_is_reported():
+    kr, ir, ks, is_ = datagen.uniform_pair(100_000, 100_000, 0, 1 << 20, 3, torch.int64)
+    with pytest.raises(api.TjError) as ei:
+        api.join_inner(kr.to(DEV), ir.to(DEV), ks.to(DEV), is_.to(DEV), mem_budget_bytes=4096,
+                       router="pla")
+    assert ei.value.status == api.TJ_ERR_BUDGET
+
+
+def test_single_router_respects_budget():
+    kr, ir, ks, is_ = datagen.uniform_pair(100_000, 100_000, 0, 1 << 20, 3, torch.int64)
+    with pytest.raises(api.TjError) as ei:
+        api.join_inner(kr.to(DEV), ir.to(DEV), ks.to(DEV), is_.to(DEV), mem_budget_bytes=1 << 20,
+                       router="single")
+    assert ei.value.status == api.TJ_ERR_BUDGET

@@ -1,0 +1,80 @@
+"""GPU tests of the serving loop (tj_server_*): every request's result is the
+same alone and in a concurrent mix, admission never exceeds the budget, an
+oversized request is rejected with TJ_ERR_BUDGET, and latency percentiles are
+reported."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2602_21237_gb300 import api, datagen
+from gpu_util import DEV
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(n, seed):
+    sizes_r = datagen.log_uniform_sizes(n, 1e3, 3e5, seed)
+    sizes_s = datagen.log_uniform_sizes(n, 1e3, 3e5, seed + 1)
+    reqs = []
+    for i, (a, b) in enumerate(zip(sizes_r, sizes_s)):
+        kr, ir, ks, is_ = datagen.fk_zipf(a, b, 1.0, seed + 10 + i, device="cuda")
+        reqs.append((kr, ir, ks, is_))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix():
+    reqs = _requests(24, 100)
+    alone = [api.join_inner(*r).clone() for r in reqs]
+    sorts_alone = []
+    for kr, ir, _, _ in reqs[:6]:
+        k, i = kr.clone(), ir.clone()
+        api.sort(k, i)
+        sorts_alone.append((k, i))
+    torch.cuda.synchronize()
+    srv = api.Server(mem_budget_bytes=256 << 20, workers=6)
+    outs, tickets = [], []
+    for kr, ir, ks, is_ in reqs:
+        out = torch.full((ks.numel(), 2), -1, dtype=torch.int64, device=DEV)
+        outs.append(out)
+        tickets.append(srv.submit(api.Server.join_request(kr, ir, ks, is_, out)))
+    sorted_mix = []
+    for kr, ir, _, _ in reqs[:6]:
+        k, i = kr.clone(), ir.clone()
+        sorted_mix.append((k, i))
+        tickets.append(srv.submit(api.Server.sort_request(k, i)))
+    res = [srv.wait(t) for t in tickets]
+    rep = srv.report()
+    srv.close()
+    for r in res:
+        assert r["status"] == 0
+    for j in range(len(reqs)):
+        n = res[j]["out_count"]
+        assert torch.equal(outs[j][:n], alone[j])
+    for (k, i), (ka, ia) in zip(sorted_mix, sorts_alone):
+        assert torch.equal(k, ka) and torch.equal(i, ia)
+    assert rep["completed"] == len(tickets)
+    assert rep["peak_reserved"] <= 256 << 20
+    assert rep["peak_inflight"] >= 2  # requests overlapped
+    assert 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
+
+
+def test_oversized_request_is_rejected():
+    kr, ir, ks, is_ = datagen.fk_zipf(200_000, 400_000, 0.0, 7, device="cuda")
+    out = torch.empty((400_000, 2), dtype=torch.int64, device=DEV)
+    srv = api.Server(mem_budget_bytes=1 << 20, workers=2)
+    t = srv.submit(api.Server.join_request(kr, ir, ks, is_, out))
+    assert srv.wait(t)["status"] == api.TJ_ERR_BUDGET
+    srv.close()
+
+
+def test_replay_poisson_stream():
+    reqs = _requests(16, 300)
+    outs = [torch.empty((r[2].numel(), 2), dtype=torch.int64, device=DEV) for r in reqs]
+    srv = api.Server(mem_budget_bytes=1 << 30, workers=4)
+    arrivals = datagen.poisson_arrivals(2000.0, len(reqs), 5)
+    tickets = srv.replay([api.Server.join_request(*r, o) for r, o in zip(reqs, outs)], arrivals)
+    res = [srv.wait(t) for t in tickets]
+    rep = srv.report()
+    srv.close()
+    assert all(r["status"] == 0 for r in res)
+    assert rep["completed"] == 16 and rep["makespan_s"] > 0
