@@ -38,12 +38,16 @@ def test_adam_matches_oracle():
         d = [torch.from_numpy(a.copy()).to(DEV) for a in (th, m, v, g)]
         # (1 - beta^t) is formed in fp32 on the device as well
         api.mlp_adam(d[0], d[1], d[2], d[3], t, 3e-3)
+        # the oracle in fp64 with the constants the device holds (their fp32 values)
+        f = lambda c: float(np.float32(c))  # noqa: E731
+        b1, b2 = f(0.9), f(0.999)
         rt, rm, rv = L.adam_step(th.astype(np.float64), m.astype(np.float64),
-                                 v.astype(np.float64), g.astype(np.float64), t, lr=3e-3)
+                                 v.astype(np.float64), g.astype(np.float64), t, lr=f(3e-3),
+                                 beta1=b1, beta2=b2, eps=f(1e-8))
         # fp32 bound: a few roundings (2^-24 each) of the summed terms' magnitudes
         eps = 4 * 2.0 ** -24
-        tol_m = eps * (np.abs(0.9 * m) + np.abs(0.1 * g))
-        tol_v = eps * (np.abs(0.999 * v) + np.abs(0.001 * g * g))
+        tol_m = eps * (np.abs(b1 * m) + np.abs((1 - b1) * g))
+        tol_v = eps * (np.abs(b2 * v) + np.abs((1 - b2) * g * g))
         assert np.all(np.abs(d[1].cpu().numpy() - rm) <= tol_m + 1e-30)
         assert np.all(np.abs(d[2].cpu().numpy() - rv) <= tol_v + 1e-30)
         # the step divides m by sqrt(v): relative error of a few 1e-7 of lr * |m / sqrt v|
