@@ -137,6 +137,27 @@ tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, i
 tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream);
 
 /*
+ * tj_sort for callers that cannot allocate device memory (the paper has no
+ * counterpart).  Some callers cannot call cudaMalloc, cudaMallocAsync or any
+ * allocator when they sort: code that runs while an outer framework owns the
+ * device's memory pool, allocation-free real-time paths, or processes that
+ * must not grow device memory after start-up.  This entry point runs the same
+ * kernels as tj_sort and allocates nothing: its scratch is one file-scope
+ * device array of about 18 MB that every GPU loading this library holds until
+ * the process exits.  Limits and rules:
+ *   - n <= 2^20 rows per call; larger n returns TJ_ERR_INVALID (use tj_sort).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU (on
+ *     different streams, or from different threads) race and must not be made;
+ *     the array keeps the last call's contents, and each call clears what it
+ *     needs zeroed.
+ * Arguments, ordering of the result and synchronisation are those of tj_sort.
+ */
+tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream);
+
+/*
  * Many independent inner joins in one batch (no counterpart in the paper; it
  * batches Sec. 4.1 joins).  Job j joins R rows [r_off[j], r_off[j+1]) with S
  * rows [s_off[j], s_off[j+1]) of the concatenated device columns; r_off and

@@ -72,6 +72,8 @@ def _load():
         lib.tj_join_inner_ex.restype = ci
         lib.tj_sort.argtypes = [ci, vp, vp, i64, vp]
         lib.tj_sort.restype = ci
+        lib.tj_sort_noalloc.argtypes = [ci, vp, vp, i64, vp]
+        lib.tj_sort_noalloc.restype = ci
         lib.tj_join_batch.argtypes = [ci, i64, p64, p64, vp, vp, vp, vp, vp, i64, vp, p64, vp]
         lib.tj_join_batch.restype = ci
         lib.tj_status_str.argtypes = [ci]

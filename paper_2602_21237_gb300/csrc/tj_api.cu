@@ -1172,6 +1172,103 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
 
 bool bad_ptr(const void* p, int64_t n) { return n > 0 && p == nullptr; }
 
+// ---- sort without allocation --------------------------------------------------------
+// Some callers cannot call cudaMalloc (or any allocator) at the point they
+// sort: code running while an outer framework owns the device memory pool,
+// allocation-free real-time paths, or hosts that must not grow device memory
+// after start-up.  For them, tj_sort_noalloc runs the same kernels as tj_sort
+// with its scratch in one file-scope device array of a fixed size, held by
+// every GPU that loads this library until the process exits.
+constexpr int64_t kNoAllocMaxRows = (int64_t)1 << 20;  // rows per call
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxRows + kTile - 1) / kTile;
+constexpr size_t kNoAllocBytes = 2 * (size_t)kNoAllocMaxRows * 8           // B keys, B ids
+                                 + (size_t)kMaxPasses * kMaxBins * 4        // digit histograms
+                                 + (size_t)kNoAllocTiles * kMaxBins * 4     // look-back words
+                                 + 4096;                                    // job, stats, flags
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress with that device current).
+tj_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  TJ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return set_err(TJ_ERR_INTERNAL, "device index %d", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    TJ_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TJ_OK;
+}
+
+template <typename K>
+tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
+  if (n <= 1) return TJ_OK;
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  unsigned char* base = nullptr;
+  s = noalloc_scratch(&base);
+  if (s != TJ_OK) return s;
+  const int64_t tiles = ceil_div(n, kTile);
+  // carve the fixed array: B keys | B ids | histograms | look-back | job | stats | flags
+  K* bk = reinterpret_cast<K*>(base);
+  K* bv = reinterpret_cast<K*>(base + (size_t)kNoAllocMaxRows * 8);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + 2 * (size_t)kNoAllocMaxRows * 8);
+  uint32_t* lb = hist + (size_t)kMaxPasses * kMaxBins;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(lb + (size_t)kNoAllocTiles * kMaxBins);
+  RadixJob<K>* d_job = reinterpret_cast<RadixJob<K>*>(tail);
+  KeyStats* d_stats = reinterpret_cast<KeyStats*>(tail + 1024);
+  int* d_err = reinterpret_cast<int*>(tail + 2048);
+  uint32_t* d_counters = reinterpret_cast<uint32_t*>(tail + 2048 + 64);
+  static_assert(sizeof(RadixJob<int64_t>) <= 1024, "job fits its slot");
+
+  RadixJob<K> hj;
+  memset(&hj, 0, sizeof(hj));
+  hj.keys = keys;
+  hj.n = n;
+  TJ_CUDA(cudaMemsetAsync(tail + 2048, 0, 2048, st));  // error word and tile counters
+  TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, sizeof(KeyStats), st));
+  TJ_CUDA(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(launch_stats<K>(d_job, 1, tiles, d_stats, st));
+  KeyStats hs;
+  TJ_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  const K lo = key_of<K>(hs.min_u), hi = key_of<K>(~hs.max_u);
+  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), /*even=*/true,
+                              max_digit_bits<K>());
+  if (plan.passes == 0) return TJ_OK;  // all keys equal
+  const int64_t bins_max = (int64_t)1 << plan.max_bits;
+  set_job_plan(hj, plan);
+  hj.hist_stride = kMaxBins;
+  hj.hist = hist;
+  hj.lookback = lb;
+  const K* rk;
+  const K* rv;
+  set_job_buffers(hj, keys, ids, bk, bv, keys, ids, &rk, &rv);
+  TJ_CUDA(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  // the array keeps the last call's contents: clear what must start at zero
+  TJ_CUDA(cudaMemsetAsync(hist, 0, (size_t)kMaxPasses * kMaxBins * sizeof(uint32_t), st));
+  TJ_CUDA(launch_histogram<K>(d_job, 1, tiles, st));
+  TJ_CUDA(launch_digit_scan<K>(d_job, 1, plan.passes, st));
+  for (int p = 0; p < plan.passes; ++p) {
+    TJ_CUDA(cudaMemsetAsync(lb, 0, (size_t)tiles * bins_max * sizeof(uint32_t), st));
+    TJ_CUDA(launch_onesweep<K>(d_job, 1, tiles, p, plan.max_bits, false, d_counters + p, d_err,
+                               st));
+  }
+  int h_err = 0;
+  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
+  if (rk != keys) return set_err(TJ_ERR_INTERNAL, "odd pass count in place");
+  return TJ_OK;
+}
+
+
 }  // namespace
 }  // namespace tj
 
@@ -1216,6 +1313,21 @@ tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, i
                               (const int64_t*)keys_s, (const int64_t*)ids_s, n_s,
                               mem_budget_bytes, o, (int64_t*)out_pairs, out_capacity, out_count,
                               st);
+  return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
+  g_err[0] = 0;
+  if (n < 0) return set_err(TJ_ERR_INVALID, "negative size");
+  if (n > kNoAllocMaxRows)
+    return set_err(TJ_ERR_INVALID,
+                   "tj_sort_noalloc sorts at most %lld rows per call (got %lld); use tj_sort",
+                   (long long)kNoAllocMaxRows, (long long)n);
+  if (bad_ptr(keys, n) || bad_ptr(ids, n))
+    return set_err(TJ_ERR_INVALID, "null pointer with a non-zero size");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == TJ_I32) return sort_noalloc_impl<int32_t>((int32_t*)keys, (int32_t*)ids, n, st);
+  if (dt == TJ_I64) return sort_noalloc_impl<int64_t>((int64_t*)keys, (int64_t*)ids, n, st);
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
 }
 
