@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the learned / batched / serving measurements")
     return ap.parse_args()
 
 
@@ -393,6 +395,13 @@ def run_tj(args, ws, rank, local):
                "sample": (f"key range [0, n_r/64) of the workload: {len(sample[0])} R rows, "
                           f"{len(sample[2])} S rows (s={sample[6]}), sort of {len(sample[4])} "
                           f"rows; {dt:.2f} s single-threaded")}
+    extras = None
+    if rank == 0 and ws == 1 and not args.no_extras:
+        del kr, ir, rels, sort_src_k, sort_src_i, out, sk, si
+        torch.cuda.empty_cache()
+        extras = {"learned_vs_radix": extra_learned(args.scale),
+                  "batched_vs_one_at_a_time": extra_batched(args.scale),
+                  "serving": extra_serving(args.scale)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
@@ -401,8 +410,135 @@ def run_tj(args, ws, rank, local):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk.summary(), "gpu_launches": launches,
                 "wall_ms_per_step": wall * 1e3 / args.steps, "ops": ops, "kernels": kernels,
-                "join_stats": st0, "parallelism": f"replicas{ws}"}
+                "join_stats": st0, "parallelism": f"replicas{ws}", "extras": extras}
         print(json.dumps(line), flush=True)
+
+
+def _events_ms(fn, reps=3, warm=1):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        r = fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, r
+
+
+def extra_learned(scale):
+    """Learned partitioning (PLA, MLP) versus equal-width radix ranges on the
+    log-normal mixture workload: 2^28 int64 keys per side, 1024 batches."""
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    n = max(1 << 16, int((1 << 28) * scale))
+    kr, ir = datagen.lognormal_mix(n, 20260223, device="cuda")
+    ks, is_ = datagen.lognormal_mix(n, 20260233, device="cuda")
+    out = torch.empty((2 * n, 2), dtype=torch.int64, device="cuda")
+    res = {"workload": f"lognormal_mix_2^{n.bit_length() - 1}_per_side_int64", "partitions": 1024}
+    pairs = None
+    for name, cfg in (("single_pass", dict(router="single")),
+                      ("radix", dict(router="radix", partitions=1024)),
+                      ("pla", dict(router="pla", partitions=1024)),
+                      ("mlp", dict(router="mlp", partitions=1024))):
+        ms, r = _events_ms(lambda: api.join_inner(kr, ir, ks, is_, out=out, **cfg))
+        st = api.stats()
+        if pairs is None:
+            pairs = r.shape[0]
+        assert r.shape[0] == pairs
+        res[name] = {"ms": ms, "tuples_per_s": 2 * n / (ms / 1e3),
+                     "balance_max_over_mean": st["balance"] if name != "single_pass" else None,
+                     "radix_passes": st["radix_passes"]}
+    res["pairs"] = pairs
+    res["radix_balance_estimated_from_sample"] = api.stats()["radix_balance"]
+    del kr, ir, ks, is_, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_batched(scale):
+    """4096 joins, |R|, |S| log-uniform in [1e3, 1e6], int32 keys uniform over
+    [0, 2|R|): one batched call (autotuned, one CUDA graph) versus one call per
+    join."""
+    import time as _t
+
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    hi = max(2e3, 1e6 * scale)
+    r_off, s_off, kr, ir, ks, is_ = datagen.batch_jobs(4096, 1e3, hi, 20260224, device="cuda")
+    out = torch.empty((max(1, s_off[-1] * 2), 2), dtype=torch.int32, device="cuda")
+    api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out, autotune=True)
+    torch.cuda.synchronize()
+    reps = 3
+    t0 = _t.perf_counter()
+    for _ in range(reps):
+        p, _o = api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out)
+    torch.cuda.synchronize()
+    tb = (_t.perf_counter() - t0) / reps
+    st = api.stats()
+    t0 = _t.perf_counter()
+    tot = 0
+    for j in range(4096):
+        a, b, c, d = r_off[j], r_off[j + 1], s_off[j], s_off[j + 1]
+        tot += api.join_inner(kr[a:b], ir[a:b], ks[c:d], is_[c:d], out=out[tot:]).shape[0]
+    torch.cuda.synchronize()
+    t1 = _t.perf_counter() - t0
+    rows = r_off[-1] + s_off[-1]
+    assert tot == p.shape[0]
+    res = {"jobs": 4096, "rows": rows, "pairs": tot,
+           "batched": {"ms": tb * 1e3, "tuples_per_s": rows / tb, "tile_rows": st["tile_rows"],
+                       "digit_cap": st["digit_cap"], "radix_passes": st["radix_passes"]},
+           "one_at_a_time": {"ms": t1 * 1e3, "tuples_per_s": rows / t1}}
+    del kr, ir, ks, is_, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_serving(scale, rates=(10.0, 100.0, 1000.0, 10000.0), budget_gb=64, workers=8):
+    """Poisson arrivals of join requests, |R|, |S| log-uniform in [1e4, 1e8],
+    int64 foreign keys Zipf(1.0), admitted against a 64 GB budget."""
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    top = max(20_000, int(1e8 * scale))
+    kr, ir, ks, is_ = datagen.fk_zipf(top, top, 1.0, 20260225, device="cuda")
+    srv = api.Server(mem_budget_bytes=int(budget_gb * (1 << 30)), workers=workers)
+    out = []
+    for i, lam in enumerate(rates):
+        n_req = int(min(200, max(20, lam * 2.0)))
+        nr = datagen.log_uniform_sizes(n_req, 1e4, top, 20260300 + i)
+        ns = datagen.log_uniform_sizes(n_req, 1e4, top, 20260400 + i)
+        g = torch.Generator().manual_seed(20260500 + i)
+        reqs = []
+        for a, b in zip(nr, ns):
+            off = int(torch.randint(0, top - b + 1, (1,), generator=g))
+            # R: the first a keys of R's permutation; S: a slice of S's Zipf draws
+            reqs.append(api.Server.join_request(kr[:a], ir[:a], ks[off:off + b],
+                                                is_[off:off + b], None, b))
+        arr = datagen.poisson_arrivals(lam, n_req, 20260600 + i)
+        srv.reset_stats()
+        tickets = srv.replay(reqs, arr)
+        res = [srv.wait(t) for t in tickets]
+        rep = srv.report()
+        assert all(r["status"] == 0 for r in res), res[:3]
+        out.append({"rate_per_s": lam, "requests": n_req, "p50_ms": rep["p50_ms"],
+                    "p99_ms": rep["p99_ms"], "max_ms": rep["max_ms"],
+                    "throughput_tuples_per_s": rep["tuples"] / max(rep["makespan_s"], 1e-9),
+                    "peak_inflight": rep["peak_inflight"],
+                    "peak_reserved_gb": rep["peak_reserved"] / 2**30})
+    srv.close()
+    del kr, ir, ks, is_
+    torch.cuda.empty_cache()
+    return {"budget_gb": budget_gb, "workers": workers, "sizes": f"log-uniform [1e4, {top:.0e}]",
+            "keys": "int64 foreign keys, Zipf(1.0)", "rates": out}
 
 
 def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort, ws):

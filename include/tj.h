@@ -66,6 +66,8 @@ typedef struct {
   int64_t max_partition;   /* rows (R + S) of the largest batch */
   double balance;          /* largest batch / mean batch (1 = perfect) */
   double radix_balance;    /* the same for equal-width key ranges, from the sample */
+  int32_t tile_rows;       /* batched join: rows per onesweep tile used */
+  int32_t digit_cap;       /* batched join: widest radix digit allowed */
 } tj_stats;
 
 /*
@@ -215,7 +217,9 @@ typedef struct {
   const void* keys_s;    /* join only */
   const void* ids_s;
   int64_t n_s;
-  void* out_pairs;       /* join only: out_capacity pairs */
+  void* out_pairs;       /* join only: out_capacity pairs; NULL = the server allocates the
+                            output inside the request's reservation, counts the pairs and
+                            releases it (load generation) */
   int64_t out_capacity;
 } tj_request;
 
@@ -251,6 +255,22 @@ tj_status tj_server_report(tj_server* s, tj_server_stats* out);
 tj_status tj_server_reset_stats(tj_server* s);
 /* Drains, stops the workers and frees the server. */
 void tj_server_destroy(tj_server* s);
+
+/*
+ * tj_join_batch after tuning (no counterpart in the paper): runs the batch
+ * once per candidate (widest radix digit 6..10 bits, which sets the passes and
+ * each pass's fan-out, and onesweep tiles of 2048 or 4096 rows), keeps the
+ * fastest, caches it for batches of the same dtype, job count and mean size
+ * (bucketed by powers of two; the file named by the environment variable
+ * TJ_TUNE_CACHE, if set, keeps the cache across processes) and returns the
+ * result of a final run with it.  tj_join_batch uses a cached choice when one
+ * exists.  Results do not depend on the choice.
+ */
+tj_status tj_autotune_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off,
+                            const int64_t* s_off, const void* keys_r, const void* ids_r,
+                            const void* keys_s, const void* ids_s, void* out_pairs,
+                            int64_t out_capacity, int64_t* out_off, int64_t* out_count,
+                            void* stream);
 
 /* Text of a status code (static storage). */
 const char* tj_status_str(tj_status s);

@@ -38,7 +38,8 @@ class _Stats(ctypes.Structure):
                 ("out_count", ctypes.c_int64), ("used_hbm_table", ctypes.c_int32),
                 ("learned", ctypes.c_int32), ("partitions", ctypes.c_int32),
                 ("heavy_keys", ctypes.c_int32), ("max_partition", ctypes.c_int64),
-                ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double)]
+                ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double),
+                ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):
@@ -76,6 +77,8 @@ def _load():
         lib.tj_sort_noalloc.restype = ci
         lib.tj_join_batch.argtypes = [ci, i64, p64, p64, vp, vp, vp, vp, vp, i64, vp, p64, vp]
         lib.tj_join_batch.restype = ci
+        lib.tj_autotune_batch.argtypes = [ci, i64, p64, p64, vp, vp, vp, vp, vp, i64, vp, p64, vp]
+        lib.tj_autotune_batch.restype = ci
         lib.tj_status_str.argtypes = [ci]
         lib.tj_status_str.restype = ctypes.c_char_p
         lib.tj_last_error.argtypes = []
@@ -253,10 +256,13 @@ def sort(keys, ids, stream=None):
     return keys, ids
 
 
-def join_batch(r_off, s_off, keys_r, ids_r, keys_s, ids_s, out=None, stream=None):
+def join_batch(r_off, s_off, keys_r, ids_r, keys_s, ids_s, out=None, stream=None,
+               autotune: bool = False):
     """Many independent joins stored back to back (job j: R rows
     [r_off[j], r_off[j+1]), S rows [s_off[j], s_off[j+1])).  Returns
-    (pairs, out_off) with out_off a device int64 tensor of n_jobs + 1 entries."""
+    (pairs, out_off) with out_off a device int64 tensor of n_jobs + 1 entries.
+    autotune=True runs tj_autotune_batch (times the candidate digit widths and
+    tiles on this batch and caches the fastest)."""
     lib = _load()
     dev = keys_r.device
     dt = _dt(keys_r)
@@ -274,8 +280,10 @@ def join_batch(r_off, s_off, keys_r, ids_r, keys_s, ids_s, out=None, stream=None
         out_off = torch.zeros(nj + 1, dtype=torch.int64, device=dev)
         sp = _stream(stream)
 
+        fn = lib.tj_autotune_batch if autotune else lib.tj_join_batch
+
         def run(buf):
-            return lib.tj_join_batch(dt, nj, ro, so, keys_r.data_ptr(), ids_r.data_ptr(),
+            return fn(dt, nj, ro, so, keys_r.data_ptr(), ids_r.data_ptr(),
                                      keys_s.data_ptr(), ids_s.data_ptr(),
                                      0 if buf is None else buf.data_ptr(),
                                      0 if buf is None else buf.shape[0], out_off.data_ptr(),
@@ -357,10 +365,13 @@ class Server:
         self._keep = {}
 
     @staticmethod
-    def join_request(keys_r, ids_r, keys_s, ids_s, out):
+    def join_request(keys_r, ids_r, keys_s, ids_s, out=None, capacity: int = 0):
+        """out=None: the server allocates `capacity` pairs (default n_s) for the
+        request's output inside its reservation, counts them and releases them."""
+        cap = out.shape[0] if out is not None else int(capacity or keys_s.numel())
         r = _Req(0, _dt(keys_r), keys_r.data_ptr(), ids_r.data_ptr(), keys_r.numel(),
-                 keys_s.data_ptr(), ids_s.data_ptr(), keys_s.numel(), out.data_ptr(),
-                 out.shape[0])
+                 keys_s.data_ptr(), ids_s.data_ptr(), keys_s.numel(),
+                 out.data_ptr() if out is not None else None, cap)
         r._tensors = (keys_r, ids_r, keys_s, ids_s, out)
         return r
 

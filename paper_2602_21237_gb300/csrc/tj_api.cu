@@ -11,6 +11,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <string>
 #include <limits>
 #include <mutex>
 #include <vector>
@@ -279,7 +281,7 @@ void set_job_buffers(RadixJob<K>& j, const K* in_k, const K* in_v, K* ak, K* av,
 // ---- inner join -------------------------------------------------------------------
 struct Opts {
   int router = TJ_ROUTE_AUTO;
-  int partitions = 1024;
+  int partitions = 512;
   int stride = 100;
   int segments = 4096;
   int mlp_steps = 600;
@@ -623,16 +625,63 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     stats.heavy_keys = heavy;
   }
 
-  // ---- 2. route pass into staging ----
-  const int64_t tiles_r = ceil_div(nr, kTile), tiles_s = ceil_div(ns, kTile);
+  // ---- 2. route pass into staging, in chunks whose look-back fits the budget ----
+  // radix index over the cuts: bucket b = (key - lo) >> rshift
+  const uint64_t krange = range_of<K>(lo, hi);
+  const int kbits = bitlen(krange);
+  const int rshift = std::max(0, kbits - 12);
+  std::vector<uint16_t> tab(kRouteBuckets + 1);
+  {
+    size_t c = 0;
+    for (int bkt = 0; bkt < kRouteBuckets; ++bkt) {
+      const uint64_t off = (uint64_t)bkt << rshift;
+      if (rshift < 64 && off <= krange) {
+        const K start = (K)(lo_bits<K>(lo) + off);
+        while (c < cuts.size() && cuts[c] < start) ++c;
+        tab[(size_t)bkt] = (uint16_t)c;
+      } else {
+        tab[(size_t)bkt] = (uint16_t)ncuts;
+      }
+    }
+    tab[kRouteBuckets] = (uint16_t)ncuts;
+  }
+  const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
+  const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
+                                  : INT64_MAX;
+  const int64_t all_tiles = ceil_div(std::max(nr, ns), kTile);
+  const int64_t chunk_tiles = std::max<int64_t>(1, std::min(all_tiles, route_lb / lb_per_tile));
+  const int64_t chunk_rows = chunk_tiles * kTile;  // <= max(n_r, n_s) rounded up to a tile
+  struct Chunk {
+    int side;
+    int64_t r0, n;
+  };
+  std::vector<Chunk> chunks;
+  for (int side = 0; side < 2; ++side) {
+    const int64_t n = side ? ns : nr;
+    for (int64_t r0 = 0; r0 < n; r0 += chunk_rows) chunks.push_back({side, r0, std::min(chunk_rows, n - r0)});
+  }
+  const int nch = (int)chunks.size();
+  // launch groups of chunks, each group's look-back within route_lb
+  std::vector<std::pair<int, int>> cgroups;
+  int64_t lb_max = 0;
+  for (int i = 0; i < nch;) {
+    int j = i;
+    int64_t acc = 0;
+    while (j < nch && (j == i || acc + ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile <= route_lb))
+      acc += ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile, ++j;
+    cgroups.push_back({i, j});
+    lb_max = std::max(lb_max, acc);
+    i = j;
+  }
   Carve cc;
   const size_t o_rk = cc.add<K>((size_t)nr), o_rv = cc.add<K>((size_t)nr);
   const size_t o_sk = cc.add<K>((size_t)ns), o_sv = cc.add<K>((size_t)ns);
   const size_t staging = cc.off;
   const size_t o_cuts = cc.add<K>(kMaxCuts);
-  const size_t o_hist = cc.add<uint32_t>(2 * kMaxBins);
-  const size_t o_lb = cc.add<uint32_t>((size_t)(tiles_r + tiles_s) << rbits);
-  const size_t o_jobs = cc.add<RadixJob<K>>(2);
+  const size_t o_tab = cc.add<uint16_t>(kRouteBuckets + 1);
+  const size_t o_hist = cc.add<uint32_t>((size_t)nch * kMaxBins);
+  const size_t o_lb = cc.add<uint32_t>((size_t)(lb_max / 4));
+  const size_t o_jobs = cc.add<RadixJob<K>>((size_t)nch * 2);
   const size_t o_misc = cc.add<int64_t>(32);
   Block stg;
   TJ_CUDA(stg.alloc(cc.off, st));
@@ -645,43 +694,104 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   std::copy(cuts.begin(), cuts.end(), hc.begin());
   TJ_CUDA(cudaMemcpyAsync(stg.at<K>(o_cuts), hc.data(), kMaxCuts * sizeof(K),
                           cudaMemcpyHostToDevice, st));
-  RadixJob<K> hj[2];
-  memset(hj, 0, sizeof(hj));
-  for (int side = 0; side < 2; ++side) {
-    RadixJob<K>& x = hj[side];
-    x.keys = side ? ks : kr;
-    x.n = side ? ns : nr;
-    x.tile0 = side ? tiles_r : 0;
+  TJ_CUDA(cudaMemcpyAsync(stg.at<uint16_t>(o_tab), tab.data(), tab.size() * sizeof(uint16_t),
+                          cudaMemcpyHostToDevice, st));
+  // histogram jobs (global tile numbering) then per-launch route jobs (tile0
+  // rebased to their launch); the route jobs' hist slots receive the bases
+  std::vector<RadixJob<K>> hj((size_t)nch * 2);
+  memset(hj.data(), 0, hj.size() * sizeof(RadixJob<K>));
+  int64_t tiles_all = 0;
+  for (int c = 0; c < nch; ++c) {
+    const Chunk& ch = chunks[(size_t)c];
+    RadixJob<K>& x = hj[(size_t)c];
+    const K* kb = ch.side ? ks : kr;
+    const K* vb = ch.side ? is : ir;
+    x.keys = kb + ch.r0;
+    x.n = ch.n;
+    x.tile0 = tiles_all;
+    tiles_all += ceil_div(ch.n, kTile);
+    x.lo = lo_bits<K>(lo);
     x.passes = 1;
     x.bits[0] = rbits;
     x.hist_stride = kMaxBins;
-    x.hist = stg.at<uint32_t>(o_hist) + side * kMaxBins;
-    x.lookback = stg.at<uint32_t>(o_lb) + (side ? (tiles_r << rbits) : 0);
-    x.src_k[0] = side ? ks : kr;
-    x.src_v[0] = side ? is : ir;
-    x.dst_k[0] = side ? stg.at<K>(o_sk) : stg.at<K>(o_rk);
-    x.dst_v[0] = side ? stg.at<K>(o_sv) : stg.at<K>(o_rv);
+    x.hist = stg.at<uint32_t>(o_hist) + (size_t)c * kMaxBins;
+    x.src_k[0] = kb + ch.r0;
+    x.src_v[0] = vb + ch.r0;
+    x.dst_k[0] = ch.side ? stg.at<K>(o_sk) : stg.at<K>(o_rk);
+    x.dst_v[0] = ch.side ? stg.at<K>(o_sv) : stg.at<K>(o_rv);
     x.cuts = stg.at<K>(o_cuts);
     x.ncuts = ncuts;
+    x.route_tab = stg.at<uint16_t>(o_tab);
+    x.route_shift = rshift;
+  }
+  for (auto& g : cgroups) {
+    int64_t t = 0, lbw = 0;
+    for (int c = g.first; c < g.second; ++c) {
+      RadixJob<K> x = hj[(size_t)c];
+      x.tile0 = t;
+      x.lookback = stg.at<uint32_t>(o_lb) + lbw;
+      t += ceil_div(x.n, kTile);
+      lbw += ceil_div(x.n, kTile) << rbits;
+      hj[(size_t)nch + c] = x;
+    }
   }
   RadixJob<K>* d_rj = stg.at<RadixJob<K>>(o_jobs);
   TJ_CUDA(cudaMemsetAsync(stg.p + o_misc, 0, 32 * sizeof(int64_t), st));
-  TJ_CUDA(cudaMemcpyAsync(d_rj, hj, sizeof(hj), cudaMemcpyHostToDevice, st));
-  TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_hist), 0, 2 * kMaxBins * sizeof(uint32_t), st));
+  TJ_CUDA(cudaMemcpyAsync(d_rj, hj.data(), hj.size() * sizeof(RadixJob<K>),
+                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_hist), 0, (size_t)nch * kMaxBins * sizeof(uint32_t), st));
   tr.begin("histogram", w * (nr + ns));
-  TJ_CUDA(launch_histogram<K>(d_rj, 2, tiles_r + tiles_s, st));
+  TJ_CUDA(launch_histogram<K>(d_rj, nch, tiles_all, st));
   tr.end();
-  std::vector<uint32_t> hcount(2 * (size_t)kMaxBins);
+  std::vector<uint32_t> hcount((size_t)nch * kMaxBins);
   TJ_CUDA(cudaMemcpyAsync(hcount.data(), stg.at<uint32_t>(o_hist), hcount.size() * 4,
                           cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(launch_digit_scan<K>(d_rj, 2, 1, st));
-  TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_lb), 0,
-                          ((size_t)(tiles_r + tiles_s) << rbits) * sizeof(uint32_t), st));
-  tr.begin("route", 4.0 * w * (nr + ns));
-  TJ_CUDA(launch_onesweep<K>(d_rj, 2, tiles_r + tiles_s, 0, rbits, true, d_counters + kMaxPasses,
-                             d_err, st));
-  tr.end();
-  TJ_CUDA(cudaStreamSynchronize(st));  // partition sizes for the grouping
+  TJ_CUDA(cudaStreamSynchronize(st));
+  // partition sizes and every chunk's base per partition (partition-major,
+  // chunks in row order: the route is stable)
+  std::vector<int64_t> pcount(2 * (size_t)nparts, 0);
+  for (int c = 0; c < nch; ++c)
+    for (int p2 = 0; p2 < nparts; ++p2)
+      pcount[(size_t)chunks[(size_t)c].side * nparts + p2] += hcount[(size_t)c * kMaxBins + p2];
+  {
+    std::vector<int64_t> run(2 * (size_t)nparts, 0);
+    for (int side = 0; side < 2; ++side) {
+      int64_t acc = 0;
+      for (int p2 = 0; p2 < nparts; ++p2) {
+        run[(size_t)side * nparts + p2] = acc;
+        acc += pcount[(size_t)side * nparts + p2];
+      }
+    }
+    for (int c = 0; c < nch; ++c) {
+      const int side = chunks[(size_t)c].side;
+      for (int p2 = 0; p2 < nparts; ++p2) {
+        const int64_t cnt = hcount[(size_t)c * kMaxBins + p2];
+        hcount[(size_t)c * kMaxBins + p2] = (uint32_t)run[(size_t)side * nparts + p2];
+        run[(size_t)side * nparts + p2] += cnt;
+      }
+    }
+    if ((int64_t)nr + ns >= ((int64_t)1 << 32))
+      return set_err(TJ_ERR_INVALID, "partitioned join needs n_r + n_s < 2^32");
+  }
+  TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_hist), hcount.data(), hcount.size() * 4,
+                          cudaMemcpyHostToDevice, st));
+  for (auto& g : cgroups) {
+    int64_t t = 0;
+    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, kTile);
+    TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_lb), 0, (size_t)lb_max, st));
+    TJ_CUDA(cudaMemsetAsync(d_counters + kMaxPasses, 0, sizeof(uint32_t), st));
+    double rows = 0;
+    for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
+    tr.begin("route", 4.0 * w * rows);
+    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
+                               d_counters + kMaxPasses, d_err, st));
+    tr.end();
+  }
+  std::vector<uint32_t> hc2(2 * (size_t)kMaxBins, 0);  // partition sizes per side
+  for (int side = 0; side < 2; ++side)
+    for (int p2 = 0; p2 < nparts; ++p2)
+      hc2[(size_t)side * kMaxBins + p2] = (uint32_t)pcount[(size_t)side * nparts + p2];
+  hcount.swap(hc2);
 
   // ---- 3. batches and groups ----
   struct Part {
@@ -709,7 +819,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     const int64_t bins = (int64_t)1 << q.plan.max_bits;
     q.ws = (int64_t)nb * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
            (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * bins * 4 +
-           ceil_div(q.ns, kJTile) * 24 + 2 * (int64_t)sizeof(RadixJob<K>) +
+           ceil_div(q.ns, kJTile) * 28 + (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * 4 +
+           2 * (int64_t)sizeof(RadixJob<K>) +
            (int64_t)sizeof(JoinJob<K>) + 2 * (int64_t)std::max(1, q.plan.passes) * bins * 4 + 4096;
     live_rows += q.nr + q.ns;
     P.push_back(q);
@@ -717,7 +828,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   if (r_at != nr || s_at != ns) return set_err(TJ_ERR_INTERNAL, "route counts do not add up");
   stats.max_partition = maxrows;
   stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
-  const int64_t fixed = (int64_t)(cc.off - staging) + 4096;
+  const int64_t fixed = (int64_t)(cc.off - staging) + 4096;  // route structures (look-back incl.)
   const int64_t room = budget ? (int64_t)budget - fixed : INT64_MAX;
   if (room <= 0) return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes",
                                 budget, (long long)fixed);
@@ -820,6 +931,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     }
     const size_t o_ra = gc.add<int64_t>((size_t)jtiles), o_rb = gc.add<int64_t>((size_t)jtiles);
     const size_t o_jlb = gc.add<uint64_t>((size_t)jtiles);
+    const size_t o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(tiles, 1));
+    const size_t o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(jtiles, 1));
     if ((int64_t)gc.off > std::max<int64_t>(ws_max, 256))
       return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, working block has %lld", gc.off,
                      (long long)ws_max);
@@ -831,10 +944,14 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     TJ_CUDA(cudaMemcpyAsync(d_gjj, jj.data(), jj.size() * sizeof(JoinJob<K>),
                             cudaMemcpyHostToDevice, st));
     TJ_CUDA(cudaMemsetAsync(d_counters, 0, (kMaxPasses + 1) * sizeof(uint32_t), st));
+    int32_t* d_tmap = wk.at<int32_t>(o_tmap);
+    int32_t* d_jmap = wk.at<int32_t>(o_jmap);
+    TJ_CUDA(launch_fill_tile_job<K>(d_gj, (int)(2 * nj), d_tmap, st));
+    TJ_CUDA(launch_fill_join_tile_job<K>(d_gjj, (int)nj, d_jmap, st));
     if (P_g > 0) {
       TJ_CUDA(cudaMemsetAsync(wk.p + o_hist_g, 0, hist_words * sizeof(uint32_t), st));
       tr.begin("histogram", w * rows);
-      TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), tiles, st));
+      TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), tiles, st, d_tmap));
       tr.end();
       TJ_CUDA(launch_digit_scan<K>(d_gj, (int)(2 * nj), P_g, st));
       for (int p = 0; p < P_g; ++p) {
@@ -845,18 +962,18 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         TJ_CUDA(cudaMemsetAsync(wk.p + o_lb_g, 0, lb_words * sizeof(uint32_t), st));
         tr.begin("onesweep", 4.0 * w * prow);
         TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), tiles, p, maxbits, false, d_counters + p,
-                                   d_err, st));
+                                   d_err, st, d_tmap));
         tr.end();
       }
     }
     TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, jtiles, wk.at<int64_t>(o_ra),
-                                  wk.at<int64_t>(o_rb), st));
+                                  wk.at<int64_t>(o_rb), st, d_jmap));
     TJ_CUDA(cudaMemsetAsync(wk.at<uint64_t>(o_jlb), 0, (size_t)std::max<int64_t>(jtiles, 1) * 8,
                             st));
     tr.begin("join", 2.0 * w * rows);
     TJ_CUDA(launch_join<K>(d_gjj, (int)nj, jtiles, wk.at<int64_t>(o_ra), wk.at<int64_t>(o_rb),
                            wk.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, d_base,
-                           nullptr, d_total, d_err, st));
+                           nullptr, d_total, d_err, st, d_jmap));
     tr.end();
     TJ_CUDA(launch_add_base(d_base, d_total, st));
   }
@@ -973,9 +1090,13 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
 template <typename K>
 tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, const K* kr,
                      const K* ir, const K* ks, const K* is, K* out, int64_t cap,
-                     int64_t* d_out_off, int64_t* out_count, cudaStream_t st) {
+                     int64_t* d_out_off, int64_t* out_count, cudaStream_t st, int digit_cap,
+                     int items) {
   tj_stats stats = {};
   stats.groups = 1;
+  const int tile = kSortThreads * items;
+  stats.tile_rows = tile;
+  stats.digit_cap = digit_cap;
   *out_count = 0;
   tj_status s = ensure_device();
   if (s != TJ_OK) return s;
@@ -991,7 +1112,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
       x.keys = (side ? ks : kr) + a;
       x.n = n;
       x.tile0 = tiles;
-      tiles += ceil_div(n, kTile);
+      tiles += ceil_div(n, tile);
     }
   }
   Carve cc;
@@ -1011,7 +1132,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, (size_t)(2 * nj) * sizeof(KeyStats), st));
   TJ_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>),
                           cudaMemcpyHostToDevice, st));
-  TJ_CUDA(launch_stats<K>(d_jobs, (int)(2 * nj), tiles, d_stats, st));
+  TJ_CUDA(launch_stats<K>(d_jobs, (int)(2 * nj), tiles, d_stats, st, tile));
   std::vector<KeyStats> hs((size_t)(2 * nj));
   TJ_CUDA(cudaMemcpyAsync(hs.data(), d_stats, hs.size() * sizeof(KeyStats),
                           cudaMemcpyDeviceToHost, st));
@@ -1033,7 +1154,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
     plo[(size_t)j] = lo_bits<K>(lo);
     prange[(size_t)j] = range_of<K>(lo, hi);
     live[(size_t)j] = 1;
-    P = std::max(P, make_plan(plo[(size_t)j], prange[(size_t)j], false, max_digit_bits<K>()).passes);
+    P = std::max(P, make_plan(plo[(size_t)j], prange[(size_t)j], false, digit_cap).passes);
   }
   stats.radix_passes = P;
   // scratch: ping-pong copies of every live pair, histograms, look-back, join state
@@ -1044,7 +1165,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   tiles = 0;
   for (int64_t j = 0; j < nj; ++j) {
     Plan pl;
-    if (live[(size_t)j]) pl = make_plan(plo[(size_t)j], prange[(size_t)j], false, max_digit_bits<K>(), P);
+    if (live[(size_t)j]) pl = make_plan(plo[(size_t)j], prange[(size_t)j], false, digit_cap, P);
     plans[(size_t)j] = pl;
     stats.key_bits = std::max(stats.key_bits, pl.key_bits);
     stats.digit_bits = std::max(stats.digit_bits, pl.max_bits);
@@ -1053,7 +1174,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
       RadixJob<K>& x = hj[(size_t)(2 * j + side)];
       if (!live[(size_t)j]) x.n = 0;
       x.tile0 = tiles;
-      const int64_t t = ceil_div(x.n, kTile);
+      const int64_t t = ceil_div(x.n, tile);
       tiles += t;
       hist_at[(size_t)(2 * j + side)] = hist_words;
       hist_words += (int64_t)std::max(P, 1) * bins;
@@ -1075,9 +1196,13 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   const size_t o_ra = bc.add<int64_t>((size_t)std::max<int64_t>(jtiles, 1));
   const size_t o_rb = bc.add<int64_t>((size_t)std::max<int64_t>(jtiles, 1));
   const size_t o_jlb = bc.add<uint64_t>((size_t)std::max<int64_t>(jtiles, 1));
+  const size_t o_tmap = bc.add<int32_t>((size_t)std::max<int64_t>(tiles, 1));
+  const size_t o_jmap = bc.add<int32_t>((size_t)std::max<int64_t>(jtiles, 1));
   Block big;
   TJ_CUDA(big.alloc(bc.off, st));
   stats.scratch_peak = (int64_t)(bc.off + cc.off);
+  int32_t* d_tmap = big.at<int32_t>(o_tmap);
+  int32_t* d_jmap = big.at<int32_t>(o_jmap);
 
   std::vector<JoinJob<K>> hjj((size_t)nj);
   int64_t jt = 0;
@@ -1124,25 +1249,27 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   auto step = [&](cudaError_t x) {
     if (e == cudaSuccess) e = x;
   };
+  step(launch_fill_tile_job<K>(d_jobs, (int)(2 * nj), d_tmap, st, tile));
+  step(launch_fill_join_tile_job<K>(d_jj, (int)nj, d_jmap, st));
   if (P > 0) {
     step(cudaMemsetAsync(big.at<uint32_t>(o_hist), 0,
                          (size_t)std::max<int64_t>(hist_words, 1) * sizeof(uint32_t), st));
-    step(launch_histogram<K>(d_jobs, (int)(2 * nj), tiles, st));
+    step(launch_histogram<K>(d_jobs, (int)(2 * nj), tiles, st, d_tmap, tile));
     step(launch_digit_scan<K>(d_jobs, (int)(2 * nj), P, st));
     for (int p = 0; p < P; ++p) {
       step(cudaMemsetAsync(big.at<uint32_t>(o_lb), 0,
                            (size_t)std::max<int64_t>(lb_words, 1) * sizeof(uint32_t), st));
       step(launch_onesweep<K>(d_jobs, (int)(2 * nj), tiles, p, stats.digit_bits, false, d_counters + p,
-                              d_err, st));
+                              d_err, st, d_tmap, items));
     }
   }
   step(launch_tile_ranges<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra),
-                             big.at<int64_t>(o_rb), st));
+                             big.at<int64_t>(o_rb), st, d_jmap));
   step(cudaMemsetAsync(big.at<uint64_t>(o_jlb), 0,
                        (size_t)std::max<int64_t>(jtiles, 1) * sizeof(uint64_t), st));
   step(launch_join<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra), big.at<int64_t>(o_rb),
                       big.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, nullptr,
-                      d_out_off, d_total, d_err, st));
+                      d_out_off, d_total, d_err, st, d_jmap));
   step(launch_fix_job_out<K>(d_jj, (int)nj, jtiles, d_out_off, d_total, st));
   if (use_graph) {
     cudaError_t e2 = cudaStreamEndCapture(st, &graph);
@@ -1168,6 +1295,98 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
     return set_err(TJ_ERR_CAPACITY, "batch result has %lld pairs, capacity %lld",
                    (long long)h_total, (long long)cap);
   return TJ_OK;
+}
+
+
+// ---- autotuner of the batched join --------------------------------------------------
+// Choices: the widest radix digit (and so the number of passes and the fan-out
+// of each pass) and the onesweep tile (2048 or 4096 rows: small jobs waste
+// less of a smaller last tile).  A choice is cached per (dtype, log2 jobs,
+// log2 mean rows per array); TJ_TUNE_CACHE names a file that persists it.
+struct TuneChoice {
+  int digit;
+  int items;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, TuneChoice>> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(int dt, int64_t nj, int64_t rows) {
+  char b[64];
+  const int64_t avg = nj > 0 ? rows / (2 * nj) : 0;
+  snprintf(b, sizeof(b), "batch_d%d_j%d_a%d", dt, bitlen((uint64_t)nj), bitlen((uint64_t)avg));
+  return b;
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = getenv("TJ_TUNE_CACHE");
+  if (!f) return;
+  FILE* fp = fopen(f, "r");
+  if (!fp) return;
+  char key[64];
+  int d, it;
+  while (fscanf(fp, "%63s %d %d", key, &d, &it) == 3)
+    if (d >= 4 && d <= kMaxDigitBits && (it == 4 || it == kItems)) g_tune.push_back({key, {d, it}});
+  fclose(fp);
+}
+
+bool tune_get(const std::string& k, TuneChoice* c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  for (auto it = g_tune.rbegin(); it != g_tune.rend(); ++it)
+    if (it->first == k) {
+      *c = it->second;
+      return true;
+    }
+  return false;
+}
+
+void tune_put(const std::string& k, TuneChoice c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_load_locked();
+  g_tune.push_back({k, c});
+  const char* f = getenv("TJ_TUNE_CACHE");
+  if (!f) return;
+  FILE* fp = fopen(f, "a");
+  if (!fp) return;
+  fprintf(fp, "%s %d %d\n", k.c_str(), c.digit, c.items);
+  fclose(fp);
+}
+
+template <typename K>
+tj_status batch_tuned(int dt, int64_t nj, const int64_t* r_off, const int64_t* s_off, const K* kr,
+                      const K* ir, const K* ks, const K* is, K* out, int64_t cap,
+                      int64_t* d_out_off, int64_t* out_count, cudaStream_t st, bool tune) {
+  const std::string key = tune_key(dt, nj, r_off[nj] + s_off[nj]);
+  TuneChoice c = {max_digit_bits<K>(), kItems};
+  if (!tune) {
+    tune_get(key, &c);
+    return batch_impl<K>(nj, r_off, s_off, kr, ir, ks, is, out, cap, d_out_off, out_count, st,
+                         c.digit, c.items);
+  }
+  // time every candidate on this batch (each run also produces the result)
+  double best = 1e300;
+  TuneChoice bc = c;
+  for (int d = 6; d <= max_digit_bits<K>(); ++d)
+    for (int it : {4, kItems}) {
+      for (int rep = 0; rep < 2; ++rep) {  // the first run warms the pool
+        const auto t0 = std::chrono::steady_clock::now();
+        tj_status s = batch_impl<K>(nj, r_off, s_off, kr, ir, ks, is, out, cap, d_out_off,
+                                    out_count, st, d, it);
+        const double dtm =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (s != TJ_OK) return s;
+        if (rep == 1 && dtm < best) {
+          best = dtm;
+          bc = {d, it};
+        }
+      }
+    }
+  tune_put(key, bc);
+  return batch_impl<K>(nj, r_off, s_off, kr, ir, ks, is, out, cap, d_out_off, out_count, st,
+                       bc.digit, bc.items);
 }
 
 bool bad_ptr(const void* p, int64_t n) { return n > 0 && p == nullptr; }
@@ -1343,10 +1562,11 @@ tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
 }
 
-tj_status tj_join_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off, const int64_t* s_off,
-                        const void* keys_r, const void* ids_r, const void* keys_s,
-                        const void* ids_s, void* out_pairs, int64_t out_capacity,
-                        int64_t* out_off, int64_t* out_count, void* stream) {
+static tj_status batch_entry(tj_dtype dt, int64_t n_jobs, const int64_t* r_off,
+                             const int64_t* s_off, const void* keys_r, const void* ids_r,
+                             const void* keys_s, const void* ids_s, void* out_pairs,
+                             int64_t out_capacity, int64_t* out_off, int64_t* out_count,
+                             void* stream, bool tune) {
   g_err[0] = 0;
   if (!out_count) return set_err(TJ_ERR_INVALID, "out_count is NULL");
   *out_count = 0;
@@ -1368,16 +1588,33 @@ tj_status tj_join_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off, const
     return set_err(TJ_ERR_INVALID, "null pointer with a non-zero size");
   cudaStream_t st = (cudaStream_t)stream;
   if (dt == TJ_I32)
-    return batch_impl<int32_t>(n_jobs, r_off, s_off, (const int32_t*)keys_r,
-                               (const int32_t*)ids_r, (const int32_t*)keys_s,
-                               (const int32_t*)ids_s, (int32_t*)out_pairs, out_capacity, out_off,
-                               out_count, st);
+    return batch_tuned<int32_t>((int)dt, n_jobs, r_off, s_off, (const int32_t*)keys_r,
+                                (const int32_t*)ids_r, (const int32_t*)keys_s,
+                                (const int32_t*)ids_s, (int32_t*)out_pairs, out_capacity,
+                                out_off, out_count, st, tune);
   if (dt == TJ_I64)
-    return batch_impl<int64_t>(n_jobs, r_off, s_off, (const int64_t*)keys_r,
-                               (const int64_t*)ids_r, (const int64_t*)keys_s,
-                               (const int64_t*)ids_s, (int64_t*)out_pairs, out_capacity, out_off,
-                               out_count, st);
+    return batch_tuned<int64_t>((int)dt, n_jobs, r_off, s_off, (const int64_t*)keys_r,
+                                (const int64_t*)ids_r, (const int64_t*)keys_s,
+                                (const int64_t*)ids_s, (int64_t*)out_pairs, out_capacity,
+                                out_off, out_count, st, tune);
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+tj_status tj_join_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off, const int64_t* s_off,
+                        const void* keys_r, const void* ids_r, const void* keys_s,
+                        const void* ids_s, void* out_pairs, int64_t out_capacity,
+                        int64_t* out_off, int64_t* out_count, void* stream) {
+  return batch_entry(dt, n_jobs, r_off, s_off, keys_r, ids_r, keys_s, ids_s, out_pairs,
+                     out_capacity, out_off, out_count, stream, false);
+}
+
+tj_status tj_autotune_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off,
+                            const int64_t* s_off, const void* keys_r, const void* ids_r,
+                            const void* keys_s, const void* ids_s, void* out_pairs,
+                            int64_t out_capacity, int64_t* out_off, int64_t* out_count,
+                            void* stream) {
+  return batch_entry(dt, n_jobs, r_off, s_off, keys_r, ids_r, keys_s, ids_s, out_pairs,
+                     out_capacity, out_off, out_count, stream, true);
 }
 
 tj_status tj_mlp_grad(const float* theta, const float* x, const float* y, int n, float* grad,

@@ -47,6 +47,7 @@ constexpr uint64_t kValMask64 = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
 // key-range partitions of one route pass: cuts <= 1023 -> digits of <= 10 bits
 constexpr int kMaxCuts = 1024;
+constexpr int kRouteBuckets = 4096;
 // predecessors read per look-back round trip
 constexpr int kLookWindow = 8;
 
@@ -77,6 +78,10 @@ struct RadixJob {
   // number of cut keys <= key, i.e. the index of its key-range partition.
   const K* cuts;        // sorted cut keys, padded to kMaxCuts with the key type's max
   int32_t ncuts;        // real cuts (<= kMaxCuts - 1); partitions = ncuts + 1
+  // Radix index over the cuts: bucket b = (key - lo) >> route_shift (clamped to
+  // kRouteBuckets - 1) holds cuts [route_tab[b], route_tab[b + 1]).
+  const uint16_t* route_tab;  // kRouteBuckets + 1 entries
+  int32_t route_shift;
 };
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).
@@ -100,31 +105,43 @@ struct JoinJob {
 
 // ---- launchers (tj_radix.cu) -----------------------------------------------
 cudaError_t radix_init_attributes();
+// Tiles of the radix kernels have `tile` rows (kTile, or kSortThreads * items
+// of a smaller onesweep tile); jobs' tile0 counts tiles of that size.
 template <typename K>
 cudaError_t launch_stats(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                         KeyStats* d_stats, cudaStream_t st);
+                         KeyStats* d_stats, cudaStream_t st, int tile = kTile);
 template <typename K>
 cudaError_t launch_histogram(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                             cudaStream_t st);
+                             cudaStream_t st, const int32_t* d_tile_job = nullptr,
+                             int tile = kTile);
+// d_map[t] = index of the job that owns tile t (jobs' tile0 / n in tile or kJTile rows)
+template <typename K>
+cudaError_t launch_fill_tile_job(const RadixJob<K>* d_jobs, int num_jobs, int32_t* d_map,
+                                 cudaStream_t st, int tile = kTile);
+template <typename K>
+cudaError_t launch_fill_join_tile_job(const JoinJob<K>* d_jobs, int num_jobs, int32_t* d_map,
+                                      cudaStream_t st);
 template <typename K>
 cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passes,
                               cudaStream_t st);
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                             int pass, int max_bits, bool route, uint32_t* d_tile_counter,
-                            int* d_err, cudaStream_t st);
+                            int* d_err, cudaStream_t st, const int32_t* d_tile_job = nullptr,
+                            int items = kItems);
 
 // ---- launchers (tj_join.cu) -------------------------------------------------
 cudaError_t join_init_attributes();
 template <typename K>
 cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st);
+                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st,
+                               const int32_t* d_tile_job = nullptr);
 template <typename K>
 cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                         const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
                         const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
-                        int* d_err, cudaStream_t st);
+                        int* d_err, cudaStream_t st, const int32_t* d_tile_job = nullptr);
 cudaError_t launch_add_base(int64_t* d_base, int64_t* d_total, cudaStream_t st);
 
 // ---- launchers (tj_learned.cu) ----------------------------------------------

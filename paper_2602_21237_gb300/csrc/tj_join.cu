@@ -85,10 +85,10 @@ __device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
 template <typename K>
 __global__ void k_tile_ranges(const JoinJob<K>* __restrict__ jobs, int num_jobs,
                               int64_t total_tiles, int64_t* __restrict__ ra,
-                              int64_t* __restrict__ rb) {
+                              int64_t* __restrict__ rb, const int32_t* __restrict__ tile_job) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total_tiles) return;
-  const int j = find_job_j(jobs, num_jobs, t);
+  const int j = tile_job ? tile_job[t] : find_job_j(jobs, num_jobs, t);
   const JoinJob<K>* J = jobs + j;
   const int64_t row0 = (t - J->tile0) * kJTile;
   const int64_t row1 = min(J->ns, row0 + kJTile);
@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(kThreads, 3)
            const int64_t* __restrict__ ra, const int64_t* __restrict__ rb,
            uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter,
            K* __restrict__ out, int64_t capacity, const int64_t* __restrict__ out_base,
-           int64_t* __restrict__ job_out, int64_t* __restrict__ total, int* __restrict__ err) {
+           int64_t* __restrict__ job_out, int64_t* __restrict__ total, int* __restrict__ err,
+           const int32_t* __restrict__ tile_job) {
   extern __shared__ __align__(16) unsigned char smem[];
   K* s_sk = reinterpret_cast<K*>(smem);
   K* s_rk = s_sk + kJTile;
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   __syncthreads();
   const int64_t t = s_t;
   if (t >= total_tiles) return;
-  const int j = find_job_j(jobs, num_jobs, t);
+  const int j = tile_job ? tile_job[t] : find_job_j(jobs, num_jobs, t);
   const JoinJob<K> J = jobs[j];
   const int64_t a = ra[t];
   const int64_t nrr = rb[t] - a;
@@ -356,10 +357,29 @@ __global__ void __launch_bounds__(kThreads, 3)
 // ---------------------------------------------------------------------------
 template <typename K>
 cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st) {
+                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st,
+                               const int32_t* d_tile_job) {
   if (total_tiles <= 0) return cudaSuccess;
   const int64_t grid = (total_tiles + kThreads - 1) / kThreads;
-  k_tile_ranges<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_ra, d_rb);
+  k_tile_ranges<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_ra, d_rb,
+                                                        d_tile_job);
+  return cudaGetLastError();
+}
+
+template <typename K>
+__global__ void k_fill_join_tile_job(const JoinJob<K>* __restrict__ jobs,
+                                     int32_t* __restrict__ map) {
+  const int j = blockIdx.x;
+  const int64_t t0 = jobs[j].tile0;
+  const int64_t nt = (jobs[j].ns + kJTile - 1) / kJTile;
+  for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) map[t0 + t] = j;
+}
+
+template <typename K>
+cudaError_t launch_fill_join_tile_job(const JoinJob<K>* d_jobs, int num_jobs, int32_t* d_map,
+                                      cudaStream_t st) {
+  if (num_jobs <= 0) return cudaSuccess;
+  k_fill_join_tile_job<K><<<num_jobs, 128, 0, st>>>(d_jobs, d_map);
   return cudaGetLastError();
 }
 
@@ -368,12 +388,12 @@ cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_ti
                         const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
                         const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
-                        int* d_err, cudaStream_t st) {
+                        int* d_err, cudaStream_t st, const int32_t* d_tile_job) {
   if (total_tiles <= 0) return cudaSuccess;
   const size_t smem = join_smem_bytes<K>();
   k_join<K><<<(unsigned)total_tiles, kThreads, smem, st>>>(
       d_jobs, num_jobs, total_tiles, d_ra, d_rb, d_lookback, d_tile_counter, out, capacity,
-      d_out_base, d_job_out, d_total, d_err);
+      d_out_base, d_job_out, d_total, d_err, d_tile_job);
   return cudaGetLastError();
 }
 
@@ -429,10 +449,13 @@ cudaError_t join_init_attributes() {
 
 #define TJ_INSTANTIATE_JOIN(K)                                                                  \
   template cudaError_t launch_tile_ranges<K>(const JoinJob<K>*, int, int64_t, int64_t*, int64_t*, \
-                                             cudaStream_t);                                     \
+                                             cudaStream_t, const int32_t*);                     \
+  template cudaError_t launch_fill_join_tile_job<K>(const JoinJob<K>*, int, int32_t*,            \
+                                                    cudaStream_t);                              \
   template cudaError_t launch_join<K>(const JoinJob<K>*, int, int64_t, const int64_t*,           \
                                       const int64_t*, uint64_t*, uint32_t*, K*, int64_t,          \
-                                      const int64_t*, int64_t*, int64_t*, int*, cudaStream_t);    \
+                                      const int64_t*, int64_t*, int64_t*, int*, cudaStream_t,     \
+                                      const int32_t*);                                            \
   template cudaError_t launch_fix_job_out<K>(const JoinJob<K>*, int, int64_t, int64_t*,          \
                                              const int64_t*, cudaStream_t);
 TJ_INSTANTIATE_JOIN(int32_t)

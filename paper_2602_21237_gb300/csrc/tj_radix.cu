@@ -76,6 +76,25 @@ __device__ __forceinline__ uint32_t route_of(K key, const K* s_cuts, int ncuts) 
   return (uint32_t)min(pos, ncuts);
 }
 
+// Route through the radix index: the cuts <= key are all cuts before the key's
+// bucket plus those of its bucket that are <= key (a short binary search).
+template <typename K>
+__device__ __forceinline__ uint32_t route_idx(K key, typename UnsignedOf<K>::type lo, int shift,
+                                              const K* s_cuts, const uint16_t* s_tab) {
+  using U = typename UnsignedOf<K>::type;
+  U b = ((U)key - lo) >> shift;
+  if (b > (U)(kRouteBuckets - 1)) b = (U)(kRouteBuckets - 1);
+  int a = s_tab[b], e = s_tab[b + 1];
+  while (a < e) {
+    const int mid = (a + e) >> 1;
+    if (s_cuts[mid] <= key)
+      a = mid + 1;
+    else
+      e = mid;
+  }
+  return (uint32_t)a;
+}
+
 // Exclusive scan of in[0, bins) into out[0, bins) by the whole CTA
 // (bins <= 2 * kThreads).  Ends with a barrier.
 __device__ __forceinline__ void block_excl_scan_bins(const uint32_t* in, uint32_t* out, int bins,
@@ -109,14 +128,14 @@ __device__ __forceinline__ void block_excl_scan_bins(const uint32_t* in, uint32_
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restrict__ jobs,
                                                     int num_jobs, int64_t total_tiles,
-                                                    KeyStats* __restrict__ stats) {
+                                                    KeyStats* __restrict__ stats, int tile) {
   __shared__ unsigned long long s_mn[kWarps], s_mx[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
     const int j = find_job(jobs, num_jobs, t);
     const K* __restrict__ keys = jobs[j].keys;
-    const int64_t row0 = (t - jobs[j].tile0) * kTile;
-    const int64_t row1 = min(jobs[j].n, row0 + kTile);
+    const int64_t row0 = (t - jobs[j].tile0) * tile;
+    const int64_t row1 = min(jobs[j].n, row0 + tile);
     unsigned long long mn = ~0ull, mx = 0ull;
     for (int64_t r = row0 + threadIdx.x; r < row1; r += kThreads) {
       const unsigned long long u = order_u(keys[r]);
@@ -150,27 +169,34 @@ __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restric
 // ---------------------------------------------------------------------------
 // K2: digit histograms of every pass in one read of the keys
 // ---------------------------------------------------------------------------
+// passes x 2^digit_bits never exceeds this (64-bit keys: 8 x 2^8 or 7 x 2^9;
+// 32-bit keys: <= 4 x 2^8 or 3 x 2^10; a route pass: 1 x 2^10)
+constexpr int kHistWords = 4096;
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __restrict__ jobs,
-                                                        int num_jobs, int64_t total_tiles) {
+                                                        int num_jobs, int64_t total_tiles,
+                                                        const int32_t* __restrict__ tile_job,
+                                                        int tile) {
   using U = typename UnsignedOf<K>::type;
-  __shared__ uint32_t s_h[kMaxPasses * kMaxBins];
+  __shared__ uint32_t s_h[kHistWords];
   __shared__ int s_shift[kMaxPasses];
   __shared__ uint32_t s_mask[kMaxPasses];
   __shared__ K s_cuts[kMaxCuts];
-  int cur = -1, passes = 0, ncuts = -1;
+  __shared__ uint16_t s_tab[kRouteBuckets + 1];
+  int cur = -1, passes = 0, ncuts = -1, rshift = 0, hs = 0;
   U lo = 0;
   auto flush = [&](int job) {
     __syncthreads();
     for (int p = 0; p < passes; ++p)
       for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) {
-        const uint32_t c = s_h[p * kMaxBins + d];
+        const uint32_t c = s_h[p * hs + d];
         if (c) atomicAdd(&jobs[job].hist[p * jobs[job].hist_stride + d], c);
       }
   };
   // grid-stride over tiles: one flush per job a CTA touched
   for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    const int j = find_job(jobs, num_jobs, t);
+    const int j = tile_job ? tile_job[t] : find_job(jobs, num_jobs, t);
     if (j != cur) {
       if (cur >= 0) flush(cur);
       __syncthreads();
@@ -178,23 +204,27 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __res
       passes = jobs[j].passes;
       lo = (U)jobs[j].lo;
       ncuts = jobs[j].cuts ? jobs[j].ncuts : -1;
-      if (ncuts >= 0)
+      rshift = jobs[j].route_shift;
+      int mb = 0;
+      for (int p = 0; p < passes; ++p) mb = max(mb, jobs[j].bits[p]);
+      hs = 1 << mb;
+      if (ncuts >= 0) {
         for (int i = threadIdx.x; i < kMaxCuts; i += kThreads) s_cuts[i] = jobs[j].cuts[i];
+        for (int i = threadIdx.x; i <= kRouteBuckets; i += kThreads) s_tab[i] = jobs[j].route_tab[i];
+      }
       if (threadIdx.x < kMaxPasses) {
         s_shift[threadIdx.x] = jobs[j].shift[threadIdx.x];
         s_mask[threadIdx.x] =
             threadIdx.x < passes ? (1u << jobs[j].bits[threadIdx.x]) - 1u : 0u;
       }
-      __syncthreads();
-      for (int p = 0; p < passes; ++p)
-        for (int d = threadIdx.x; d <= (int)s_mask[p]; d += kThreads) s_h[p * kMaxBins + d] = 0;
+      for (int i = threadIdx.x; i < passes * hs; i += kThreads) s_h[i] = 0;
       __syncthreads();
     }
     const K* __restrict__ keys = jobs[j].keys;
-    const int64_t row0 = (t - jobs[j].tile0) * kTile;
-    const int row1 = (int)min((int64_t)kTile, jobs[j].n - row0);
+    const int64_t row0 = (t - jobs[j].tile0) * tile;
+    const int row1 = (int)min((int64_t)tile, jobs[j].n - row0);  // tile <= kTile
     const K* __restrict__ kp = keys + row0;
-    constexpr int kU = kTile / kThreads;  // 16 rows per thread, loads issued together
+    constexpr int kU = kTile / kThreads;  // up to 16 rows per thread, loads issued together
     K kv[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
@@ -206,11 +236,11 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __res
       const int r = threadIdx.x + u * kThreads;
       if (r < row1) {
         if (ncuts >= 0) {
-          atomicAdd(&s_h[route_of<K>(kv[u], s_cuts, ncuts)], 1u);
+          atomicAdd(&s_h[route_idx<K>(kv[u], lo, rshift, s_cuts, s_tab)], 1u);
         } else {
           const U x = (U)kv[u] - lo;
           for (int p = 0; p < passes; ++p)
-            atomicAdd(&s_h[p * kMaxBins + ((uint32_t)(x >> s_shift[p]) & s_mask[p])], 1u);
+            atomicAdd(&s_h[p * hs + ((uint32_t)(x >> s_shift[p]) & s_mask[p])], 1u);
         }
       }
     }
@@ -251,10 +281,12 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 //   keys[kTile] K | ids[kTile] K | warp counters[kSortWarps][bins] u32 |
 //   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
 //   [cut keys[kMaxCuts] K, when the pass routes by a cut table]
+//   [cut keys[kMaxCuts] K, radix index[kRouteBuckets + 1] u16, when routing]
 template <typename K>
-__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route) {
-  return 2 * sizeof(K) * kTile + sizeof(uint32_t) * (size_t)(kSortWarps + 2) * bins +
-         sizeof(long long) * (size_t)bins + (route ? sizeof(K) * kMaxCuts : 0);
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile) {
+  return 2 * sizeof(K) * (size_t)tile + sizeof(uint32_t) * (size_t)(kSortWarps + 2) * bins +
+         sizeof(long long) * (size_t)bins +
+         (route ? sizeof(K) * kMaxCuts + sizeof(uint16_t) * (kRouteBuckets + 8) : 0);
 }
 
 // Exclusive scan of in[0, bins) by a CTA of kSortThreads (bins <= 2 * kSortThreads).
@@ -283,11 +315,13 @@ __device__ __forceinline__ void sort_block_excl_scan(const uint32_t* in, uint32_
   __syncthreads();
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     k_onesweep(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles, int pass,
-               uint32_t* __restrict__ tile_counter, int* __restrict__ err) {
+               uint32_t* __restrict__ tile_counter, int* __restrict__ err,
+               const int32_t* __restrict__ tile_job) {
   using U = typename UnsignedOf<K>::type;
+  constexpr int TILE = kSortThreads * ITEMS;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_warp[kSortWarps];
   __shared__ uint32_t s_t;
@@ -297,12 +331,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   __syncthreads();
   const int64_t t = s_t;
   if (t >= total_tiles) return;
-  const int j = find_job(jobs, num_jobs, t);
+  const int j = tile_job ? tile_job[t] : find_job(jobs, num_jobs, t);
   const RadixJob<K>* J = jobs + j;
   if (pass >= J->passes) return;  // this array needs fewer passes than the batch
   const int64_t lt = t - J->tile0;
-  const int64_t row0 = lt * kTile;
-  const int nvalid = (int)min((int64_t)kTile, J->n - row0);
+  const int64_t row0 = lt * TILE;
+  const int nvalid = (int)min((int64_t)TILE, J->n - row0);
   const int shift = J->shift[pass];
   const int bins = 1 << J->bits[pass];
   const uint32_t mask = (uint32_t)bins - 1u;
@@ -316,32 +350,37 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   const uint32_t* hist = J->hist + pass * J->hist_stride;
 
   K* s_keys = reinterpret_cast<K*>(smem);
-  K* s_vals = s_keys + kTile;
-  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + kTile);
+  K* s_vals = s_keys + TILE;
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + TILE);
   uint32_t* s_count = s_whist + kSortWarps * bins;
   uint32_t* s_excl = s_count + bins;
   long long* s_gbase = reinterpret_cast<long long*>(s_excl + bins);
   K* s_cuts = reinterpret_cast<K*>(s_gbase + bins);
+  uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_cuts + kMaxCuts);
   const int ncuts = J->cuts ? J->ncuts : -1;
-  if (ncuts >= 0)
+  const int rshift = J->route_shift;
+  if (ncuts >= 0) {
     for (int i = tid; i < kMaxCuts; i += kSortThreads) s_cuts[i] = J->cuts[i];
+    for (int i = tid; i <= kRouteBuckets; i += kSortThreads) s_tab[i] = J->route_tab[i];
+  }
   // the digit of a row in this pass: a radix digit of key - lo, or its route
   auto dig = [&](K k) -> uint32_t {
-    return ncuts >= 0 ? route_of<K>(k, s_cuts, ncuts) : digit_of<K>(k, lo, shift, mask);
+    return ncuts >= 0 ? route_idx<K>(k, lo, rshift, s_cuts, s_tab)
+                      : digit_of<K>(k, lo, shift, mask);
   };
 
-  // Warp-striped rows: warp w owns rows [w*32*kItems, (w+1)*32*kItems) of the
+  // Warp-striped rows: warp w owns rows [w*32*ITEMS, (w+1)*32*ITEMS) of the
   // tile; item i covers 32 consecutive rows, so ranks follow row order.
-  const int wbase = warp * 32 * kItems;
-  K key[kItems];
-  K val[kItems];
+  const int wbase = warp * 32 * ITEMS;
+  K key[ITEMS];
+  K val[ITEMS];
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int r = wbase + i * 32 + lane;
     key[i] = r < nvalid ? src_k[r] : K(0);
   }
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int r = wbase + i * 32 + lane;
     val[i] = r < nvalid ? src_v[r] : K(0);
   }
@@ -349,9 +388,9 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   __syncthreads();
 
   // 1. peer groups of equal digits for every item (independent -> pipelined)
-  uint32_t peers[kItems];
+  uint32_t peers[ITEMS];
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int r = wbase + i * 32 + lane;
     const uint32_t d = r < nvalid ? dig(key[i]) : 0xFFFFFFFFu;
     peers[i] = __match_any_sync(0xFFFFFFFFu, d);
@@ -359,9 +398,9 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   // 2. one shared-memory atomicAdd per group, issued by the group's highest
   //    lane; it returns the warp's running count of that digit (items in order)
   uint32_t* wh = s_whist + warp * bins;
-  uint32_t rk[kItems];
+  uint32_t rk[ITEMS];
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int r = wbase + i * 32 + lane;
     rk[i] = 0u;
     if (r < nvalid && (peers[i] >> lane) == 1u)
@@ -370,7 +409,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   // 3. broadcast the group's base and add the rank inside the group
   const uint32_t ltm = lanemask_lt();
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int leader = 31 - __clz(peers[i]);
     const uint32_t base = __shfl_sync(0xFFFFFFFFu, rk[i], leader);
     rk[i] = base + __popc(peers[i] & ltm);
@@ -405,7 +444,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     win[w] = (tid < bins && lt - 1 - w >= 0) ? ld_volatile_u32(lb_base + (lt - 1 - w) * bins + tid)
                                              : 0u;
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const int r = wbase + i * 32 + lane;
     if (r < nvalid) {
       const uint32_t d = dig(key[i]);
@@ -484,19 +523,37 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
 // ---------------------------------------------------------------------------
 template <typename K>
 cudaError_t launch_stats(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                         KeyStats* d_stats, cudaStream_t st) {
+                         KeyStats* d_stats, cudaStream_t st, int tile) {
   if (total_tiles <= 0) return cudaSuccess;
   const int64_t grid = total_tiles < 152 * 8 ? total_tiles : 152 * 8;
-  k_stats<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_stats);
+  k_stats<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_stats, tile);
   return cudaGetLastError();
 }
 
 template <typename K>
 cudaError_t launch_histogram(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int32_t* d_tile_job, int tile) {
   if (total_tiles <= 0) return cudaSuccess;
   const int64_t grid = total_tiles < 152 * 6 ? total_tiles : 152 * 6;
-  k_histogram<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles);
+  k_histogram<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_tile_job,
+                                                      tile);
+  return cudaGetLastError();
+}
+
+template <typename K>
+__global__ void k_fill_tile_job(const RadixJob<K>* __restrict__ jobs, int32_t* __restrict__ map,
+                                int tile) {
+  const int j = blockIdx.x;
+  const int64_t t0 = jobs[j].tile0;
+  const int64_t nt = (jobs[j].n + tile - 1) / tile;
+  for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) map[t0 + t] = j;
+}
+
+template <typename K>
+cudaError_t launch_fill_tile_job(const RadixJob<K>* d_jobs, int num_jobs, int32_t* d_map,
+                                 cudaStream_t st, int tile) {
+  if (num_jobs <= 0) return cudaSuccess;
+  k_fill_tile_job<K><<<num_jobs, 128, 0, st>>>(d_jobs, d_map, tile);
   return cudaGetLastError();
 }
 
@@ -513,30 +570,46 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                             int pass, int max_bits, bool route, uint32_t* d_tile_counter,
-                            int* d_err, cudaStream_t st) {
+                            int* d_err, cudaStream_t st, const int32_t* d_tile_job, int items) {
   if (total_tiles <= 0) return cudaSuccess;
-  const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route);
-  k_onesweep<K><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(d_jobs, num_jobs, total_tiles,
-                                                                   pass, d_tile_counter, d_err);
+  if (items == 4) {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4);
+    k_onesweep<K, 4><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  } else {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route);
+    k_onesweep<K, kItems><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t radix_init_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_onesweep<int32_t>,
+  cudaError_t e = cudaFuncSetAttribute(k_onesweep<int32_t, kItems>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)onesweep_smem_bytes<int32_t>(kMaxBins, true));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_onesweep<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)onesweep_smem_bytes<int64_t>(kMaxBins, true));
+  e = cudaFuncSetAttribute(k_onesweep<int64_t, kItems>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<int64_t>(kMaxBins, true));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_onesweep<int32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kSortThreads * 4));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_onesweep<int64_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kSortThreads * 4));
 }
 
 #define TJ_INSTANTIATE_RADIX(K)                                                                 \
   template cudaError_t launch_stats<K>(const RadixJob<K>*, int, int64_t, KeyStats*,             \
-                                       cudaStream_t);                                           \
-  template cudaError_t launch_histogram<K>(const RadixJob<K>*, int, int64_t, cudaStream_t);     \
+                                       cudaStream_t, int);                                      \
+  template cudaError_t launch_histogram<K>(const RadixJob<K>*, int, int64_t, cudaStream_t,      \
+                                           const int32_t*, int);                                \
+  template cudaError_t launch_fill_tile_job<K>(const RadixJob<K>*, int, int32_t*, cudaStream_t, \
+                                               int);                                            \
   template cudaError_t launch_digit_scan<K>(const RadixJob<K>*, int, int, cudaStream_t);        \
   template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, bool,    \
-                                          uint32_t*, int*, cudaStream_t);
+                                          uint32_t*, int*, cudaStream_t, const int32_t*, int);
 TJ_INSTANTIATE_RADIX(int32_t)
 TJ_INSTANTIATE_RADIX(int64_t)
 

@@ -95,8 +95,19 @@ void worker_main(tj_server* S) {
     } else {
       // the call's working set stays inside the reservation minus its output
       const size_t lib = p.footprint - (size_t)r.out_capacity * 2 * w;
-      res.status = tj_join_inner((tj_dtype)r.dt, r.keys_r, r.ids_r, r.n_r, r.keys_s, r.ids_s,
-                                 r.n_s, lib, r.out_pairs, r.out_capacity, &res.out_count, st);
+      void* out = r.out_pairs;
+      if (!out && r.out_capacity > 0 &&
+          cudaMallocAsync(&out, (size_t)r.out_capacity * 2 * w, st) != cudaSuccess) {
+        out = nullptr;
+        res.status = TJ_ERR_CUDA;
+      }
+      if (res.status == TJ_OK)
+        res.status = tj_join_inner((tj_dtype)r.dt, r.keys_r, r.ids_r, r.n_r, r.keys_s, r.ids_s,
+                                   r.n_s, lib, out, r.out_capacity, &res.out_count, st);
+      if (!r.out_pairs && out) {  // a server-owned output is counted, then released
+        cudaFreeAsync(out, st);
+        cudaStreamSynchronize(st);
+      }
     }
     const Clock::time_point t1 = Clock::now();
     res.latency_ms = std::chrono::duration<double, std::milli>(t1 - p.arrival).count();

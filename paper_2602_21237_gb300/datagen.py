@@ -13,7 +13,8 @@ were the same for both paths; these shapes stand in for them):
   [0, n_r) (optionally scattered over 64 bits by a fixed bijection), S keys
   drawn Zipf(s) over R's keys, the rank -> key map an independent permutation.
 * ``lognormal_mix``  -- 8 log-normal clusters (medians 2^(24+2c), log-sigma
-  0.3 + 0.05c, weight 0.95/8 each) plus 5% uniform noise on [0, 2^40).
+  0.3 + 0.05c, weight 0.95/8 each) plus 5% uniform noise on [0, 2^40); draws
+  at or above 2^40 wrap around modulo 2^40.
 * ``batch_jobs``     -- many joins with |R|, |S| log-uniform, int32 keys
   uniform over [0, 2|R|).
 * ``poisson_arrivals`` -- exponential inter-arrival times of a Poisson stream.
@@ -112,7 +113,9 @@ def lognormal_mix(n: int, seed: int, device="cpu", clusters: int = 8, noise: flo
                        dtype=torch.float64)
     z = torch.randn(n, generator=g, device=device, dtype=torch.float64)
     x = torch.exp(med[comp] + sig[comp] * z)
-    x = torch.round(x).clamp_(0, top - 1).to(torch.int64)
+    # the upper tail of the widest clusters passes 2^key_bits: wrap it around
+    # (clamping would pile ~2% of a cluster onto the single key 2^key_bits - 1)
+    x = torch.remainder(torch.round(x), float(top)).to(torch.int64)
     noise_keys = torch.randint(0, top, (n,), generator=g, device=device, dtype=torch.int64)
     keys = torch.where(comp == clusters, noise_keys, x)
     return keys, torch.arange(n, device=device, dtype=torch.int64)

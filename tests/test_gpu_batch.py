@@ -49,3 +49,17 @@ def test_batch_equals_one_at_a_time():
         one = api.join_inner(d[0][r_off[j]:r_off[j + 1]], d[1][r_off[j]:r_off[j + 1]],
                              d[2][s_off[j]:s_off[j + 1]], d[3][s_off[j]:s_off[j + 1]])
         assert torch.equal(one, pairs[off[j]:off[j + 1]])
+
+
+def test_autotune_keeps_results_and_caches_choice():
+    r_off, s_off, kr, ir, ks, is_ = datagen.batch_jobs(64, 1000, 20000, 91)
+    d = [x.to(DEV) for x in (kr, ir, ks, is_)]
+    exp, eoff = oracle.join_batch(np.array(r_off), np.array(s_off), kr.numpy(), ir.numpy(),
+                                  ks.numpy(), is_.numpy())
+    pairs, off = api.join_batch(r_off, s_off, *d, autotune=True)
+    assert_pairs_equal(pairs, exp)
+    tuned = (api.stats()["tile_rows"], api.stats()["digit_cap"])
+    assert tuned[0] in (2048, 4096) and 6 <= tuned[1] <= 10
+    pairs2, off2 = api.join_batch(r_off, s_off, *d)  # uses the cached choice
+    assert (api.stats()["tile_rows"], api.stats()["digit_cap"]) == tuned
+    assert torch.equal(pairs2, pairs) and np.array_equal(np_of(off2), eoff)
