@@ -55,6 +55,25 @@ std::mutex g_trace_mu;
 bool g_trace_on = false;
 std::vector<TraceRow> g_trace;
 
+// Events are taken from a per-thread pool and returned after use, so tracing
+// costs two cudaEventRecord calls per launch.
+thread_local std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t pool_get() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void pool_put(cudaEvent_t e) {
+  if (e) g_event_pool.push_back(e);
+}
+
 // Per call: event pairs around each launch, resolved after the call's final sync.
 class Tracer {
  public:
@@ -69,8 +88,8 @@ class Tracer {
   }
   ~Tracer() {
     for (auto& p : pend_) {
-      cudaEventDestroy(p.e0);
-      cudaEventDestroy(p.e1);
+      pool_put(p.e0);
+      pool_put(p.e1);
     }
   }
   void begin(const char* name, double bytes) {
@@ -78,9 +97,11 @@ class Tracer {
     Pending p;
     p.name = name;
     p.bytes = bytes;
-    if (cudaEventCreate(&p.e0) != cudaSuccess) return;
-    if (cudaEventCreate(&p.e1) != cudaSuccess) {
-      cudaEventDestroy(p.e0);
+    p.e0 = pool_get();
+    p.e1 = pool_get();
+    if (!p.e0 || !p.e1) {
+      pool_put(p.e0);
+      pool_put(p.e1);
       return;
     }
     cudaEventRecord(p.e0, st_);
@@ -184,6 +205,42 @@ struct Block {
   }
 };
 
+// ---- pinned host staging for job-table uploads (one per thread, grows) ------
+struct Pinned {
+  unsigned char* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;  // last upload from this buffer
+  ~Pinned() {
+    if (ev) cudaEventDestroy(ev);
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local Pinned g_pinned;
+
+cudaEvent_t pinned_event() { return g_pinned.ev; }
+
+// A pinned buffer of at least n bytes whose previous upload has completed.
+cudaError_t pinned_staging(size_t n, unsigned char** out) {
+  cudaError_t e;
+  if (!g_pinned.ev) {
+    e = cudaEventCreateWithFlags(&g_pinned.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaEventSynchronize(g_pinned.ev);
+  if (e != cudaSuccess) return e;
+  if (n > g_pinned.cap) {
+    if (g_pinned.p) cudaFreeHost(g_pinned.p);
+    g_pinned.p = nullptr;
+    g_pinned.cap = 0;
+    const size_t c = std::max(n, (size_t)1 << 20);
+    e = cudaMallocHost((void**)&g_pinned.p, c);
+    if (e != cudaSuccess) return e;
+    g_pinned.cap = c;
+  }
+  *out = g_pinned.p;
+  return cudaSuccess;
+}
+
 // ---- digit plan -----------------------------------------------------------------
 struct Plan {
   uint64_t lo = 0;
@@ -281,7 +338,7 @@ void set_job_buffers(RadixJob<K>& j, const K* in_k, const K* in_v, K* ak, K* av,
 // ---- inner join -------------------------------------------------------------------
 struct Opts {
   int router = TJ_ROUTE_AUTO;
-  int partitions = 512;
+  int partitions = 256;
   int stride = 100;
   int segments = 4096;
   int mlp_steps = 600;
@@ -533,6 +590,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     Carve c;
     const size_t o_k = c.add<K>((size_t)m), o_v = c.add<K>((size_t)m), o_b = c.add<K>((size_t)parts);
     const size_t o_th = c.add<float>(kMlpParams), o_tab = c.add<float>(kMlpTable + 1);
+    const size_t o_edges = c.add<int64_t>(kMaxCuts + 2);
     Block sb;
     TJ_CUDA(sb.alloc(c.off, st));
     TJ_CUDA(launch_sample_gather<K>(kr, m_r, off_r, ks, m_s, off_s, stride, sb.at<K>(o_k),
@@ -579,24 +637,24 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     }
     TJ_CUDA(cudaMemcpyAsync(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K),
                             cudaMemcpyDeviceToHost, st));
-    // radix judge on the sample: balance of equal-width ranges of the same count
-    std::vector<K> samp((size_t)m);
-    TJ_CUDA(cudaMemcpyAsync(samp.data(), sb.at<K>(o_k), samp.size() * sizeof(K),
-                            cudaMemcpyDeviceToHost, st));
-    TJ_CUDA(cudaStreamSynchronize(st));
+    // radix judge on the (sorted) sample: balance of equal-width ranges of the
+    // same count, from bucket edges found by binary search on the device
     {
       const int b = bitlen(range_of<K>(lo, hi));
       int plog = 0;
       while ((2 << plog) <= parts) ++plog;
       const int sh = std::max(0, b - plog);
-      std::vector<int64_t> cnt((size_t)1 << plog, 0);
-      for (K x : samp) {
-        uint64_t d = range_of<K>(lo, x) >> sh;
-        if (d >= cnt.size()) d = cnt.size() - 1;
-        ++cnt[(size_t)d];
-      }
-      const int64_t mx = *std::max_element(cnt.begin(), cnt.end());
-      stats.radix_balance = (double)mx * (double)cnt.size() / (double)std::max<int64_t>(1, m);
+      const int nb = 1 << plog;
+      TJ_CUDA(launch_sorted_bucket_edges<K>(sb.at<K>(o_k), m, lo_bits<K>(lo), sh, nb,
+                                            sb.at<int64_t>(o_edges), st));
+      std::vector<int64_t> edges((size_t)nb + 1);
+      TJ_CUDA(cudaMemcpyAsync(edges.data(), sb.at<int64_t>(o_edges), edges.size() * 8,
+                              cudaMemcpyDeviceToHost, st));
+      TJ_CUDA(cudaStreamSynchronize(st));
+      int64_t mx = 0;
+      for (int d = 0; d < nb; ++d)
+        mx = std::max(mx, (d + 1 < nb ? edges[(size_t)d + 1] : m) - edges[(size_t)d]);
+      stats.radix_balance = (double)mx * (double)nb / (double)std::max<int64_t>(1, m);
     }
     cuts = make_cuts<K>(bnd);
   } else {  // TJ_ROUTE_RADIX
@@ -626,24 +684,28 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
 
   // ---- 2. route pass into staging, in chunks whose look-back fits the budget ----
-  // radix index over the cuts: bucket b = (key - lo) >> rshift
+  // log-scale index over the cuts (see RadixJob::route_tab): tab[b] = number of
+  // cuts below the first key of bucket b
   const uint64_t krange = range_of<K>(lo, hi);
-  const int kbits = bitlen(krange);
-  const int rshift = std::max(0, kbits - 12);
   std::vector<uint16_t> tab(kRouteBuckets + 1);
-  {
-    size_t c = 0;
-    for (int bkt = 0; bkt < kRouteBuckets; ++bkt) {
-      const uint64_t off = (uint64_t)bkt << rshift;
-      if (rshift < 64 && off <= krange) {
-        const K start = (K)(lo_bits<K>(lo) + off);
-        while (c < cuts.size() && cuts[c] < start) ++c;
-        tab[(size_t)bkt] = (uint16_t)c;
-      } else {
-        tab[(size_t)bkt] = (uint16_t)ncuts;
-      }
+  for (int bkt = 0; bkt <= kRouteBuckets; ++bkt) {
+    uint64_t start;  // smallest x = key - lo whose bucket is >= bkt
+    bool beyond = bkt == kRouteBuckets;
+    if (bkt < 32) {
+      start = (uint64_t)bkt;
+    } else if (bkt <= 192) {
+      start = 32;
+    } else {
+      const int e = bkt >> 5, mnt = bkt & 31;
+      start = e > 64 ? 0 : ((uint64_t)(32 + mnt) << (e - 6));
+      if (e > 64) beyond = true;
     }
-    tab[kRouteBuckets] = (uint16_t)ncuts;
+    if (beyond || start > krange) {
+      tab[(size_t)bkt] = (uint16_t)ncuts;
+    } else {
+      const K sk = (K)(lo_bits<K>(lo) + start);
+      tab[(size_t)bkt] = (uint16_t)(std::lower_bound(cuts.begin(), cuts.end(), sk) - cuts.begin());
+    }
   }
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
@@ -722,7 +784,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     x.cuts = stg.at<K>(o_cuts);
     x.ncuts = ncuts;
     x.route_tab = stg.at<uint16_t>(o_tab);
-    x.route_shift = rshift;
   }
   for (auto& g : cgroups) {
     int64_t t = 0, lbw = 0;
@@ -820,15 +881,17 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     q.ws = (int64_t)nb * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
            (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * bins * 4 +
            ceil_div(q.ns, kJTile) * 28 + (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * 4 +
-           2 * (int64_t)sizeof(RadixJob<K>) +
-           (int64_t)sizeof(JoinJob<K>) + 2 * (int64_t)std::max(1, q.plan.passes) * bins * 4 + 4096;
+           2 * (int64_t)std::max(1, q.plan.passes) * bins * 4 + 4096;
     live_rows += q.nr + q.ns;
     P.push_back(q);
   }
   if (r_at != nr || s_at != ns) return set_err(TJ_ERR_INTERNAL, "route counts do not add up");
   stats.max_partition = maxrows;
   stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
-  const int64_t fixed = (int64_t)(cc.off - staging) + 4096;  // route structures (look-back incl.)
+  // route structures (look-back included) and every group's job tables
+  const int64_t fixed = (int64_t)(cc.off - staging) + 4096 +
+                        (int64_t)P.size() * (2 * (int64_t)sizeof(RadixJob<K>) +
+                                             (int64_t)sizeof(JoinJob<K>) + 64);
   const int64_t room = budget ? (int64_t)budget - fixed : INT64_MAX;
   if (room <= 0) return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes",
                                 budget, (long long)fixed);
@@ -852,15 +915,31 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   stats.scratch_peak = (int64_t)(cc.off - staging) + ws_max;
 
   // ---- 4. one batched sort + align per group ----
-  // Group layout in the working block: job tables | sort buffers of every batch
-  // | histograms of every batch | look-back words of every batch | join state.
+  // Group layout in the working block: sort buffers of every batch | histograms
+  // | look-back words | join state | tile maps.  Every group's job tables are
+  // built first and uploaded once (from pinned memory), so the group loop
+  // below only enqueues kernels and memsets.
+  struct GroupPlan {
+    size_t first, nj;
+    size_t rj_at, jj_at;  // offsets into the uploaded tables
+    size_t o_hist, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
+    size_t hist_words, lb_words;
+    int64_t tiles, jtiles;
+    int P, maxbits;
+    double rows, prow[kMaxPasses];
+  };
   Block wk;
   TJ_CUDA(wk.alloc((size_t)std::max<int64_t>(ws_max, 256), st));
+  std::vector<RadixJob<K>> all_rj;
+  std::vector<JoinJob<K>> all_jj;
+  std::vector<GroupPlan> plans;
   int maxp = 0;
   for (auto& g : groups) {
-    const size_t nj = g.second - g.first;
+    GroupPlan gp = {};
+    gp.first = g.first;
+    gp.nj = g.second - g.first;
+    const size_t nj = gp.nj;
     Carve gc;
-    const size_t o_gj = gc.add<RadixJob<K>>(2 * nj), o_gjj = gc.add<JoinJob<K>>(nj);
     std::vector<size_t> o_buf(nj * 8, 0);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
@@ -871,30 +950,27 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         o_buf[i * 8 + 4 * b2 + 3] = gc.add<K>((size_t)q.ns);
       }
     }
-    int P_g = 0, maxbits = 0;
-    size_t hist_words = 0, lb_words = 0;
     std::vector<size_t> hist_at(nj * 2), lb_at(nj * 2);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
       const size_t bins = (size_t)1 << q.plan.max_bits;
       for (int side = 0; side < 2; ++side) {
-        hist_at[i * 2 + side] = hist_words;
-        hist_words += (size_t)std::max(1, q.plan.passes) * bins;
-        lb_at[i * 2 + side] = lb_words;
-        lb_words += (size_t)ceil_div(side ? q.ns : q.nr, kTile) * bins;
+        hist_at[i * 2 + side] = gp.hist_words;
+        gp.hist_words += (size_t)std::max(1, q.plan.passes) * bins;
+        lb_at[i * 2 + side] = gp.lb_words;
+        gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, kTile) * bins;
       }
-      P_g = std::max(P_g, q.plan.passes);
-      maxbits = std::max(maxbits, q.plan.max_bits);
+      gp.P = std::max(gp.P, q.plan.passes);
+      gp.maxbits = std::max(gp.maxbits, q.plan.max_bits);
+      for (int p = 0; p < q.plan.passes; ++p) gp.prow[p] += (double)(q.nr + q.ns);
     }
-    const size_t o_hist_g = gc.add<uint32_t>(std::max<size_t>(hist_words, 1));
-    const size_t o_lb_g = gc.add<uint32_t>(std::max<size_t>(lb_words, 1));
-    std::vector<RadixJob<K>> rj;
-    std::vector<JoinJob<K>> jj;
-    int64_t tiles = 0, jtiles = 0;
-    double rows = 0;
+    gp.o_hist = gc.add<uint32_t>(std::max<size_t>(gp.hist_words, 1));
+    gp.o_lb = gc.add<uint32_t>(std::max<size_t>(gp.lb_words, 1));
+    gp.rj_at = all_rj.size();
+    gp.jj_at = all_jj.size();
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
-      rows += (double)(q.nr + q.ns);
+      gp.rows += (double)(q.nr + q.ns);
       const K* res[4];
       for (int side = 0; side < 2; ++side) {
         RadixJob<K> x;
@@ -904,19 +980,19 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         const K* v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
         x.keys = k0;
         x.n = n;
-        x.tile0 = tiles;
-        tiles += ceil_div(n, kTile);
+        x.tile0 = gp.tiles;
+        gp.tiles += ceil_div(n, kTile);
         set_job_plan(x, q.plan);
         x.hist_stride = 1 << q.plan.max_bits;
-        x.hist = wk.at<uint32_t>(o_hist_g) + hist_at[i * 2 + side];
-        x.lookback = wk.at<uint32_t>(o_lb_g) + lb_at[i * 2 + side];
+        x.hist = wk.at<uint32_t>(gp.o_hist) + hist_at[i * 2 + side];
+        x.lookback = wk.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
         const int nb = std::min(q.plan.passes, 2);
         K* ak = nb > 0 ? wk.at<K>(o_buf[i * 8 + 2 * side]) : nullptr;
         K* av = nb > 0 ? wk.at<K>(o_buf[i * 8 + 2 * side + 1]) : nullptr;
         K* bk = nb > 1 ? wk.at<K>(o_buf[i * 8 + 4 + 2 * side]) : nullptr;
         K* bv = nb > 1 ? wk.at<K>(o_buf[i * 8 + 4 + 2 * side + 1]) : nullptr;
         set_job_buffers(x, k0, v0, ak, av, bk, bv, &res[2 * side], &res[2 * side + 1]);
-        rj.push_back(x);
+        all_rj.push_back(x);
       }
       JoinJob<K> y;
       y.rk = res[0];
@@ -925,55 +1001,69 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       y.sk = res[2];
       y.sv = res[3];
       y.ns = q.ns;
-      y.tile0 = jtiles;
-      jtiles += ceil_div(q.ns, kJTile);
-      jj.push_back(y);
+      y.tile0 = gp.jtiles;
+      gp.jtiles += ceil_div(q.ns, kJTile);
+      all_jj.push_back(y);
     }
-    const size_t o_ra = gc.add<int64_t>((size_t)jtiles), o_rb = gc.add<int64_t>((size_t)jtiles);
-    const size_t o_jlb = gc.add<uint64_t>((size_t)jtiles);
-    const size_t o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(tiles, 1));
-    const size_t o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(jtiles, 1));
+    gp.o_ra = gc.add<int64_t>((size_t)gp.jtiles);
+    gp.o_rb = gc.add<int64_t>((size_t)gp.jtiles);
+    gp.o_jlb = gc.add<uint64_t>((size_t)gp.jtiles);
+    gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
+    gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     if ((int64_t)gc.off > std::max<int64_t>(ws_max, 256))
       return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, working block has %lld", gc.off,
                      (long long)ws_max);
-    maxp = std::max(maxp, P_g);
-    RadixJob<K>* d_gj = wk.at<RadixJob<K>>(o_gj);
-    JoinJob<K>* d_gjj = wk.at<JoinJob<K>>(o_gjj);
-    TJ_CUDA(cudaMemcpyAsync(d_gj, rj.data(), rj.size() * sizeof(RadixJob<K>),
-                            cudaMemcpyHostToDevice, st));
-    TJ_CUDA(cudaMemcpyAsync(d_gjj, jj.data(), jj.size() * sizeof(JoinJob<K>),
-                            cudaMemcpyHostToDevice, st));
+    maxp = std::max(maxp, gp.P);
+    plans.push_back(gp);
+  }
+  // one upload of every group's job tables
+  const size_t rj_bytes = all_rj.size() * sizeof(RadixJob<K>);
+  const size_t jj_bytes = all_jj.size() * sizeof(JoinJob<K>);
+  Block tbl;
+  TJ_CUDA(tbl.alloc(rj_bytes + jj_bytes + 256, st));
+  {
+    unsigned char* h = nullptr;
+    TJ_CUDA(pinned_staging(rj_bytes + jj_bytes, &h));
+    memcpy(h, all_rj.data(), rj_bytes);
+    memcpy(h + rj_bytes, all_jj.data(), jj_bytes);
+    TJ_CUDA(cudaMemcpyAsync(tbl.p, h, rj_bytes + jj_bytes, cudaMemcpyHostToDevice, st));
+    TJ_CUDA(cudaEventRecord(pinned_event(), st));  // the staging buffer is busy until here
+  }
+  RadixJob<K>* d_rj_all = tbl.at<RadixJob<K>>(0);
+  JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + rj_bytes);
+  stats.scratch_peak += (int64_t)(rj_bytes + jj_bytes);
+  for (const GroupPlan& gp : plans) {
+    const size_t nj = gp.nj;
+    RadixJob<K>* d_gj = d_rj_all + gp.rj_at;
+    JoinJob<K>* d_gjj = d_jj_all + gp.jj_at;
     TJ_CUDA(cudaMemsetAsync(d_counters, 0, (kMaxPasses + 1) * sizeof(uint32_t), st));
-    int32_t* d_tmap = wk.at<int32_t>(o_tmap);
-    int32_t* d_jmap = wk.at<int32_t>(o_jmap);
+    int32_t* d_tmap = wk.at<int32_t>(gp.o_tmap);
+    int32_t* d_jmap = wk.at<int32_t>(gp.o_jmap);
     TJ_CUDA(launch_fill_tile_job<K>(d_gj, (int)(2 * nj), d_tmap, st));
     TJ_CUDA(launch_fill_join_tile_job<K>(d_gjj, (int)nj, d_jmap, st));
-    if (P_g > 0) {
-      TJ_CUDA(cudaMemsetAsync(wk.p + o_hist_g, 0, hist_words * sizeof(uint32_t), st));
-      tr.begin("histogram", w * rows);
-      TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), tiles, st, d_tmap));
+    if (gp.P > 0) {
+      TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_hist, 0, gp.hist_words * sizeof(uint32_t), st));
+      tr.begin("histogram", w * gp.rows);
+      TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), gp.tiles, st, d_tmap));
       tr.end();
-      TJ_CUDA(launch_digit_scan<K>(d_gj, (int)(2 * nj), P_g, st));
-      for (int p = 0; p < P_g; ++p) {
-        double prow = 0;
-        for (size_t i = 0; i < nj; ++i)
-          if (P[g.first + i].plan.passes > p)
-            prow += (double)(P[g.first + i].nr + P[g.first + i].ns);
-        TJ_CUDA(cudaMemsetAsync(wk.p + o_lb_g, 0, lb_words * sizeof(uint32_t), st));
-        tr.begin("onesweep", 4.0 * w * prow);
-        TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), tiles, p, maxbits, false, d_counters + p,
-                                   d_err, st, d_tmap));
+      TJ_CUDA(launch_digit_scan<K>(d_gj, (int)(2 * nj), gp.P, st));
+      for (int p = 0; p < gp.P; ++p) {
+        TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_lb, 0, gp.lb_words * sizeof(uint32_t), st));
+        tr.begin("onesweep", 4.0 * w * gp.prow[p]);
+        TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
+                                   d_counters + p, d_err, st, d_tmap));
         tr.end();
       }
     }
-    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, jtiles, wk.at<int64_t>(o_ra),
-                                  wk.at<int64_t>(o_rb), st, d_jmap));
-    TJ_CUDA(cudaMemsetAsync(wk.at<uint64_t>(o_jlb), 0, (size_t)std::max<int64_t>(jtiles, 1) * 8,
-                            st));
-    tr.begin("join", 2.0 * w * rows);
-    TJ_CUDA(launch_join<K>(d_gjj, (int)nj, jtiles, wk.at<int64_t>(o_ra), wk.at<int64_t>(o_rb),
-                           wk.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, d_base,
-                           nullptr, d_total, d_err, st, d_jmap));
+    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
+                                  wk.at<int64_t>(gp.o_rb), st, d_jmap));
+    TJ_CUDA(cudaMemsetAsync(wk.at<uint64_t>(gp.o_jlb), 0,
+                            (size_t)std::max<int64_t>(gp.jtiles, 1) * 8, st));
+    tr.begin("join", 2.0 * w * gp.rows);
+    TJ_CUDA(launch_join<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
+                           wk.at<int64_t>(gp.o_rb), wk.at<uint64_t>(gp.o_jlb),
+                           d_counters + kMaxPasses, out, cap, d_base, nullptr, d_total, d_err, st,
+                           d_jmap));
     tr.end();
     TJ_CUDA(launch_add_base(d_base, d_total, st));
   }

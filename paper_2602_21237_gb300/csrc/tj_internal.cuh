@@ -18,6 +18,9 @@ constexpr int kWarps = kThreads / 32;
 #ifndef TJ_SORT_THREADS
 #define TJ_SORT_THREADS 512
 #endif
+#ifndef TJ_ONESWEEP_PF  // 1: persistent onesweep with TMA prefetch for 4096-row tiles
+#define TJ_ONESWEEP_PF 0
+#endif
 #ifndef TJ_SORT_MINB
 #define TJ_SORT_MINB 2
 #endif
@@ -32,7 +35,8 @@ constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass
 constexpr int kJTile = 2048;                // S rows per join tile
-constexpr int kRCap = 2048;                 // R rows a join tile keeps on chip
+constexpr int kRCap = 2048;                 // R rows a join tile keeps on chip at once
+constexpr int kMaxChunks = 4;               // R chunks a join tile aligns on chip
 constexpr int kHTSlots = 4096;              // on-chip hash table slots (load <= 0.5)
 
 // ---- decoupled look-back words (30-bit counts) ----------------------------
@@ -47,7 +51,7 @@ constexpr uint64_t kValMask64 = (1ull << 62) - 1ull;
 constexpr int kSpinLimit = 1 << 22;
 // key-range partitions of one route pass: cuts <= 1023 -> digits of <= 10 bits
 constexpr int kMaxCuts = 1024;
-constexpr int kRouteBuckets = 4096;
+constexpr int kRouteBuckets = 65 * 32;  // b(x) < 32 * 65
 // predecessors read per look-back round trip
 constexpr int kLookWindow = 8;
 
@@ -78,10 +82,11 @@ struct RadixJob {
   // number of cut keys <= key, i.e. the index of its key-range partition.
   const K* cuts;        // sorted cut keys, padded to kMaxCuts with the key type's max
   int32_t ncuts;        // real cuts (<= kMaxCuts - 1); partitions = ncuts + 1
-  // Radix index over the cuts: bucket b = (key - lo) >> route_shift (clamped to
-  // kRouteBuckets - 1) holds cuts [route_tab[b], route_tab[b + 1]).
+  // Log-scale index over the cuts: with x = key - lo, bucket b(x) = x for
+  // x < 32, else 32 * bitlen(x) + the 5 bits below x's leading one; bucket b
+  // holds cuts [route_tab[b], route_tab[b + 1]).  Fine-grained at every
+  // magnitude, so clustered keys still find their cut in a few steps.
   const uint16_t* route_tab;  // kRouteBuckets + 1 entries
-  int32_t route_shift;
 };
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).
@@ -151,6 +156,9 @@ cudaError_t launch_sample_gather(const K* a, int64_t ma, int64_t off_a, const K*
 template <typename K>
 cudaError_t launch_quantiles(const K* sorted, int64_t m, int G, int first, int last, int step,
                              K* out, cudaStream_t st);
+template <typename K>
+cudaError_t launch_sorted_bucket_edges(const K* sorted, int64_t m, uint64_t lo, int shift, int nb,
+                                       int64_t* edges, cudaStream_t st);
 template <typename K>
 cudaError_t launch_fix_job_out(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                                int64_t* d_job_out, const int64_t* d_total, cudaStream_t st);

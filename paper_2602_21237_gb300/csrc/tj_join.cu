@@ -142,7 +142,6 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int64_t lt = t - J.tile0;
   const int64_t row0 = lt * kJTile;
   const int nv = (int)min((int64_t)kJTile, J.ns - row0);
-  const bool small = nrr <= kRCap;
   const K* __restrict__ sk_g = J.sk + row0;
   const K* __restrict__ sv_g = J.sv + row0;
   const K* __restrict__ rk_g = J.rk + a;
@@ -157,43 +156,84 @@ __global__ void __launch_bounds__(kThreads, 3)
     sid[u] = q < nv ? sv_g[q] : K(0);
   }
   for (int q = tid; q < nv; q += kThreads) s_sk[q] = sk_g[q];
-  if (small) {
-    for (int i = tid; i < (int)nrr; i += kThreads) s_rk[i] = rk_g[i];
-    for (int i = tid; i < kHTSlots; i += kThreads) s_ht[i] = kHTEmpty;
-  }
-  __syncthreads();
 
-  if (small) {
-    // insert the first row of every run of equal keys; keys are distinct, so
-    // an occupied slot is never this key and insertion needs no comparison
-    for (int i = tid; i < (int)nrr; i += kThreads) {
-      if (i == 0 || s_rk[i] != s_rk[i - 1]) {
-        uint32_t h = ht_hash(s_rk[i]);
-        while (atomicCAS(&s_ht[h], kHTEmpty, (uint32_t)i | 0xFFFF0000u) != kHTEmpty)
-          h = (h + 1) & (kHTSlots - 1);
+  // Probe: match count and run start of every S row of the tile.  The tile's
+  // R range is aligned chunk by chunk (kRCap rows each, up to kMaxChunks)
+  // through the on-chip table; a run of equal keys that straddles chunks adds
+  // up.  Tiles whose R range is wider (S sparse against R) binary-search R in
+  // global memory instead.
+  const int64_t nchunks = (nrr + kRCap - 1) / kRCap;
+  uint32_t cnt[kRows], start[kRows];
+#pragma unroll
+  for (int u = 0; u < kRows; ++u) cnt[u] = start[u] = 0u;
+  if (nchunks <= kMaxChunks) {
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int c0 = (int)(c * kRCap);
+      const int nc = (int)min((int64_t)kRCap, nrr - c0);
+      __syncthreads();  // the previous chunk's probes are done
+      for (int i = tid; i < nc; i += kThreads) s_rk[i] = rk_g[c0 + i];
+      for (int i = tid; i < kHTSlots; i += kThreads) s_ht[i] = kHTEmpty;
+      __syncthreads();
+      // insert the first row of every run of equal keys; keys are distinct, so
+      // an occupied slot is never this key and insertion needs no comparison
+      for (int i = tid; i < nc; i += kThreads) {
+        if (i == 0 || s_rk[i] != s_rk[i - 1]) {
+          uint32_t h = ht_hash(s_rk[i]);
+          while (atomicCAS(&s_ht[h], kHTEmpty, (uint32_t)i | 0xFFFF0000u) != kHTEmpty)
+            h = (h + 1) & (kHTSlots - 1);
+        }
       }
-    }
-    __syncthreads();
-    // the last row of every run records the run's end
-    for (int i = tid; i < (int)nrr; i += kThreads) {
-      if (i == (int)nrr - 1 || s_rk[i] != s_rk[i + 1]) {
-        const K key = s_rk[i];
+      __syncthreads();
+      // the last row of every run records the run's end
+      for (int i = tid; i < nc; i += kThreads) {
+        if (i == nc - 1 || s_rk[i] != s_rk[i + 1]) {
+          const K key = s_rk[i];
+          uint32_t h = ht_hash(key);
+          while (true) {
+            const uint32_t w = s_ht[h];
+            if (s_rk[w & 0xFFFFu] == key) {
+              s_ht[h] = (w & 0xFFFFu) | ((uint32_t)(i + 1) << 16);
+              break;
+            }
+            h = (h + 1) & (kHTSlots - 1);
+          }
+        }
+      }
+      __syncthreads();
+      const K cf = s_rk[0], cl = s_rk[nc - 1];
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        const int q = tid + u * kThreads;
+        if (q >= nv) continue;
+        const K key = s_sk[q];
+        if (key < cf || cl < key) continue;
         uint32_t h = ht_hash(key);
         while (true) {
           const uint32_t w = s_ht[h];
-          if (s_rk[w & 0xFFFFu] == key) {
-            s_ht[h] = (w & 0xFFFFu) | ((uint32_t)(i + 1) << 16);
+          if (w == kHTEmpty) break;
+          const uint32_t f = w & 0xFFFFu;
+          if (s_rk[f] == key) {
+            if (cnt[u] == 0u) start[u] = (uint32_t)c0 + f;
+            cnt[u] += (w >> 16) - f;
             break;
           }
           h = (h + 1) & (kHTSlots - 1);
         }
       }
     }
-    __syncthreads();
+  } else {
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      const int q = tid + u * kThreads;
+      if (q >= nv) continue;
+      const K key = s_sk[q];
+      const int64_t lo = lower_bound_g(rk_g, nrr, key);
+      const int64_t hi = upper_bound_g(rk_g, nrr, key);
+      start[u] = (uint32_t)lo;
+      cnt[u] = (uint32_t)(hi - lo);
+    }
   }
-
-  // probe: match count and run start of every S row of the tile; the R id of
-  // the first match is gathered right away (used when writing)
+  // the R id of each row's first match is gathered right away (used when writing)
   int mymax = 0;
   K rid[kRows];
 #pragma unroll
@@ -201,31 +241,10 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int q = tid + u * kThreads;
     rid[u] = K(0);
     if (q >= nv) continue;
-    const K key = s_sk[q];
-    uint32_t cnt = 0, start = 0;
-    if (small) {
-      uint32_t h = ht_hash(key);
-      while (true) {
-        const uint32_t w = s_ht[h];
-        if (w == kHTEmpty) break;
-        const uint32_t f = w & 0xFFFFu;
-        if (s_rk[f] == key) {
-          start = f;
-          cnt = (w >> 16) - f;
-          break;
-        }
-        h = (h + 1) & (kHTSlots - 1);
-      }
-    } else {
-      const int64_t lo = lower_bound_g(rk_g, nrr, key);
-      const int64_t hi = upper_bound_g(rk_g, nrr, key);
-      start = (uint32_t)lo;
-      cnt = (uint32_t)(hi - lo);
-    }
-    s_off[q] = cnt;
-    s_rs[q] = start;
-    if (cnt) rid[u] = rv_g[start];
-    mymax = max(mymax, (int)cnt);
+    s_off[q] = cnt[u];
+    s_rs[q] = start[u];
+    if (cnt[u]) rid[u] = rv_g[start[u]];
+    mymax = max(mymax, (int)cnt[u]);
   }
   if (mymax > 1) atomicMax(&s_maxcnt, mymax);
   __syncthreads();

@@ -38,6 +38,40 @@ __global__ void k_quantiles(const K* __restrict__ sorted, int64_t m, int G, int 
   out[i] = sorted[idx];
 }
 
+// edges[d] = number of sorted sample keys below lo + d * 2^shift, d = 0..nb
+// (the balance of equal-width key ranges, judged on the sample)
+template <typename K>
+__global__ void k_sorted_bucket_edges(const K* __restrict__ sorted, int64_t m, uint64_t lo,
+                                      int shift, int nb, int64_t* __restrict__ edges) {
+  using U = typename UnsignedOf<K>::type;
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d > nb) return;
+  const unsigned long long off = shift >= 64 ? 0ull : ((unsigned long long)d << shift);
+  const bool past = d > 0 && (shift >= 64 || (off >> shift) != (unsigned long long)d ||
+                              off > (unsigned long long)(U)(~(U)0));
+  int64_t a = 0, b = m;  // first index with (key - lo) >= off
+  if (past) {
+    a = m;
+  } else {
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if ((unsigned long long)(U)((U)sorted[mid] - (U)lo) < off)
+        a = mid + 1;
+      else
+        b = mid;
+    }
+  }
+  edges[d] = a;
+}
+
+template <typename K>
+cudaError_t launch_sorted_bucket_edges(const K* sorted, int64_t m, uint64_t lo, int shift, int nb,
+                                       int64_t* edges, cudaStream_t st) {
+  k_sorted_bucket_edges<K><<<(nb + 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+      sorted, m, lo, shift, nb, edges);
+  return cudaGetLastError();
+}
+
 template <typename K>
 cudaError_t launch_sample_gather(const K* a, int64_t ma, int64_t off_a, const K* b, int64_t mb,
                                  int64_t off_b, int stride, K* out_k, K* out_v, cudaStream_t st) {
@@ -61,7 +95,9 @@ cudaError_t launch_quantiles(const K* sorted, int64_t m, int G, int first, int l
 #define TJ_INSTANTIATE_LEARNED(K)                                                                \
   template cudaError_t launch_sample_gather<K>(const K*, int64_t, int64_t, const K*, int64_t,    \
                                                int64_t, int, K*, K*, cudaStream_t);              \
-  template cudaError_t launch_quantiles<K>(const K*, int64_t, int, int, int, int, K*, cudaStream_t);
+  template cudaError_t launch_quantiles<K>(const K*, int64_t, int, int, int, int, K*, cudaStream_t); \
+  template cudaError_t launch_sorted_bucket_edges<K>(const K*, int64_t, uint64_t, int, int,      \
+                                                     int64_t*, cudaStream_t);
 TJ_INSTANTIATE_LEARNED(int32_t)
 TJ_INSTANTIATE_LEARNED(int64_t)
 

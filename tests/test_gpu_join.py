@@ -147,3 +147,17 @@ def test_nondefault_stream():
         got = api.join_inner(*d, stream=st)
     st.synchronize()
     assert_pairs_equal(got, oracle.join_inner(kr.numpy(), ir.numpy(), ks.numpy(), is_.numpy()))
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
+@pytest.mark.parametrize("dup", [1, 3])
+def test_r_range_spans_several_chunks(dtype, dup):
+    # each 2048-row S tile spans 2-4 chunks of 2048 sorted R rows; with dup > 1
+    # runs of equal R keys straddle chunk boundaries
+    g = torch.Generator().manual_seed(40 + dup)
+    dom = 4000
+    kr = torch.randint(0, dom, (dom * dup,), generator=g).to(dtype)
+    ks = torch.randint(0, dom, (5000,), generator=g).to(dtype)
+    ir = torch.arange(kr.numel(), dtype=dtype)
+    is_ = torch.arange(ks.numel(), dtype=dtype)
+    check(kr, ir, ks, is_)
