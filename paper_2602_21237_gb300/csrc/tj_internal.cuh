@@ -18,9 +18,6 @@ constexpr int kWarps = kThreads / 32;
 #ifndef TJ_SORT_THREADS
 #define TJ_SORT_THREADS 512
 #endif
-#ifndef TJ_ONESWEEP_PF  // 1: persistent onesweep with TMA prefetch for 4096-row tiles
-#define TJ_ONESWEEP_PF 0
-#endif
 #ifndef TJ_SORT_MINB
 #define TJ_SORT_MINB 2
 #endif

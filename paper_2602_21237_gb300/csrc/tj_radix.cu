@@ -6,11 +6,12 @@
 //   k_histogram  : the counts of every digit of every pass, in one read of the
 //                  keys (per-CTA shared-memory histograms merged into global).
 //   k_digit_scan : exclusive scan of each pass's digit counts (digit bases).
-//   k_onesweep   : one digit pass: a tile of 4096 rows is ranked stably inside
-//                  the CTA (warp __match_any_sync groups + per-warp counters),
-//                  its per-digit counts are published to a decoupled look-back
-//                  chain, and the rows are scattered through shared memory so
-//                  that each digit's run is written contiguously.
+//   k_onesweep   : one digit pass: a tile of 4096 rows is copied to shared
+//                  memory, publishes its digit counts to a decoupled
+//                  look-back chain, is ranked stably inside the CTA
+//                  (ballot-matched digit groups + per-warp counters), and is
+//                  written out in tile-sorted order so that each digit's run
+//                  lands contiguously.
 //
 // Every kernel takes an array of jobs so that one launch serves any number of
 // arrays (both sides of a join, or thousands of joins of a batch).
@@ -277,17 +278,21 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 // ---------------------------------------------------------------------------
 // K4: one onesweep digit pass
 // ---------------------------------------------------------------------------
-// Shared memory (bins = 2^bits of this pass, set at launch):
-//   keys[kTile] K | ids[kTile] K | warp counters[kSortWarps][bins] u32 |
+// Shared memory (bins = 2^bits of this pass, set at launch; hb = ceil(bins/2)):
+//   keys[tile] K | ids[tile] K          rows in input order (never moved)
+//   src[tile] u16                       input row of each tile-sorted slot
+//   warp counters[kSortWarps][hb] u32   two 16-bit digit counters per word
 //   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
-//   [cut keys[kMaxCuts] K, when the pass routes by a cut table]
-//   [cut keys[bins] K, radix index[kRouteBuckets + 1] u16, when routing: a
-//    route pass has at most bins - 1 cuts]
+//   [route passes only: cut keys[bins] K | radix index[kRouteBuckets + 8] u16 |
+//    digit of each tile-sorted slot[tile] u16]   (a route pass has < bins cuts)
 template <typename K>
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile) {
-  return 2 * sizeof(K) * (size_t)tile + sizeof(uint32_t) * (size_t)(kSortWarps + 2) * bins +
-         sizeof(long long) * (size_t)bins +
-         (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) : 0);
+  return 2 * sizeof(K) * (size_t)tile + sizeof(uint16_t) * (size_t)tile +
+         sizeof(uint32_t) * (size_t)kSortWarps * (size_t)((bins + 1) / 2) +
+         sizeof(uint32_t) * 2 * (size_t)bins + sizeof(long long) * (size_t)bins +
+         (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
+                      sizeof(uint16_t) * (size_t)tile
+                : 0);
 }
 
 // Exclusive scan of in[0, bins) by a CTA of kSortThreads (bins <= 2 * kSortThreads).
@@ -316,6 +321,114 @@ __device__ __forceinline__ void sort_block_excl_scan(const uint32_t* in, uint32_
   __syncthreads();
 }
 
+// Sum look-back words v[0..W) (newest predecessor first) into `prefix` up to
+// and including the first inclusive word; stop early at a predecessor that
+// has published nothing yet.  Returns the number of words consumed.
+template <int W>
+__device__ __forceinline__ int lookback_consume(const uint32_t (&v)[W], uint32_t& prefix,
+                                                bool& done) {
+  int used = 0;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    if (used != w) break;
+    const uint32_t f = v[w] & ~kValMask;
+    if (f == 0u) break;
+    acc += v[w] & kValMask;
+    ++used;
+    if (f == kFlagInc) {
+      done = true;
+      break;
+    }
+  }
+  prefix += acc;
+  return used;
+}
+
+// Asynchronous global -> shared copy of n elements of K (no registers held):
+// 16-byte chunks when both ends allow it, else one element per copy.
+template <typename K>
+__device__ __forceinline__ void copy_rows_async(K* dst, const K* __restrict__ src, int n) {
+  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
+  if ((((uintptr_t)src) & 15u) == 0) {
+    constexpr int kPer = 16 / (int)sizeof(K);
+    const int chunks = n / kPer;
+    for (int c = threadIdx.x; c < chunks; c += kSortThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst + 16u * c),
+                   "l"(src + c * kPer)
+                   : "memory");
+    for (int i = chunks * kPer + threadIdx.x; i < n; i += kSortThreads)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                       sdst + (uint32_t)(i * sizeof(K))),
+                   "l"(src + i), "n"(sizeof(K))
+                   : "memory");
+  } else {
+    for (int i = threadIdx.x; i < n; i += kSortThreads)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                       sdst + (uint32_t)(i * sizeof(K))),
+                   "l"(src + i), "n"(sizeof(K))
+                   : "memory");
+  }
+}
+
+// Stable ranks of a warp's rows by digit.  Row i*32 + lane of the warp holds
+// digit dr[i] (low 16 bits); rows at or beyond nv are padding.  Lanes with the
+// same digit are found by one ballot per digit bit; the group's highest lane
+// adds the group size to the warp's 16-bit counter of that digit (two per
+// word; items in order, so ranks follow row order), and the rank (returned
+// base + lanes of the group below this one) goes to the high 16 bits of dr[i].
+template <int NB, int ITEMS>
+__device__ __forceinline__ void rank_items(uint32_t (&dr)[ITEMS], int nv, uint32_t* wh) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t ltm = lanemask_lt();
+  constexpr int kHalf = ITEMS >= 4 ? 4 : ITEMS;
+#pragma unroll
+  for (int i0 = 0; i0 < ITEMS; i0 += kHalf) {
+    uint32_t peers[kHalf];
+#pragma unroll
+    for (int h = 0; h < kHalf; ++h) {
+      const bool ok = (i0 + h) * 32 + lane < nv;
+      const uint32_t v = __ballot_sync(0xFFFFFFFFu, ok);
+      peers[h] = ok ? v : ~v;
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+#pragma unroll
+      for (int h = 0; h < kHalf; ++h) {
+        const bool one = (dr[i0 + h] >> b) & 1u;
+        const uint32_t x = __ballot_sync(0xFFFFFFFFu, one);
+        peers[h] &= one ? x : ~x;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kHalf; ++h) {
+      const int i = i0 + h;
+      const bool ok = i * 32 + lane < nv;
+      const int leader = 31 - __clz(peers[h]);
+      const uint32_t d = dr[i] & 0xFFFFu;
+      const uint32_t sh = (d & 1u) * 16u;
+      uint32_t base = 0u;
+      if (ok && leader == lane)
+        base = (atomicAdd(&wh[d >> 1], (uint32_t)__popc(peers[h]) << sh) >> sh) & 0xFFFFu;
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      dr[i] |= (base + __popc(peers[h] & ltm)) << 16;
+    }
+  }
+}
+
+// One LSD pass over a tile of kSortThreads * ITEMS rows:
+//   1. copy the tile's keys and ids into shared memory (cp.async, 16-byte
+//      chunks) where they stay in input order;
+//   2. take every row's digit, count the tile's digits (shared atomics) and
+//      publish the counts to the look-back chain at once, so that successors
+//      rarely wait on this tile;
+//   3. rank stably inside each warp (rank_items; warp w owns rows
+//      [w*32*ITEMS, (w+1)*32*ITEMS), item i covers 32 consecutive rows);
+//   4. record, for every tile-sorted slot, its input row (a 16-bit index)
+//      while the first look-back window is in flight, then finish the
+//      look-back (bounded wait; on timeout report TJ_ERR_TIMEOUT and go on);
+//   5. walk the slots in order and write each row to its global position:
+//      consecutive slots of one digit go to consecutive addresses.
 template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     k_onesweep(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles, int pass,
@@ -323,6 +436,8 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
                const int32_t* __restrict__ tile_job) {
   using U = typename UnsignedOf<K>::type;
   constexpr int TILE = kSortThreads * ITEMS;
+  static_assert(TILE <= 65536, "slot indices are 16-bit");
+  constexpr int kLookWide = 16;  // predecessors per round trip after the first
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_warp[kSortWarps];
   __shared__ uint32_t s_t;
@@ -339,120 +454,108 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   const int64_t row0 = lt * TILE;
   const int nvalid = (int)min((int64_t)TILE, J->n - row0);
   const int shift = J->shift[pass];
-  const int bins = 1 << J->bits[pass];
+  const int nbits = J->bits[pass];
+  const int bins = 1 << nbits;
+  const int hb = (bins + 1) >> 1;
   const uint32_t mask = (uint32_t)bins - 1u;
   const U lo = (U)J->lo;
-  const K* __restrict__ src_k = J->src_k[pass] + row0;
-  const K* __restrict__ src_v = J->src_v[pass] + row0;
-  K* __restrict__ dst_k = J->dst_k[pass];
-  K* __restrict__ dst_v = J->dst_v[pass];
   uint32_t* lb_base = J->lookback;
   uint32_t* lb_mine = lb_base + lt * bins;
-  const uint32_t* hist = J->hist + pass * J->hist_stride;
 
   K* s_keys = reinterpret_cast<K*>(smem);
   K* s_vals = s_keys + TILE;
-  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_vals + TILE);
-  uint32_t* s_count = s_whist + kSortWarps * bins;
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(s_vals + TILE);
+  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_src + TILE);
+  uint32_t* s_count = s_whist + kSortWarps * hb;  // contiguous with s_whist
   uint32_t* s_excl = s_count + bins;
   long long* s_gbase = reinterpret_cast<long long*>(s_excl + bins);
   K* s_cuts = reinterpret_cast<K*>(s_gbase + bins);
   uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_cuts + bins);
-  const int ncuts = J->cuts ? J->ncuts : -1;
-  if (ncuts >= 0) {
+  uint16_t* s_dig = s_tab + (kRouteBuckets + 8);
+  const bool route = J->cuts != nullptr;
+
+  // 1. tile -> shared memory (asynchronous), counters zeroed meanwhile
+  copy_rows_async<K>(s_keys, J->src_k[pass] + row0, nvalid);
+  copy_rows_async<K>(s_vals, J->src_v[pass] + row0, nvalid);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  if (route) {
     for (int i = tid; i < bins; i += kSortThreads) s_cuts[i] = J->cuts[i];
     for (int i = tid; i <= kRouteBuckets; i += kSortThreads) s_tab[i] = J->route_tab[i];
   }
-  // the digit of a row in this pass: a radix digit of key - lo, or its route
-  auto dig = [&](K k) -> uint32_t {
-    return ncuts >= 0 ? route_idx<K>(k, lo, s_cuts, s_tab)
-                      : digit_of<K>(k, lo, shift, mask);
-  };
+  for (int i = tid; i < kSortWarps * hb + bins; i += kSortThreads) s_whist[i] = 0u;
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
 
-  // Warp-striped rows: warp w owns rows [w*32*ITEMS, (w+1)*32*ITEMS) of the
-  // tile; item i covers 32 consecutive rows, so ranks follow row order.
+  // 2. digits (low 16 bits of dr; the rank goes to the high 16 bits later)
   const int wbase = warp * 32 * ITEMS;
-  K key[ITEMS];
-  K val[ITEMS];
+  uint32_t dr[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const int r = wbase + i * 32 + lane;
-    key[i] = r < nvalid ? src_k[r] : K(0);
+    const K k = s_keys[wbase + i * 32 + lane];  // padding rows: unused values
+    dr[i] = route ? route_idx<K>(k, lo, s_cuts, s_tab) : digit_of<K>(k, lo, shift, mask);
   }
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int r = wbase + i * 32 + lane;
-    val[i] = r < nvalid ? src_v[r] : K(0);
-  }
-  for (int i = tid; i < kSortWarps * bins; i += kSortThreads) s_whist[i] = 0u;
+  for (int i = 0; i < ITEMS; ++i)
+    if (wbase + i * 32 + lane < nvalid) atomicAdd(&s_count[dr[i]], 1u);
   __syncthreads();
+  for (int d = tid; d < bins; d += kSortThreads)
+    st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | s_count[d]);
 
-  // 1. peer groups of equal digits for every item (independent -> pipelined)
-  uint32_t peers[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int r = wbase + i * 32 + lane;
-    const uint32_t d = r < nvalid ? dig(key[i]) : 0xFFFFFFFFu;
-    peers[i] = __match_any_sync(0xFFFFFFFFu, d);
-  }
-  // 2. one shared-memory atomicAdd per group, issued by the group's highest
-  //    lane; it returns the warp's running count of that digit (items in order)
-  uint32_t* wh = s_whist + warp * bins;
-  uint32_t rk[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int r = wbase + i * 32 + lane;
-    rk[i] = 0u;
-    if (r < nvalid && (peers[i] >> lane) == 1u)
-      rk[i] = atomicAdd(&wh[dig(key[i])], (uint32_t)__popc(peers[i]));
-  }
-  // 3. broadcast the group's base and add the rank inside the group
-  const uint32_t ltm = lanemask_lt();
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int leader = 31 - __clz(peers[i]);
-    const uint32_t base = __shfl_sync(0xFFFFFFFFu, rk[i], leader);
-    rk[i] = base + __popc(peers[i] & ltm);
+  // 3. stable rank inside the warp (digit width fixed at compile time so that
+  //    the ballots of several items interleave)
+  {
+    uint32_t* wh = s_whist + warp * hb;
+    const int nv = nvalid - wbase;  // valid rows of this warp (may be <= 0)
+    switch (nbits) {
+      case 1: rank_items<1, ITEMS>(dr, nv, wh); break;
+      case 2: rank_items<2, ITEMS>(dr, nv, wh); break;
+      case 3: rank_items<3, ITEMS>(dr, nv, wh); break;
+      case 4: rank_items<4, ITEMS>(dr, nv, wh); break;
+      case 5: rank_items<5, ITEMS>(dr, nv, wh); break;
+      case 6: rank_items<6, ITEMS>(dr, nv, wh); break;
+      case 7: rank_items<7, ITEMS>(dr, nv, wh); break;
+      case 8: rank_items<8, ITEMS>(dr, nv, wh); break;
+      case 9: rank_items<9, ITEMS>(dr, nv, wh); break;
+      default: rank_items<10, ITEMS>(dr, nv, wh); break;
+    }
   }
   __syncthreads();
 
-  // per digit: exclusive prefix over warps and the tile's count; publish it
-  for (int d = tid; d < bins; d += kSortThreads) {
+  // per pair of digits: exclusive prefix over the warps (16-bit halves; the
+  // tile's totals are already in s_count)
+  for (int p = tid; p < hb; p += kSortThreads) {
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = s_whist[w * bins + d];
-      s_whist[w * bins + d] = run;
+      const uint32_t c = s_whist[w * hb + p];
+      s_whist[w * hb + p] = run;
       run += c;
     }
-    s_count[d] = run;
-    st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | run);
   }
-  __syncthreads();
-  sort_block_excl_scan(s_count, s_excl, bins, s_warp);
+  sort_block_excl_scan(s_count, s_excl, bins, s_warp);  // its barriers order the loop above
 
-  // Look-back and placement overlap: each digit thread first issues the loads
-  // of its first look-back window, then every thread places its rows at their
-  // tile-sorted position in shared memory, then the digit threads finish the
-  // decoupled look-back (summing predecessors' counts of their digit until an
-  // inclusive prefix, kLookWindow words per round trip; bounded wait, on
-  // timeout report and go on).
+  // 4. first look-back window in flight while the slots are recorded
   constexpr int kDPer = (kMaxBins + kSortThreads - 1) / kSortThreads;
-  uint32_t win[kLookWindow];  // first window of this thread's first digit
+  uint32_t win[kLookWindow];
 #pragma unroll
   for (int w = 0; w < kLookWindow; ++w)
     win[w] = (tid < bins && lt - 1 - w >= 0) ? ld_volatile_u32(lb_base + (lt - 1 - w) * bins + tid)
-                                             : 0u;
+                                             : kFlagInc;
+  {
+    const uint32_t* wx = s_whist + warp * hb;
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int r = wbase + i * 32 + lane;
-    if (r < nvalid) {
-      const uint32_t d = dig(key[i]);
-      const uint32_t pos = s_excl[d] + s_whist[warp * bins + d] + rk[i];
-      s_keys[pos] = key[i];
-      s_vals[pos] = val[i];
+    for (int i = 0; i < ITEMS; ++i) {
+      const int r = wbase + i * 32 + lane;
+      if (r < nvalid) {
+        const uint32_t d = dr[i] & 0xFFFFu;
+        const uint32_t wpre = (wx[d >> 1] >> ((d & 1u) * 16u)) & 0xFFFFu;
+        const uint32_t pos = s_excl[d] + wpre + (dr[i] >> 16);
+        s_src[pos] = (uint16_t)r;
+        if (route) s_dig[pos] = (uint16_t)d;
+      }
     }
   }
+  const uint32_t* hist = J->hist + pass * J->hist_stride;
 #pragma unroll
   for (int e = 0; e < kDPer; ++e) {
     const int d = tid + e * kSortThreads;
@@ -460,45 +563,22 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     uint32_t prefix = 0;
     if (lt > 0) {
       int64_t k = lt - 1;  // newest predecessor not yet summed
-      int spins = 0;
       bool done = false;
-      bool first = (e == 0);
+      if (e == 0) k -= lookback_consume<kLookWindow>(win, prefix, done);
+      int spins = 0;
       while (!done) {
-        uint32_t v[kLookWindow];
+        uint32_t v[kLookWide];
 #pragma unroll
-        for (int w = 0; w < kLookWindow; ++w)
-          v[w] = first ? win[w]
-                       : ((k - w >= 0) ? ld_volatile_u32(lb_base + (k - w) * bins + d) : kFlagInc);
-        if (first)
-#pragma unroll
-          for (int w = 0; w < kLookWindow; ++w)
-            if (k - w < 0) v[w] = kFlagInc;
-        first = false;
-        int used = 0;
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < kLookWindow; ++w) {
-          if (used != w) break;
-          const uint32_t f = v[w] & ~kValMask;
-          if (f == 0u) break;
-          acc += v[w] & kValMask;
-          ++used;
-          if (f == kFlagInc) {
-            done = true;
-            break;
-          }
-        }
-        prefix += acc;
+        for (int w = 0; w < kLookWide; ++w)
+          v[w] = (k - w >= 0) ? ld_volatile_u32(lb_base + (k - w) * bins + d) : kFlagInc;
+        const int used = lookback_consume<kLookWide>(v, prefix, done);
         k -= used;
-        if (done || k < 0) break;
         if (used == 0) {
           if (++spins > kSpinLimit) {
             atomicExch(err, (int)TJ_ERR_TIMEOUT);
             break;
           }
           __nanosleep(32);
-        } else {
-          spins = 0;
         }
       }
       st_volatile_u32(lb_mine + d, kFlagInc | ((prefix + s_count[d]) & kValMask));
@@ -507,314 +587,18 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   }
   __syncthreads();
 
-  // scatter: consecutive staged rows of one digit go to consecutive addresses
+  // 5. slots in order -> global
+  K* __restrict__ dst_k = J->dst_k[pass];
+  K* __restrict__ dst_v = J->dst_v[pass];
 #pragma unroll 4
   for (int q = tid; q < nvalid; q += kSortThreads) {
-    const K k = s_keys[q];
-    const uint32_t d = dig(k);
+    const int r = s_src[q];
+    const K k = s_keys[r];
+    const uint32_t d = route ? (uint32_t)s_dig[q] : digit_of<K>(k, lo, shift, mask);
     const long long g = s_gbase[d] + q;
     dst_k[g] = k;
-    dst_v[g] = s_vals[q];
+    dst_v[g] = s_vals[r];
   }
-}
-
-// ---------------------------------------------------------------------------
-// K4': persistent onesweep pass with TMA prefetch of the next tile
-// ---------------------------------------------------------------------------
-// One CTA per SM loops over tiles taken from the atomic tile counter.  While
-// it ranks and scatters tile t from shared buffer b, the next tile's keys and
-// ids are already being copied into buffer b ^ 1 by the tensor memory
-// accelerator (cp.async.bulk, completion counted on an mbarrier), so HBM reads
-// stay in flight for the whole tile instead of only at its start.  Tiles whose
-// rows are not 16-byte aligned in global memory (a job starting at an odd
-// offset, a ragged last tile) are copied by the threads instead.  A CTA takes
-// tile ids in increasing order and finishes them in that order, so the tile a
-// look-back waits on is always being processed (no deadlock).
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  uint64_t g;
-  asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(g), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Bounded wait for a buffer's copy; false (and the error word set) on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
-  for (int i = 0; i < kSpinLimit; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (i > 64) __nanosleep(32);
-  }
-  atomicExch(err, (int)TJ_ERR_TIMEOUT);
-  return false;
-}
-
-// Shared memory: two tile buffers (keys | ids) | warp counters[kSortWarps][bins]
-// | tile count[bins] | tile exclusive[bins] | global base[bins] | [cuts, index]
-template <typename K>
-__host__ __device__ constexpr size_t onesweep_pf_smem_bytes(int bins, bool route) {
-  return 4 * sizeof(K) * (size_t)kTile + sizeof(uint32_t) * (size_t)(kSortWarps + 2) * bins +
-         sizeof(long long) * (size_t)bins +
-         (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) : 0);
-}
-
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads, 1)
-    k_onesweep_pf(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles,
-                  int pass, int max_bins, uint32_t* __restrict__ tile_counter,
-                  int* __restrict__ err, const int32_t* __restrict__ tile_job) {
-  using U = typename UnsignedOf<K>::type;
-  constexpr int TILE = kTile;
-  extern __shared__ __align__(128) unsigned char smem[];
-  K* s_buf = reinterpret_cast<K*>(smem);  // buffer b: keys at 2*b*TILE, ids at (2*b+1)*TILE
-  uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_buf + 4 * TILE);
-  uint32_t* s_count = s_whist + kSortWarps * max_bins;
-  uint32_t* s_excl = s_count + max_bins;
-  long long* s_gbase = reinterpret_cast<long long*>(s_excl + max_bins);
-  K* s_cuts = reinterpret_cast<K*>(s_gbase + max_bins);
-  uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_cuts + max_bins);
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ long long s_tile[2];
-  __shared__ int s_mode[2];  // 0: nothing to do, 1: copied by TMA, 2: threads copy it
-  __shared__ uint32_t s_warp[kSortWarps];
-  __shared__ int s_route_job, s_stop;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t parity[2] = {0u, 0u};
-
-  // thread 0 only: take the next tile id and start copying it into buffer b
-  auto fetch = [&](int b) {
-    const long long t = (long long)atomicAdd(tile_counter, 1u);
-    int mode = 0;
-    if (t < total_tiles) {
-      const int j = tile_job ? tile_job[t] : find_job(jobs, num_jobs, t);
-      const RadixJob<K>* J = jobs + j;
-      if (pass < J->passes) {
-        const int64_t row0 = (t - J->tile0) * TILE;
-        const int nvalid = (int)min((int64_t)TILE, J->n - row0);
-        const K* sk = J->src_k[pass] + row0;
-        const K* sv = J->src_v[pass] + row0;
-        const uint32_t bytes = (uint32_t)nvalid * (uint32_t)sizeof(K);
-        mode = 2;
-        if ((((uintptr_t)sk | (uintptr_t)sv) & 15u) == 0 && (bytes & 15u) == 0) {
-          mode = 1;
-          // the buffer's previous contents were written through the generic proxy
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_expect_tx(&s_bar[b], 2 * bytes);
-          bulk_g2s(s_buf + 2 * b * TILE, sk, bytes, &s_bar[b]);
-          bulk_g2s(s_buf + (2 * b + 1) * TILE, sv, bytes, &s_bar[b]);
-        }
-      }
-    }
-    s_tile[b] = t;
-    s_mode[b] = mode;
-  };
-
-  if (tid == 0) {
-    mbar_init(&s_bar[0]);
-    mbar_init(&s_bar[1]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_route_job = -1;
-    s_stop = 0;
-    fetch(0);
-  }
-  __syncthreads();
-  int b = 0;
-  while (true) {
-    const long long t = s_tile[b];
-    const int mode = s_mode[b];
-    if (t >= total_tiles || s_stop) break;
-    if (tid == 0) fetch(b ^ 1);  // buffer b ^ 1 was released at the end of the last tile
-    if (mode == 0) {
-      __syncthreads();
-      b ^= 1;
-      continue;
-    }
-    const int j = tile_job ? tile_job[t] : find_job(jobs, num_jobs, t);
-    const RadixJob<K>* J = jobs + j;
-    const int64_t lt = t - J->tile0;
-    const int64_t row0 = lt * TILE;
-    const int nvalid = (int)min((int64_t)TILE, J->n - row0);
-    const int shift = J->shift[pass];
-    const int bins = 1 << J->bits[pass];
-    const uint32_t mask = (uint32_t)bins - 1u;
-    const U lo = (U)J->lo;
-    K* __restrict__ dst_k = J->dst_k[pass];
-    K* __restrict__ dst_v = J->dst_v[pass];
-    uint32_t* lb_base = J->lookback;
-    uint32_t* lb_mine = lb_base + lt * bins;
-    const uint32_t* hist = J->hist + pass * J->hist_stride;
-    const int ncuts = J->cuts ? J->ncuts : -1;
-    K* bk = s_buf + 2 * b * TILE;
-    K* bv = s_buf + (2 * b + 1) * TILE;
-    const bool reload = ncuts >= 0 && s_route_job != j;
-    auto dig = [&](K k) -> uint32_t {
-      return ncuts >= 0 ? route_idx<K>(k, lo, s_cuts, s_tab) : digit_of<K>(k, lo, shift, mask);
-    };
-
-    if (mode == 1) {
-      mbar_wait_bounded(&s_bar[b], parity[b], err);
-      parity[b] ^= 1u;
-    } else {
-      const K* __restrict__ src_k = J->src_k[pass] + row0;
-      const K* __restrict__ src_v = J->src_v[pass] + row0;
-      for (int i = tid; i < nvalid; i += kSortThreads) {
-        bk[i] = src_k[i];
-        bv[i] = src_v[i];
-      }
-    }
-    if (reload) {
-      for (int i = tid; i < bins; i += kSortThreads) s_cuts[i] = J->cuts[i];
-      for (int i = tid; i <= kRouteBuckets; i += kSortThreads) s_tab[i] = J->route_tab[i];
-    }
-    for (int i = tid; i < kSortWarps * bins; i += kSortThreads) s_whist[i] = 0u;
-    __syncthreads();
-    if (tid == 0 && reload) s_route_job = j;
-
-    const int wbase = warp * 32 * kItems;
-    K key[kItems];
-    K val[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const int r = wbase + i * 32 + lane;
-      key[i] = r < nvalid ? bk[r] : K(0);
-      val[i] = r < nvalid ? bv[r] : K(0);
-    }
-    uint32_t peers[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const int r = wbase + i * 32 + lane;
-      const uint32_t d = r < nvalid ? dig(key[i]) : 0xFFFFFFFFu;
-      peers[i] = __match_any_sync(0xFFFFFFFFu, d);
-    }
-    uint32_t* wh = s_whist + warp * bins;
-    uint32_t rk[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const int r = wbase + i * 32 + lane;
-      rk[i] = 0u;
-      if (r < nvalid && (peers[i] >> lane) == 1u)
-        rk[i] = atomicAdd(&wh[dig(key[i])], (uint32_t)__popc(peers[i]));
-    }
-    const uint32_t ltm = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const int leader = 31 - __clz(peers[i]);
-      const uint32_t base = __shfl_sync(0xFFFFFFFFu, rk[i], leader);
-      rk[i] = base + __popc(peers[i] & ltm);
-    }
-    __syncthreads();
-
-    for (int d = tid; d < bins; d += kSortThreads) {
-      uint32_t run = 0;
-#pragma unroll
-      for (int w = 0; w < kSortWarps; ++w) {
-        const uint32_t c = s_whist[w * bins + d];
-        s_whist[w * bins + d] = run;
-        run += c;
-      }
-      s_count[d] = run;
-      st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | run);
-    }
-    __syncthreads();
-    sort_block_excl_scan(s_count, s_excl, bins, s_warp);
-
-    // placement into the tile buffer (every row has been read into registers)
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      const int r = wbase + i * 32 + lane;
-      if (r < nvalid) {
-        const uint32_t d = dig(key[i]);
-        const uint32_t pos = s_excl[d] + s_whist[warp * bins + d] + rk[i];
-        bk[pos] = key[i];
-        bv[pos] = val[i];
-      }
-    }
-    // decoupled look-back, kLookWindow predecessors per round trip, bounded
-    for (int d = tid; d < bins; d += kSortThreads) {
-      uint32_t prefix = 0;
-      if (lt > 0) {
-        int64_t k = lt - 1;
-        int spins = 0;
-        bool done = false;
-        while (!done) {
-          uint32_t v[kLookWindow];
-#pragma unroll
-          for (int w = 0; w < kLookWindow; ++w)
-            v[w] = (k - w >= 0) ? ld_volatile_u32(lb_base + (k - w) * bins + d) : kFlagInc;
-          int used = 0;
-          uint32_t acc = 0;
-#pragma unroll
-          for (int w = 0; w < kLookWindow; ++w) {
-            if (used != w) break;
-            const uint32_t f = v[w] & ~kValMask;
-            if (f == 0u) break;
-            acc += v[w] & kValMask;
-            ++used;
-            if (f == kFlagInc) {
-              done = true;
-              break;
-            }
-          }
-          prefix += acc;
-          k -= used;
-          if (done || k < 0) break;
-          if (used == 0) {
-            if (++spins > kSpinLimit) {
-              atomicExch(err, (int)TJ_ERR_TIMEOUT);
-              break;
-            }
-            __nanosleep(32);
-          } else {
-            spins = 0;
-          }
-        }
-        st_volatile_u32(lb_mine + d, kFlagInc | ((prefix + s_count[d]) & kValMask));
-      }
-      s_gbase[d] = (long long)hist[d] + (long long)prefix - (long long)s_excl[d];
-    }
-    __syncthreads();
-
-#pragma unroll 4
-    for (int q = tid; q < nvalid; q += kSortThreads) {
-      const K k = bk[q];
-      const long long g = s_gbase[dig(k)] + q;
-      dst_k[g] = k;
-      dst_v[g] = bv[q];
-    }
-    if (tid == 0) s_stop = ld_volatile_u32(reinterpret_cast<const uint32_t*>(err)) != 0u;
-    // order this tile's generic-proxy reads and writes of buffer b before the
-    // bulk copy that will refill it
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();  // buffer b is free again
-    b ^= 1;
-  }
-  // a copy started for a tile this CTA will not process must land before exit
-  if (tid == 0 && s_tile[b] < total_tiles && s_mode[b] == 1)
-    mbar_wait_bounded(&s_bar[b], parity[b], err);
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -871,25 +655,6 @@ cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t tot
                             int pass, int max_bits, bool route, uint32_t* d_tile_counter,
                             int* d_err, cudaStream_t st, const int32_t* d_tile_job, int items) {
   if (total_tiles <= 0) return cudaSuccess;
-#if TJ_ONESWEEP_PF
-  if (items == kItems) {
-    // persistent: one CTA per SM, each prefetching its next tile
-    static int sms[256] = {0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 256 && sms[dev] == 0) {
-      e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-      if (e != cudaSuccess) return e;
-    }
-    const int nsm = (dev >= 0 && dev < 256 && sms[dev] > 0) ? sms[dev] : 152;
-    const int64_t grid = total_tiles < nsm ? total_tiles : nsm;
-    const size_t smem = onesweep_pf_smem_bytes<K>(1 << max_bits, route);
-    k_onesweep_pf<K><<<(unsigned)grid, kSortThreads, smem, st>>>(
-        d_jobs, num_jobs, total_tiles, pass, 1 << max_bits, d_tile_counter, d_err, d_tile_job);
-    return cudaGetLastError();
-  }
-#endif
   if (items == 4) {
     const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4);
     k_onesweep<K, 4><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
@@ -910,12 +675,6 @@ cudaError_t radix_init_attributes() {
   e = cudaFuncSetAttribute(k_onesweep<int64_t, kItems>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)onesweep_smem_bytes<int64_t>(kMaxBins, true));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_onesweep_pf<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_pf_smem_bytes<int32_t>(kMaxBins, true));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_onesweep_pf<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_pf_smem_bytes<int64_t>(kMaxBins, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_onesweep<int32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kSortThreads * 4));
