@@ -750,8 +750,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   stats.staging_bytes = (int64_t)staging;
   int* d_err = stg.at<int>(o_misc);
   uint32_t* d_counters = stg.at<uint32_t>(o_misc + 16);
-  int64_t* d_total = stg.at<int64_t>(o_misc + 128);
-  int64_t* d_base = stg.at<int64_t>(o_misc + 136);
   std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
   std::copy(cuts.begin(), cuts.end(), hc.begin());
   TJ_CUDA(cudaMemcpyAsync(stg.at<K>(o_cuts), hc.data(), kMaxCuts * sizeof(K),
@@ -859,7 +857,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     int64_t r0, nr, s0, ns;
     K lo, hi;
     Plan plan;
-    int64_t ws;
+    int64_t ws;  // working set without the look-back words
+    int64_t lb;  // look-back bytes of one pass
+    int np;      // passes (at least 1)
   };
   std::vector<Part> P;
   int64_t r_at = 0, s_at = 0, maxrows = 0, live_rows = 0;
@@ -876,12 +876,18 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     q.lo = j == 0 ? lo : std::max(lo, cuts[(size_t)j - 1]);
     q.hi = j == ncuts ? hi : std::min(hi, (K)(cuts[(size_t)j] - 1));
     q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd);
-    const int nb = std::min(q.plan.passes, 2);
+    // one sort buffer (the passes alternate between it and the batch's routed
+    // copy), one look-back region per pass, join tile state (ra, rb, chained
+    // words, tile map), the radix tile map, histograms, alignment
+    // (a group keeps one look-back region per pass of its deepest batch)
+    const int nb = std::min(q.plan.passes, 1);
+    const int np = std::max(1, q.plan.passes);
     const int64_t bins = (int64_t)1 << q.plan.max_bits;
-    q.ws = (int64_t)nb * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
-           (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * bins * 4 +
-           ceil_div(q.ns, kJTile) * 28 + (ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile)) * 4 +
-           2 * (int64_t)std::max(1, q.plan.passes) * bins * 4 + 4096;
+    const int64_t rtiles = ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile);
+    q.lb = rtiles * bins * 4;
+    q.np = np;
+    q.ws = (int64_t)nb * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) + ceil_div(q.ns, kJTile) * 28 +
+           rtiles * 4 + 2 * (int64_t)np * bins * 4 + 4096;
     live_rows += q.nr + q.ns;
     P.push_back(q);
   }
@@ -898,15 +904,22 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   std::vector<std::pair<size_t, size_t>> groups;  // [first, last) into P
   int64_t ws_max = 0;
   for (size_t i = 0; i < P.size();) {
-    if (P[i].ws > room)
+    const int64_t need_i = P[i].ws + P[i].lb * P[i].np;
+    if (need_i > room)
       return set_err(TJ_ERR_BUDGET,
                      "batch of keys [%lld, %lld] needs %lld bytes of working set, budget "
                      "leaves %lld (raise the budget or the number of batches)",
-                     (long long)P[i].lo, (long long)P[i].hi, (long long)P[i].ws,
+                     (long long)P[i].lo, (long long)P[i].hi, (long long)need_i,
                      (long long)room);
     size_t j = i;
-    int64_t acc = 0;
-    while (j < P.size() && acc + P[j].ws <= room) acc += P[j].ws, ++j;
+    int64_t ws = 0, lb = 0, acc = 0;
+    int np = 1;
+    while (j < P.size()) {
+      const int np2 = std::max(np, P[j].np);
+      const int64_t acc2 = ws + P[j].ws + (lb + P[j].lb) * np2;
+      if (acc2 > room) break;
+      ws += P[j].ws, lb += P[j].lb, np = np2, acc = acc2, ++j;
+    }
     groups.push_back({i, j});
     ws_max = std::max(ws_max, acc);
     i = j;
@@ -915,14 +928,16 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   stats.scratch_peak = (int64_t)(cc.off - staging) + ws_max;
 
   // ---- 4. one batched sort + align per group ----
-  // Group layout in the working block: sort buffers of every batch | histograms
-  // | look-back words | join state | tile maps.  Every group's job tables are
-  // built first and uploaded once (from pinned memory), so the group loop
-  // below only enqueues kernels and memsets.
+  // Group layout in the working block: the sort buffer of every batch | one
+  // zeroed region (tile counters, histograms, one look-back region per pass,
+  // chained join words) | join tile ranges | tile maps.  Every group's job
+  // tables are built first and uploaded once (from pinned memory) together
+  // with the groups' output bases, so the group loop below only enqueues a
+  // memset and six kernels per group.
   struct GroupPlan {
     size_t first, nj;
     size_t rj_at, jj_at;  // offsets into the uploaded tables
-    size_t o_hist, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
+    size_t o_zero, zero_bytes, o_cnt, o_hist, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
     size_t hist_words, lb_words;
     int64_t tiles, jtiles;
     int P, maxbits;
@@ -940,14 +955,14 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     gp.nj = g.second - g.first;
     const size_t nj = gp.nj;
     Carve gc;
-    std::vector<size_t> o_buf(nj * 8, 0);
+    std::vector<size_t> o_buf(nj * 4, 0);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
-      for (int b2 = 0; b2 < std::min(q.plan.passes, 2); ++b2) {
-        o_buf[i * 8 + 4 * b2 + 0] = gc.add<K>((size_t)q.nr);
-        o_buf[i * 8 + 4 * b2 + 1] = gc.add<K>((size_t)q.nr);
-        o_buf[i * 8 + 4 * b2 + 2] = gc.add<K>((size_t)q.ns);
-        o_buf[i * 8 + 4 * b2 + 3] = gc.add<K>((size_t)q.ns);
+      if (q.plan.passes > 0) {
+        o_buf[i * 4 + 0] = gc.add<K>((size_t)q.nr);
+        o_buf[i * 4 + 1] = gc.add<K>((size_t)q.nr);
+        o_buf[i * 4 + 2] = gc.add<K>((size_t)q.ns);
+        o_buf[i * 4 + 3] = gc.add<K>((size_t)q.ns);
       }
     }
     std::vector<size_t> hist_at(nj * 2), lb_at(nj * 2);
@@ -964,10 +979,16 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       gp.maxbits = std::max(gp.maxbits, q.plan.max_bits);
       for (int p = 0; p < q.plan.passes; ++p) gp.prow[p] += (double)(q.nr + q.ns);
     }
+    for (size_t i = 0; i < nj; ++i) gp.jtiles += ceil_div(P[g.first + i].ns, kJTile);
+    gp.o_cnt = gc.add<uint32_t>(kMaxPasses + 1);
+    gp.o_zero = gp.o_cnt;
     gp.o_hist = gc.add<uint32_t>(std::max<size_t>(gp.hist_words, 1));
-    gp.o_lb = gc.add<uint32_t>(std::max<size_t>(gp.lb_words, 1));
+    gp.o_lb = gc.add<uint32_t>(std::max<size_t>(gp.lb_words, 1) * (size_t)std::max(1, gp.P));
+    gp.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
+    gp.zero_bytes = gc.off - gp.o_zero;
     gp.rj_at = all_rj.size();
     gp.jj_at = all_jj.size();
+    int64_t jt = 0;
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
       gp.rows += (double)(q.nr + q.ns);
@@ -976,8 +997,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         RadixJob<K> x;
         memset(&x, 0, sizeof(x));
         const int64_t n = side ? q.ns : q.nr;
-        const K* k0 = side ? stg.at<K>(o_sk) + q.s0 : stg.at<K>(o_rk) + q.r0;
-        const K* v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
+        K* k0 = side ? stg.at<K>(o_sk) + q.s0 : stg.at<K>(o_rk) + q.r0;
+        K* v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
         x.keys = k0;
         x.n = n;
         x.tile0 = gp.tiles;
@@ -986,12 +1007,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         x.hist_stride = 1 << q.plan.max_bits;
         x.hist = wk.at<uint32_t>(gp.o_hist) + hist_at[i * 2 + side];
         x.lookback = wk.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
-        const int nb = std::min(q.plan.passes, 2);
-        K* ak = nb > 0 ? wk.at<K>(o_buf[i * 8 + 2 * side]) : nullptr;
-        K* av = nb > 0 ? wk.at<K>(o_buf[i * 8 + 2 * side + 1]) : nullptr;
-        K* bk = nb > 1 ? wk.at<K>(o_buf[i * 8 + 4 + 2 * side]) : nullptr;
-        K* bv = nb > 1 ? wk.at<K>(o_buf[i * 8 + 4 + 2 * side + 1]) : nullptr;
-        set_job_buffers(x, k0, v0, ak, av, bk, bv, &res[2 * side], &res[2 * side + 1]);
+        x.lb_stride = (int64_t)gp.lb_words;
+        // passes alternate: routed copy -> buffer -> routed copy -> ...
+        K* ak = q.plan.passes > 0 ? wk.at<K>(o_buf[i * 4 + 2 * side]) : nullptr;
+        K* av = q.plan.passes > 0 ? wk.at<K>(o_buf[i * 4 + 2 * side + 1]) : nullptr;
+        set_job_buffers(x, k0, v0, ak, av, k0, v0, &res[2 * side], &res[2 * side + 1]);
         all_rj.push_back(x);
       }
       JoinJob<K> y;
@@ -1001,13 +1021,12 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       y.sk = res[2];
       y.sv = res[3];
       y.ns = q.ns;
-      y.tile0 = gp.jtiles;
-      gp.jtiles += ceil_div(q.ns, kJTile);
+      y.tile0 = jt;
+      jt += ceil_div(q.ns, kJTile);
       all_jj.push_back(y);
     }
     gp.o_ra = gc.add<int64_t>((size_t)gp.jtiles);
     gp.o_rb = gc.add<int64_t>((size_t)gp.jtiles);
-    gp.o_jlb = gc.add<uint64_t>((size_t)gp.jtiles);
     gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
     gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     if ((int64_t)gc.off > std::max<int64_t>(ws_max, 256))
@@ -1016,61 +1035,63 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     maxp = std::max(maxp, gp.P);
     plans.push_back(gp);
   }
-  // one upload of every group's job tables
+  // one upload of every group's job tables and of the output bases: group g
+  // writes from base[g] on and its last join tile sets base[g + 1]
   const size_t rj_bytes = all_rj.size() * sizeof(RadixJob<K>);
   const size_t jj_bytes = all_jj.size() * sizeof(JoinJob<K>);
+  const size_t base_at = (rj_bytes + jj_bytes + 15) & ~(size_t)15;
+  const size_t base_bytes = (plans.size() + 1) * sizeof(int64_t);
   Block tbl;
-  TJ_CUDA(tbl.alloc(rj_bytes + jj_bytes + 256, st));
+  TJ_CUDA(tbl.alloc(base_at + base_bytes + 256, st));
   {
     unsigned char* h = nullptr;
-    TJ_CUDA(pinned_staging(rj_bytes + jj_bytes, &h));
+    TJ_CUDA(pinned_staging(base_at + base_bytes, &h));
     memcpy(h, all_rj.data(), rj_bytes);
     memcpy(h + rj_bytes, all_jj.data(), jj_bytes);
-    TJ_CUDA(cudaMemcpyAsync(tbl.p, h, rj_bytes + jj_bytes, cudaMemcpyHostToDevice, st));
+    memset(h + base_at, 0, base_bytes);
+    TJ_CUDA(cudaMemcpyAsync(tbl.p, h, base_at + base_bytes, cudaMemcpyHostToDevice, st));
     TJ_CUDA(cudaEventRecord(pinned_event(), st));  // the staging buffer is busy until here
   }
   RadixJob<K>* d_rj_all = tbl.at<RadixJob<K>>(0);
   JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + rj_bytes);
-  stats.scratch_peak += (int64_t)(rj_bytes + jj_bytes);
-  for (const GroupPlan& gp : plans) {
+  int64_t* d_gbase = reinterpret_cast<int64_t*>(tbl.p + base_at);
+  stats.scratch_peak += (int64_t)(base_at + base_bytes);
+  for (size_t g = 0; g < plans.size(); ++g) {
+    const GroupPlan& gp = plans[g];
     const size_t nj = gp.nj;
     RadixJob<K>* d_gj = d_rj_all + gp.rj_at;
     JoinJob<K>* d_gjj = d_jj_all + gp.jj_at;
-    TJ_CUDA(cudaMemsetAsync(d_counters, 0, (kMaxPasses + 1) * sizeof(uint32_t), st));
+    uint32_t* d_gcnt = wk.at<uint32_t>(gp.o_cnt);
     int32_t* d_tmap = wk.at<int32_t>(gp.o_tmap);
     int32_t* d_jmap = wk.at<int32_t>(gp.o_jmap);
-    TJ_CUDA(launch_fill_tile_job<K>(d_gj, (int)(2 * nj), d_tmap, st));
-    TJ_CUDA(launch_fill_join_tile_job<K>(d_gjj, (int)nj, d_jmap, st));
+    TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_zero, 0, gp.zero_bytes, st));
+    TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, st));
     if (gp.P > 0) {
-      TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_hist, 0, gp.hist_words * sizeof(uint32_t), st));
       tr.begin("histogram", w * gp.rows);
       TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), gp.tiles, st, d_tmap));
       tr.end();
       TJ_CUDA(launch_digit_scan<K>(d_gj, (int)(2 * nj), gp.P, st));
       for (int p = 0; p < gp.P; ++p) {
-        TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_lb, 0, gp.lb_words * sizeof(uint32_t), st));
         tr.begin("onesweep", 4.0 * w * gp.prow[p]);
         TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
-                                   d_counters + p, d_err, st, d_tmap));
+                                   d_gcnt + p, d_err, st, d_tmap));
         tr.end();
       }
     }
     TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
                                   wk.at<int64_t>(gp.o_rb), st, d_jmap));
-    TJ_CUDA(cudaMemsetAsync(wk.at<uint64_t>(gp.o_jlb), 0,
-                            (size_t)std::max<int64_t>(gp.jtiles, 1) * 8, st));
     tr.begin("join", 2.0 * w * gp.rows);
     TJ_CUDA(launch_join<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
                            wk.at<int64_t>(gp.o_rb), wk.at<uint64_t>(gp.o_jlb),
-                           d_counters + kMaxPasses, out, cap, d_base, nullptr, d_total, d_err, st,
-                           d_jmap));
+                           d_gcnt + kMaxPasses, out, cap, d_gbase + g, nullptr, d_gbase + g + 1,
+                           d_err, st, d_jmap));
     tr.end();
-    TJ_CUDA(launch_add_base(d_base, d_total, st));
   }
   stats.radix_passes = maxp;
   int64_t h_total = 0;
   int h_err = 0;
-  TJ_CUDA(cudaMemcpyAsync(&h_total, d_base, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaMemcpyAsync(&h_total, d_gbase + plans.size(), sizeof(int64_t),
+                          cudaMemcpyDeviceToHost, st));
   TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TJ_CUDA(cudaStreamSynchronize(st));
   if (h_total <= cap) tr.add_bytes("join", 2.0 * w * (double)h_total);

@@ -71,6 +71,8 @@ struct RadixJob {
   int32_t hist_stride;  // words between passes in `hist`
   uint32_t* hist;       // [passes][hist_stride]: counts, then exclusive bases
   uint32_t* lookback;   // [tiles][1 << bits[p]] words of the current pass
+  int64_t lb_stride;    // words between the look-back regions of consecutive
+                        // passes (0: one region, cleared before every pass)
   const K* src_k[kMaxPasses];
   const K* src_v[kMaxPasses];
   K* dst_k[kMaxPasses];
@@ -144,7 +146,11 @@ cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_ti
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
                         const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
                         int* d_err, cudaStream_t st, const int32_t* d_tile_job = nullptr);
-cudaError_t launch_add_base(int64_t* d_base, int64_t* d_total, cudaStream_t st);
+// tile -> job maps of a group's radix jobs (tile of kTile rows) and join jobs
+template <typename K>
+cudaError_t launch_group_maps(const RadixJob<K>* d_rjobs, int nr, int32_t* d_rmap,
+                              const JoinJob<K>* d_jjobs, int nj, int32_t* d_jmap,
+                              cudaStream_t st);
 
 // ---- launchers (tj_learned.cu) ----------------------------------------------
 template <typename K>

@@ -5,18 +5,17 @@
 //                   sorted R rows whose keys lie between the tile's first and
 //                   last key (two binary searches per tile).
 //   k_join        : per S tile, fused count -> scan -> write:
-//                     1. stage the tile's S rows and (if b - a <= 2048) its R
-//                        range in shared memory;
-//                     2. build an open-addressing hash table of the R range's
+//                     1. stage the tile's S rows and its R range (in chunks of
+//                        2048 rows, up to 4) in shared memory with cp.async;
+//                     2. build an open-addressing hash table of each chunk's
 //                        distinct keys with shared-memory atomicCAS: slot ->
 //                        (first, end) of the key's run of R rows;
-//                     3. probe it once per S row -> match count and run start;
-//                     4. exclusive scan of the counts inside the CTA, then a
-//                        decoupled look-back over all tiles of all jobs gives
+//                     3. probe it once per S row -> match count, run start;
+//                     4. a decoupled look-back over all tiles of all jobs gives
 //                        the tile's first output index;
 //                     5. write the pairs, ordered by key, S position, R
 //                        position, if they fit the caller's capacity.
-//                   Tiles whose R range exceeds the on-chip capacity (S sparse
+//                   Tiles whose R range exceeds the on-chip chunks (S sparse
 //                   against R) binary-search each key in global memory instead.
 #include "tj_internal.cuh"
 
@@ -72,6 +71,12 @@ static_assert(kRCap < 0xFFFF, "run bounds are packed in 16 bits");
 
 constexpr uint32_t kHTEmpty = 0xFFFFFFFFu;
 
+__device__ __forceinline__ uint32_t lanemask_lt_j() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
   uint64_t v;
   asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -82,34 +87,113 @@ __device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
 }
 
 // ---------------------------------------------------------------------------
+// k_tile_ranges: one warp per S tile.  Lanes 0-15 find the first R row with
+// key >= the tile's first key, lanes 16-31 the first R row with key > the
+// tile's last key, each by a 16-ary search (16 probes per round trip).
 template <typename K>
 __global__ void k_tile_ranges(const JoinJob<K>* __restrict__ jobs, int num_jobs,
                               int64_t total_tiles, int64_t* __restrict__ ra,
                               int64_t* __restrict__ rb, const int32_t* __restrict__ tile_job) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total_tiles) return;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= total_tiles) return;  // whole warps leave together
+  const int lane = threadIdx.x & 31, sub = lane & 15;
+  const bool upper = lane >= 16;
+  const uint32_t half = upper ? 0xFFFF0000u : 0x0000FFFFu;
   const int j = tile_job ? tile_job[t] : find_job_j(jobs, num_jobs, t);
   const JoinJob<K>* J = jobs + j;
   const int64_t row0 = (t - J->tile0) * kJTile;
   const int64_t row1 = min(J->ns, row0 + kJTile);
-  const K kf = J->sk[row0];
-  const K kl = J->sk[row1 - 1];
-  ra[t] = lower_bound_g(J->rk, J->nr, kf);
-  rb[t] = upper_bound_g(J->rk, J->nr, kl);
+  const K key = upper ? J->sk[row1 - 1] : J->sk[row0];
+  const K* __restrict__ r = J->rk;
+  // invariant: every row before lo satisfies the predicate, none from hi on
+  // (predicate: r[i] < key for the lower bound, r[i] <= key for the upper)
+  int64_t lo = 0, hi = J->nr;
+  while (true) {
+    const int64_t len = hi - lo;
+    if (__all_sync(0xFFFFFFFFu, len <= 16)) break;
+    const int64_t step = (len + 15) / 16;
+    const int64_t p = lo + sub * step;
+    bool pred = false;
+    if (len > 16 && p < hi) pred = upper ? !(key < r[p]) : (r[p] < key);
+    const int c = __popc(__ballot_sync(0xFFFFFFFFu, pred) & half);
+    if (len > 16) {
+      // probes 0..c-1 satisfy the predicate, probe c (if any) does not
+      const int64_t lo0 = lo;
+      if (c > 0) lo = lo0 + (int64_t)(c - 1) * step + 1;
+      if (c < 16) hi = min(hi, lo0 + (int64_t)c * step);
+    }
+  }
+  const int64_t p = lo + sub;
+  const bool pred = p < hi && (upper ? !(key < r[p]) : (r[p] < key));
+  const int64_t res = lo + __popc(__ballot_sync(0xFFFFFFFFu, pred) & half);
+  if (sub == 0) {
+    if (upper)
+      rb[t] = res;
+    else
+      ra[t] = res;
+  }
 }
 
 // ---------------------------------------------------------------------------
+constexpr int kJThreads = 512;                  // threads per join CTA (16 warps)
+constexpr int kJWarps = kJThreads / 32;
+constexpr int kJItems = kJTile / kJThreads;     // S rows per thread
+static_assert(kJItems * kJThreads == kJTile, "join tile = threads x items");
+
+// Shared memory: S keys[kJTile] | S ids[kJTile] | R keys[kRCap] | R ids[kRCap]
+// | hash table[kHTSlots] u32.  After the probe the R region and the table are
+// free; the many-matches write path keeps per-row offsets (u64) and run
+// starts (u32) there.
 template <typename K>
 constexpr size_t join_smem_bytes() {
-  return sizeof(K) * kJTile             // S keys of the tile
-         + sizeof(K) * kRCap            // R keys of the tile's R range
-         + sizeof(uint32_t) * kHTSlots  // hash table: packed (first, end) of a run
-         + sizeof(uint64_t) * kJTile    // per-row counts -> exclusive offsets
-         + sizeof(uint32_t) * kJTile;   // per-row run start (relative to a)
+  return sizeof(K) * (size_t)(2 * kJTile + 2 * kRCap) + sizeof(uint32_t) * kHTSlots;
+}
+static_assert(sizeof(int32_t) * 2 * kRCap + sizeof(uint32_t) * kHTSlots >=
+                  (sizeof(uint64_t) + sizeof(uint32_t)) * kJTile,
+              "offsets and run starts fit where the R rows and the table were");
+
+// Asynchronous global -> shared copy of n elements (16-byte chunks when the
+// source allows it, else one element per copy); every thread of the CTA calls it.
+template <typename K>
+__device__ __forceinline__ void join_copy_async(K* dst, const K* __restrict__ src, int n) {
+  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
+  int done = 0;
+  if ((((uintptr_t)src) & 15u) == 0) {
+    constexpr int kPer = 16 / (int)sizeof(K);
+    const int chunks = n / kPer;
+    for (int c = threadIdx.x; c < chunks; c += kJThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst + 16u * c),
+                   "l"(src + c * kPer)
+                   : "memory");
+    done = chunks * kPer;
+  }
+  for (int i = done + threadIdx.x; i < n; i += kJThreads)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sdst + (uint32_t)(i * sizeof(K))),
+                 "l"(src + i), "n"(sizeof(K))
+                 : "memory");
 }
 
+template <typename K> struct PairOf;
+template <> struct PairOf<int32_t> { using type = int2; };
+template <> struct PairOf<int64_t> { using type = longlong2; };
+
+// One join tile: 2048 consecutive rows of sorted S against the range [a, b)
+// of sorted R whose keys lie between the tile's first and last key.
+//   1. S keys and ids and the first chunk of the R range go to shared memory
+//      (cp.async); warp w owns S rows [w*32*kJItems, ...), item u = 32 rows;
+//   2. per chunk of the R range (kRCap rows, at most kMaxChunks): an
+//      open-addressing table of the chunk's distinct keys is built with
+//      shared-memory atomicCAS (slot -> first and end of the key's run), and
+//      every S row probes it -> match count, run start and the R id of the
+//      first match; wider R ranges are binary-searched in global memory;
+//   3. the tile's total goes to the decoupled look-back chain over all tiles
+//      (thread 0), which yields the tile's first output index;
+//   4. at most one match per row (a foreign-key join): each row's output index
+//      comes from ballots over the warp and the warps' totals; otherwise the
+//      tile's counts are scanned and each output index finds its S row.
+// Output order: key, then S position, then R position.
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kJThreads, 2)
     k_join(const JoinJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles,
            const int64_t* __restrict__ ra, const int64_t* __restrict__ rb,
            uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter,
@@ -118,20 +202,16 @@ __global__ void __launch_bounds__(kThreads, 3)
            const int32_t* __restrict__ tile_job) {
   extern __shared__ __align__(16) unsigned char smem[];
   K* s_sk = reinterpret_cast<K*>(smem);
-  K* s_rk = s_sk + kJTile;
-  uint32_t* s_ht = reinterpret_cast<uint32_t*>(s_rk + kRCap);
-  uint64_t* s_off = reinterpret_cast<uint64_t*>(s_ht + kHTSlots);
-  uint32_t* s_rs = reinterpret_cast<uint32_t*>(s_off + kJTile);
-  __shared__ uint64_t s_wsum[kWarps];
-  __shared__ uint64_t s_base, s_tot;
+  K* s_sv = s_sk + kJTile;
+  K* s_rk = s_sv + kJTile;
+  K* s_rv = s_rk + kRCap;
+  uint32_t* s_ht = reinterpret_cast<uint32_t*>(s_rv + kRCap);
+  __shared__ uint64_t s_wsum[kJWarps];
+  __shared__ uint64_t s_base;
   __shared__ uint32_t s_t;
-  __shared__ int s_maxcnt;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    s_t = atomicAdd(tile_counter, 1u);
-    s_maxcnt = 0;
-  }
+  if (tid == 0) s_t = atomicAdd(tile_counter, 1u);
   __syncthreads();
   const int64_t t = s_t;
   if (t >= total_tiles) return;
@@ -142,41 +222,46 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int64_t lt = t - J.tile0;
   const int64_t row0 = lt * kJTile;
   const int nv = (int)min((int64_t)kJTile, J.ns - row0);
-  const K* __restrict__ sk_g = J.sk + row0;
-  const K* __restrict__ sv_g = J.sv + row0;
   const K* __restrict__ rk_g = J.rk + a;
   const K* __restrict__ rv_g = J.rv + a;
-
-  // S ids of this thread's rows, loaded now and used only when writing
-  constexpr int kRows = kJTile / kThreads;
-  K sid[kRows];
-#pragma unroll
-  for (int u = 0; u < kRows; ++u) {
-    const int q = tid + u * kThreads;
-    sid[u] = q < nv ? sv_g[q] : K(0);
-  }
-  for (int q = tid; q < nv; q += kThreads) s_sk[q] = sk_g[q];
-
-  // Probe: match count and run start of every S row of the tile.  The tile's
-  // R range is aligned chunk by chunk (kRCap rows each, up to kMaxChunks)
-  // through the on-chip table; a run of equal keys that straddles chunks adds
-  // up.  Tiles whose R range is wider (S sparse against R) binary-search R in
-  // global memory instead.
   const int64_t nchunks = (nrr + kRCap - 1) / kRCap;
-  uint32_t cnt[kRows], start[kRows];
+  const bool onchip = nchunks <= kMaxChunks;
+
+  // 1. stage S and the first R chunk
+  join_copy_async<K>(s_sk, J.sk + row0, nv);
+  join_copy_async<K>(s_sv, J.sv + row0, nv);
+  if (onchip && nchunks > 0) {
+    const int nc0 = (int)min((int64_t)kRCap, nrr);
+    join_copy_async<K>(s_rk, rk_g, nc0);
+    join_copy_async<K>(s_rv, rv_g, nc0);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+
+  // 2. probe
+  const int wbase = warp * 32 * kJItems;
+  uint32_t cnt[kJItems], start[kJItems];
+  K rid[kJItems];
 #pragma unroll
-  for (int u = 0; u < kRows; ++u) cnt[u] = start[u] = 0u;
-  if (nchunks <= kMaxChunks) {
+  for (int u = 0; u < kJItems; ++u) {
+    cnt[u] = start[u] = 0u;
+    rid[u] = K(0);
+  }
+  if (onchip) {
     for (int64_t c = 0; c < nchunks; ++c) {
       const int c0 = (int)(c * kRCap);
       const int nc = (int)min((int64_t)kRCap, nrr - c0);
-      __syncthreads();  // the previous chunk's probes are done
-      for (int i = tid; i < nc; i += kThreads) s_rk[i] = rk_g[c0 + i];
-      for (int i = tid; i < kHTSlots; i += kThreads) s_ht[i] = kHTEmpty;
+      if (c > 0) {
+        __syncthreads();  // the previous chunk's probes are done
+        join_copy_async<K>(s_rk, rk_g + c0, nc);
+        join_copy_async<K>(s_rv, rv_g + c0, nc);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      for (int i = tid; i < kHTSlots; i += kJThreads) s_ht[i] = kHTEmpty;
+      asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
       // insert the first row of every run of equal keys; keys are distinct, so
       // an occupied slot is never this key and insertion needs no comparison
-      for (int i = tid; i < nc; i += kThreads) {
+      for (int i = tid; i < nc; i += kJThreads) {
         if (i == 0 || s_rk[i] != s_rk[i - 1]) {
           uint32_t h = ht_hash(s_rk[i]);
           while (atomicCAS(&s_ht[h], kHTEmpty, (uint32_t)i | 0xFFFF0000u) != kHTEmpty)
@@ -185,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       }
       __syncthreads();
       // the last row of every run records the run's end
-      for (int i = tid; i < nc; i += kThreads) {
+      for (int i = tid; i < nc; i += kJThreads) {
         if (i == nc - 1 || s_rk[i] != s_rk[i + 1]) {
           const K key = s_rk[i];
           uint32_t h = ht_hash(key);
@@ -202,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 3)
       __syncthreads();
       const K cf = s_rk[0], cl = s_rk[nc - 1];
 #pragma unroll
-      for (int u = 0; u < kRows; ++u) {
-        const int q = tid + u * kThreads;
+      for (int u = 0; u < kJItems; ++u) {
+        const int q = wbase + u * 32 + lane;
         if (q >= nv) continue;
         const K key = s_sk[q];
         if (key < cf || cl < key) continue;
@@ -213,7 +298,10 @@ __global__ void __launch_bounds__(kThreads, 3)
           if (w == kHTEmpty) break;
           const uint32_t f = w & 0xFFFFu;
           if (s_rk[f] == key) {
-            if (cnt[u] == 0u) start[u] = (uint32_t)c0 + f;
+            if (cnt[u] == 0u) {
+              start[u] = (uint32_t)c0 + f;
+              rid[u] = s_rv[f];
+            }
             cnt[u] += (w >> 16) - f;
             break;
           }
@@ -221,72 +309,42 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
       }
     }
+    if (nchunks == 0) asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
 #pragma unroll
-    for (int u = 0; u < kRows; ++u) {
-      const int q = tid + u * kThreads;
+    for (int u = 0; u < kJItems; ++u) {
+      const int q = wbase + u * 32 + lane;
       if (q >= nv) continue;
       const K key = s_sk[q];
       const int64_t lo = lower_bound_g(rk_g, nrr, key);
       const int64_t hi = upper_bound_g(rk_g, nrr, key);
       start[u] = (uint32_t)lo;
       cnt[u] = (uint32_t)(hi - lo);
+      if (hi > lo) rid[u] = rv_g[lo];
     }
   }
-  // the R id of each row's first match is gathered right away (used when writing)
-  int mymax = 0;
-  K rid[kRows];
-#pragma unroll
-  for (int u = 0; u < kRows; ++u) {
-    const int q = tid + u * kThreads;
-    rid[u] = K(0);
-    if (q >= nv) continue;
-    s_off[q] = cnt[u];
-    s_rs[q] = start[u];
-    if (cnt[u]) rid[u] = rv_g[start[u]];
-    mymax = max(mymax, (int)cnt[u]);
-  }
-  if (mymax > 1) atomicMax(&s_maxcnt, mymax);
-  __syncthreads();
 
-  // exclusive scan of the tile's counts: thread tid owns rows [8 tid, 8 tid + 8)
-  {
-    constexpr int kPer = kJTile / kThreads;
-    uint64_t v[kPer];
-    uint64_t sum = 0;
+  // 3. the tile's total, its warps' prefixes and the chained scan over tiles
+  uint64_t mysum = 0;
+  uint32_t mymax = 0;
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int q = tid * kPer + i;
-      v[i] = q < nv ? s_off[q] : 0ull;
-      sum += v[i];
-    }
-    uint64_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wsum[warp] = x;
-    __syncthreads();
-    uint64_t pre = 0, tot = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      if (w < warp) pre += s_wsum[w];
-      tot += s_wsum[w];
-    }
-    uint64_t run = pre + x - sum;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int q = tid * kPer + i;
-      if (q < nv) s_off[q] = run;
-      run += v[i];
-    }
-    if (tid == 0) s_tot = tot;
+  for (int u = 0; u < kJItems; ++u) {
+    mysum += cnt[u];
+    mymax = max(mymax, cnt[u]);
   }
-  __syncthreads();
-  const uint64_t C = s_tot;
-
-  // chained scan over all join tiles (all jobs): this tile's first output index
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) mysum += __shfl_xor_sync(0xFFFFFFFFu, mysum, o);
+  if (lane == 0) s_wsum[warp] = mysum;
+  const bool multi = __syncthreads_or(mymax > 1u) != 0;  // also publishes s_wsum
+  uint64_t C = 0, wpre = 0;
+#pragma unroll
+  for (int w = 0; w < kJWarps; ++w) {
+    const uint64_t x = s_wsum[w];
+    if (w < warp) wpre += x;
+    C += x;
+  }
   if (tid == 0) {
     uint64_t* mine = lookback + t;
     uint64_t prefix = 0;
@@ -333,7 +391,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
     s_base = prefix;
     if (lt == 0 && job_out) job_out[j] = (int64_t)prefix;
-    if (t == total_tiles - 1) *total = (int64_t)(prefix + C);
+    // the end of this launch's output (absolute when the launch has a base)
+    if (t == total_tiles - 1) *total = (int64_t)(prefix + C) + (out_base ? *out_base : 0);
   }
   __syncthreads();
   // output index of this tile's first pair: the group's base (the partitioned
@@ -341,23 +400,79 @@ __global__ void __launch_bounds__(kThreads, 3)
   const uint64_t E = s_base + (out_base ? (uint64_t)*out_base : 0ull);
   if (E + C > (uint64_t)capacity) return;  // the host reports TJ_ERR_CAPACITY
 
-  K* __restrict__ o = out + 2 * E;
-  if (s_maxcnt <= 1) {
-    // at most one match per S row (e.g. a foreign-key join): row-wise writes
+  // 4. write
+  if (!multi) {
+    using P = typename PairOf<K>::type;
+    const bool vec = (((uintptr_t)out) & (2 * sizeof(K) - 1)) == 0;
+    const uint32_t ltm = lanemask_lt_j();
+    uint64_t off = E + wpre;
 #pragma unroll
-    for (int u = 0; u < kRows; ++u) {
-      const int q = tid + u * kThreads;
-      if (q >= nv) break;
-      const uint64_t off = s_off[q];
-      const bool hit = (q + 1 < nv ? s_off[q + 1] : C) > off;
-      if (hit) {
-        o[2 * off] = rid[u];
-        o[2 * off + 1] = sid[u];
+    for (int u = 0; u < kJItems; ++u) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, cnt[u] != 0u);
+      if (cnt[u] != 0u) {
+        const uint64_t o = off + __popc(m & ltm);
+        const K sid = s_sv[wbase + u * 32 + lane];
+        if (vec) {
+          P pr;
+          pr.x = rid[u];
+          pr.y = sid;
+          *reinterpret_cast<P*>(out + 2 * o) = pr;
+        } else {
+          out[2 * o] = rid[u];
+          out[2 * o + 1] = sid;
+        }
       }
+      off += __popc(m);
     }
   } else {
-    // general fan-out: output-wise, each output index finds its S row
-    for (uint64_t x = tid; x < C; x += kThreads) {
+    // many matches: per-row counts -> exclusive offsets, then each output
+    // index finds its S row by binary search
+    uint64_t* s_off = reinterpret_cast<uint64_t*>(s_rk);
+    uint32_t* s_rs = reinterpret_cast<uint32_t*>(s_off + kJTile);
+#pragma unroll
+    for (int u = 0; u < kJItems; ++u) {
+      const int q = wbase + u * 32 + lane;
+      if (q < nv) {
+        s_off[q] = cnt[u];
+        s_rs[q] = start[u];
+      }
+    }
+    __syncthreads();
+    {
+      constexpr int kPer = kJTile / kJThreads;
+      uint64_t v[kPer];
+      uint64_t sum = 0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int q = tid * kPer + i;
+        v[i] = q < nv ? s_off[q] : 0ull;
+        sum += v[i];
+      }
+      uint64_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      __syncthreads();  // every thread has read its counts
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      uint64_t pre = 0;
+#pragma unroll
+      for (int w = 0; w < kJWarps; ++w)
+        if (w < warp) pre += s_wsum[w];
+      uint64_t run = pre + x - sum;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int q = tid * kPer + i;
+        if (q < nv) s_off[q] = run;
+        run += v[i];
+      }
+    }
+    __syncthreads();
+    const K* __restrict__ sv_g = J.sv + row0;
+    K* __restrict__ o = out + 2 * E;
+    for (uint64_t x = tid; x < C; x += kJThreads) {
       int lo = 0, hi = nv - 1;  // last q with s_off[q] <= x
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -379,9 +494,37 @@ cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t t
                                int64_t* d_ra, int64_t* d_rb, cudaStream_t st,
                                const int32_t* d_tile_job) {
   if (total_tiles <= 0) return cudaSuccess;
-  const int64_t grid = (total_tiles + kThreads - 1) / kThreads;
+  const int64_t grid = (total_tiles * 32 + kThreads - 1) / kThreads;
   k_tile_ranges<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_ra, d_rb,
                                                         d_tile_job);
+  return cudaGetLastError();
+}
+
+// Tile -> job maps of one group of a partitioned join: blocks [0, nr) fill
+// the radix map from the radix jobs, the rest the join map from the join jobs.
+template <typename K>
+__global__ void k_group_maps(const RadixJob<K>* __restrict__ rjobs, int nr,
+                             int32_t* __restrict__ rmap, const JoinJob<K>* __restrict__ jjobs,
+                             int32_t* __restrict__ jmap) {
+  const int b = blockIdx.x;
+  if (b < nr) {
+    const int64_t t0 = rjobs[b].tile0;
+    const int64_t nt = (rjobs[b].n + kTile - 1) / kTile;
+    for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) rmap[t0 + t] = b;
+  } else {
+    const int j = b - nr;
+    const int64_t t0 = jjobs[j].tile0;
+    const int64_t nt = (jjobs[j].ns + kJTile - 1) / kJTile;
+    for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) jmap[t0 + t] = j;
+  }
+}
+
+template <typename K>
+cudaError_t launch_group_maps(const RadixJob<K>* d_rjobs, int nr, int32_t* d_rmap,
+                              const JoinJob<K>* d_jjobs, int nj, int32_t* d_jmap,
+                              cudaStream_t st) {
+  if (nr + nj <= 0) return cudaSuccess;
+  k_group_maps<K><<<nr + nj, 256, 0, st>>>(d_rjobs, nr, d_rmap, d_jjobs, d_jmap);
   return cudaGetLastError();
 }
 
@@ -410,20 +553,9 @@ cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_ti
                         int* d_err, cudaStream_t st, const int32_t* d_tile_job) {
   if (total_tiles <= 0) return cudaSuccess;
   const size_t smem = join_smem_bytes<K>();
-  k_join<K><<<(unsigned)total_tiles, kThreads, smem, st>>>(
+  k_join<K><<<(unsigned)total_tiles, kJThreads, smem, st>>>(
       d_jobs, num_jobs, total_tiles, d_ra, d_rb, d_lookback, d_tile_counter, out, capacity,
       d_out_base, d_job_out, d_total, d_err, d_tile_job);
-  return cudaGetLastError();
-}
-
-// base += group total (stream-ordered between the groups of a partitioned join)
-__global__ void k_add_base(int64_t* base, int64_t* total) {
-  *base += *total;
-  *total = 0;
-}
-
-cudaError_t launch_add_base(int64_t* d_base, int64_t* d_total, cudaStream_t st) {
-  k_add_base<<<1, 1, 0, st>>>(d_base, d_total);
   return cudaGetLastError();
 }
 
@@ -476,7 +608,9 @@ cudaError_t join_init_attributes() {
                                       const int64_t*, int64_t*, int64_t*, int*, cudaStream_t,     \
                                       const int32_t*);                                            \
   template cudaError_t launch_fix_job_out<K>(const JoinJob<K>*, int, int64_t, int64_t*,          \
-                                             const int64_t*, cudaStream_t);
+                                             const int64_t*, cudaStream_t);                     \
+  template cudaError_t launch_group_maps<K>(const RadixJob<K>*, int, int32_t*, const JoinJob<K>*, \
+                                            int, int32_t*, cudaStream_t);
 TJ_INSTANTIATE_JOIN(int32_t)
 TJ_INSTANTIATE_JOIN(int64_t)
 

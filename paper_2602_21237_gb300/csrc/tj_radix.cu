@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restric
 constexpr int kHistWords = 4096;
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __restrict__ jobs,
+__global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __restrict__ jobs,
                                                         int num_jobs, int64_t total_tiles,
                                                         const int32_t* __restrict__ tile_job,
                                                         int tile) {
@@ -188,6 +188,13 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __res
   __shared__ uint16_t s_tab[kRouteBuckets + 1];
   int cur = -1, passes = 0, ncuts = -1, hs = 0;
   U lo = 0;
+  int sh[kMaxPasses];
+  uint32_t mk[kMaxPasses];
+#pragma unroll
+  for (int p = 0; p < kMaxPasses; ++p) {
+    sh[p] = 0;
+    mk[p] = 0u;
+  }
   auto flush = [&](int job) {
     __syncthreads();
     for (int p = 0; p < passes; ++p)
@@ -218,6 +225,11 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __res
         s_mask[threadIdx.x] =
             threadIdx.x < passes ? (1u << jobs[j].bits[threadIdx.x]) - 1u : 0u;
       }
+#pragma unroll
+      for (int p = 0; p < kMaxPasses; ++p) {
+        sh[p] = p < passes ? jobs[j].shift[p] : 0;
+        mk[p] = p < passes ? (1u << jobs[j].bits[p]) - 1u : 0u;
+      }
       for (int i = threadIdx.x; i < passes * hs; i += kThreads) s_h[i] = 0;
       __syncthreads();
     }
@@ -240,8 +252,9 @@ __global__ void __launch_bounds__(kThreads) k_histogram(const RadixJob<K>* __res
           atomicAdd(&s_h[route_idx<K>(kv[u], lo, s_cuts, s_tab)], 1u);
         } else {
           const U x = (U)kv[u] - lo;
-          for (int p = 0; p < passes; ++p)
-            atomicAdd(&s_h[p * hs + ((uint32_t)(x >> s_shift[p]) & s_mask[p])], 1u);
+#pragma unroll
+          for (int p = 0; p < kMaxPasses; ++p)
+            if (p < passes) atomicAdd(&s_h[p * hs + ((uint32_t)(x >> sh[p]) & mk[p])], 1u);
         }
       }
     }
@@ -459,7 +472,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   const int hb = (bins + 1) >> 1;
   const uint32_t mask = (uint32_t)bins - 1u;
   const U lo = (U)J->lo;
-  uint32_t* lb_base = J->lookback;
+  uint32_t* lb_base = J->lookback + pass * J->lb_stride;
   uint32_t* lb_mine = lb_base + lt * bins;
 
   K* s_keys = reinterpret_cast<K*>(smem);
