@@ -31,7 +31,7 @@ constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (4096)
 constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass
-constexpr int kJTile = 2048;                // S rows per join tile
+constexpr int kJTile = 4096;                // S rows per join tile
 constexpr int kRCap = 2048;                 // R rows a join tile keeps on chip at once
 constexpr int kMaxChunks = 4;               // R chunks a join tile aligns on chip
 constexpr int kHTSlots = 4096;              // on-chip hash table slots (load <= 0.5)

@@ -1,7 +1,7 @@
 // Join of two key-sorted relations on their common key axis (paper Sec. 4.1)
 // with a single final materialisation of (r_id, s_id) pairs (Sec. 3.1).
 //
-//   k_tile_ranges : for every tile of 2048 sorted S rows, the range [a, b) of
+//   k_tile_ranges : for every tile of 4096 sorted S rows, the range [a, b) of
 //                   sorted R rows whose keys lie between the tile's first and
 //                   last key (two binary searches per tile).
 //   k_join        : per S tile, fused count -> scan -> write:
@@ -141,16 +141,16 @@ constexpr int kJItems = kJTile / kJThreads;     // S rows per thread
 static_assert(kJItems * kJThreads == kJTile, "join tile = threads x items");
 
 // Shared memory: S keys[kJTile] | S ids[kJTile] | R keys[kRCap] | R ids[kRCap]
-// | hash table[kHTSlots] u32.  After the probe the R region and the table are
-// free; the many-matches write path keeps per-row offsets (u64) and run
-// starts (u32) there.
+// | hash table[kHTSlots] u32.  After the probe the many-matches write path
+// (which reads ids from global memory) keeps per-row offsets (u64) and run
+// starts (u32) from the start of it.
 template <typename K>
 constexpr size_t join_smem_bytes() {
   return sizeof(K) * (size_t)(2 * kJTile + 2 * kRCap) + sizeof(uint32_t) * kHTSlots;
 }
-static_assert(sizeof(int32_t) * 2 * kRCap + sizeof(uint32_t) * kHTSlots >=
+static_assert(sizeof(int32_t) * (2 * kJTile + 2 * kRCap) + sizeof(uint32_t) * kHTSlots >=
                   (sizeof(uint64_t) + sizeof(uint32_t)) * kJTile,
-              "offsets and run starts fit where the R rows and the table were");
+              "offsets and run starts fit in the join's shared memory");
 
 // Asynchronous global -> shared copy of n elements (16-byte chunks when the
 // source allows it, else one element per copy); every thread of the CTA calls it.
@@ -177,7 +177,7 @@ template <typename K> struct PairOf;
 template <> struct PairOf<int32_t> { using type = int2; };
 template <> struct PairOf<int64_t> { using type = longlong2; };
 
-// One join tile: 2048 consecutive rows of sorted S against the range [a, b)
+// One join tile: 4096 consecutive rows of sorted S against the range [a, b)
 // of sorted R whose keys lie between the tile's first and last key.
 //   1. S keys and ids and the first chunk of the R range go to shared memory
 //      (cp.async); warp w owns S rows [w*32*kJItems, ...), item u = 32 rows;
@@ -187,7 +187,8 @@ template <> struct PairOf<int64_t> { using type = longlong2; };
 //      every S row probes it -> match count, run start and the R id of the
 //      first match; wider R ranges are binary-searched in global memory;
 //   3. the tile's total goes to the decoupled look-back chain over all tiles
-//      (thread 0), which yields the tile's first output index;
+//      (warp 0, 32 predecessors per round trip), which yields the tile's
+//      first output index;
 //   4. at most one match per row (a foreign-key join): each row's output index
 //      comes from ballots over the warp and the warps' totals; otherwise the
 //      tile's counts are scanned and each output index finds its S row.
@@ -240,12 +241,8 @@ __global__ void __launch_bounds__(kJThreads, 2)
   // 2. probe
   const int wbase = warp * 32 * kJItems;
   uint32_t cnt[kJItems], start[kJItems];
-  K rid[kJItems];
 #pragma unroll
-  for (int u = 0; u < kJItems; ++u) {
-    cnt[u] = start[u] = 0u;
-    rid[u] = K(0);
-  }
+  for (int u = 0; u < kJItems; ++u) cnt[u] = start[u] = 0u;
   if (onchip) {
     for (int64_t c = 0; c < nchunks; ++c) {
       const int c0 = (int)(c * kRCap);
@@ -298,10 +295,7 @@ __global__ void __launch_bounds__(kJThreads, 2)
           if (w == kHTEmpty) break;
           const uint32_t f = w & 0xFFFFu;
           if (s_rk[f] == key) {
-            if (cnt[u] == 0u) {
-              start[u] = (uint32_t)c0 + f;
-              rid[u] = s_rv[f];
-            }
+            if (cnt[u] == 0u) start[u] = (uint32_t)c0 + f;
             cnt[u] += (w >> 16) - f;
             break;
           }
@@ -322,7 +316,6 @@ __global__ void __launch_bounds__(kJThreads, 2)
       const int64_t hi = upper_bound_g(rk_g, nrr, key);
       start[u] = (uint32_t)lo;
       cnt[u] = (uint32_t)(hi - lo);
-      if (hi > lo) rid[u] = rv_g[lo];
     }
   }
 
@@ -345,41 +338,36 @@ __global__ void __launch_bounds__(kJThreads, 2)
     if (w < warp) wpre += x;
     C += x;
   }
-  if (tid == 0) {
+  // chained scan over all tiles by warp 0: each round trip reads the 32 newest
+  // predecessors not yet summed (lane l: tile k - l), sums the run of ready
+  // words up to the first inclusive one, and stops there
+  if (warp == 0) {
     uint64_t* mine = lookback + t;
     uint64_t prefix = 0;
     if (t == 0) {
-      st_volatile_u64(mine, kFlagInc64 | (C & kValMask64));
+      if (lane == 0) st_volatile_u64(mine, kFlagInc64 | (C & kValMask64));
     } else {
-      st_volatile_u64(mine, kFlagAgg64 | (C & kValMask64));
+      if (lane == 0) st_volatile_u64(mine, kFlagAgg64 | (C & kValMask64));
       int64_t k = t - 1;  // newest predecessor not yet summed
       int spins = 0;
-      bool done = false;
-      while (!done) {
-        uint64_t v[kLookWindow];
+      while (true) {
+        const int64_t idx = k - lane;
+        const uint64_t v = idx >= 0 ? ld_volatile_u64(lookback + idx) : kFlagInc64;
+        const uint64_t f = v & ~kValMask64;
+        const uint32_t notready = __ballot_sync(0xFFFFFFFFu, f == 0ull);
+        const uint32_t inc = __ballot_sync(0xFFFFFFFFu, f == kFlagInc64);
+        const int first_nr = notready ? __ffs(notready) - 1 : 32;
+        const int first_inc = inc ? __ffs(inc) - 1 : 32;
+        const int take = first_inc < first_nr ? first_inc + 1 : first_nr;  // lanes summed
+        uint64_t x = lane < take ? (v & kValMask64) : 0ull;
 #pragma unroll
-        for (int w = 0; w < kLookWindow; ++w)
-          v[w] = (k - w >= 0) ? ld_volatile_u64(lookback + (k - w)) : kFlagInc64;
-        int used = 0;
-        uint64_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < kLookWindow; ++w) {
-          if (used != w) break;
-          const uint64_t f = v[w] & ~kValMask64;
-          if (f == 0ull) break;
-          acc += v[w] & kValMask64;
-          ++used;
-          if (f == kFlagInc64) {
-            done = true;
-            break;
-          }
-        }
-        prefix += acc;
-        k -= used;
-        if (done || k < 0) break;
-        if (used == 0) {
+        for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        prefix += x;
+        if (first_inc < first_nr) break;
+        k -= take;
+        if (take == 0) {
           if (++spins > kSpinLimit) {
-            atomicExch(err, (int)TJ_ERR_TIMEOUT);
+            if (lane == 0) atomicExch(err, (int)TJ_ERR_TIMEOUT);
             break;
           }
           __nanosleep(32);
@@ -387,12 +375,14 @@ __global__ void __launch_bounds__(kJThreads, 2)
           spins = 0;
         }
       }
-      st_volatile_u64(mine, kFlagInc64 | ((prefix + C) & kValMask64));
+      if (lane == 0) st_volatile_u64(mine, kFlagInc64 | ((prefix + C) & kValMask64));
     }
-    s_base = prefix;
-    if (lt == 0 && job_out) job_out[j] = (int64_t)prefix;
-    // the end of this launch's output (absolute when the launch has a base)
-    if (t == total_tiles - 1) *total = (int64_t)(prefix + C) + (out_base ? *out_base : 0);
+    if (lane == 0) {
+      s_base = prefix;
+      if (lt == 0 && job_out) job_out[j] = (int64_t)prefix;
+      // the end of this launch's output (absolute when the launch has a base)
+      if (t == total_tiles - 1) *total = (int64_t)(prefix + C) + (out_base ? *out_base : 0);
+    }
   }
   __syncthreads();
   // output index of this tile's first pair: the group's base (the partitioned
@@ -405,6 +395,9 @@ __global__ void __launch_bounds__(kJThreads, 2)
     using P = typename PairOf<K>::type;
     const bool vec = (((uintptr_t)out) & (2 * sizeof(K) - 1)) == 0;
     const uint32_t ltm = lanemask_lt_j();
+    // R rows of the chunk still in shared memory (the last one) are read
+    // there, earlier ones from global memory
+    const int64_t cres = onchip && nchunks > 0 ? (nchunks - 1) * kRCap : INT64_MAX;
     uint64_t off = E + wpre;
 #pragma unroll
     for (int u = 0; u < kJItems; ++u) {
@@ -412,13 +405,15 @@ __global__ void __launch_bounds__(kJThreads, 2)
       if (cnt[u] != 0u) {
         const uint64_t o = off + __popc(m & ltm);
         const K sid = s_sv[wbase + u * 32 + lane];
+        const int64_t st0 = (int64_t)start[u];
+        const K rid = st0 >= cres ? s_rv[st0 - cres] : rv_g[st0];
         if (vec) {
           P pr;
-          pr.x = rid[u];
+          pr.x = rid;
           pr.y = sid;
           *reinterpret_cast<P*>(out + 2 * o) = pr;
         } else {
-          out[2 * o] = rid[u];
+          out[2 * o] = rid;
           out[2 * o + 1] = sid;
         }
       }
@@ -427,7 +422,7 @@ __global__ void __launch_bounds__(kJThreads, 2)
   } else {
     // many matches: per-row counts -> exclusive offsets, then each output
     // index finds its S row by binary search
-    uint64_t* s_off = reinterpret_cast<uint64_t*>(s_rk);
+    uint64_t* s_off = reinterpret_cast<uint64_t*>(smem);
     uint32_t* s_rs = reinterpret_cast<uint32_t*>(s_off + kJTile);
 #pragma unroll
     for (int u = 0; u < kJItems; ++u) {
