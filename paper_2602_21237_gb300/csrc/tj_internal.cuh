@@ -15,11 +15,11 @@ namespace tj {
 // ---- launch geometry -------------------------------------------------------
 constexpr int kThreads = 256;               // threads per CTA of most kernels (8 warps)
 constexpr int kWarps = kThreads / 32;
-#ifndef TJ_SORT_THREADS
-#define TJ_SORT_THREADS 512
+#ifndef TJ_SORT_THREADS  // 12 warps: three CTAs fit an SM (registers and shared memory)
+#define TJ_SORT_THREADS 384
 #endif
 #ifndef TJ_SORT_MINB
-#define TJ_SORT_MINB 2
+#define TJ_SORT_MINB 3
 #endif
 #ifndef TJ_SORT_ITEMS
 #define TJ_SORT_ITEMS 8
@@ -27,7 +27,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kSortThreads = TJ_SORT_THREADS;  // threads per onesweep CTA
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = TJ_SORT_ITEMS;          // rows per thread in a sort tile
-constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (4096)
+constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (3072)
 constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass

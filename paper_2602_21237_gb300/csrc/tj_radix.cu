@@ -308,14 +308,20 @@ __host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, i
                 : 0);
 }
 
-// Exclusive scan of in[0, bins) by a CTA of kSortThreads (bins <= 2 * kSortThreads).
+// Exclusive scan of in[0, bins) by a CTA of kSortThreads (bins <= kMaxBins):
+// thread t scans entries [t * kPer, (t + 1) * kPer).  Ends with a barrier.
 __device__ __forceinline__ void sort_block_excl_scan(const uint32_t* in, uint32_t* out, int bins,
                                                      uint32_t* s_warp) {
+  constexpr int kPer = (kMaxBins + kSortThreads - 1) / kSortThreads;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int d0 = tid * 2;
-  const uint32_t a = d0 < bins ? in[d0] : 0u;
-  const uint32_t b = d0 + 1 < bins ? in[d0 + 1] : 0u;
-  const uint32_t s = a + b;
+  const int d0 = tid * kPer;
+  uint32_t v[kPer];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    v[i] = d0 + i < bins ? in[d0 + i] : 0u;
+    s += v[i];
+  }
   uint32_t x = s;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -324,13 +330,15 @@ __device__ __forceinline__ void sort_block_excl_scan(const uint32_t* in, uint32_
   }
   if (lane == 31) s_warp[warp] = x;
   __syncthreads();
-  uint32_t wpre = 0;
+  uint32_t run = x - s;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w)
-    if (w < warp) wpre += s_warp[w];
-  const uint32_t excl = wpre + x - s;
-  if (d0 < bins) out[d0] = excl;
-  if (d0 + 1 < bins) out[d0 + 1] = excl + a;
+    if (w < warp) run += s_warp[w];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    if (d0 + i < bins) out[d0 + i] = run;
+    run += v[i];
+  }
   __syncthreads();
 }
 

@@ -1,7 +1,7 @@
 """GPU parity of tj_join_inner against the CPU oracle, element by element.
 
 Output order is fixed by the API (key, then S position, then R position), so
-the comparison is exact.  Sizes span several sort tiles (4096 rows) and join
+the comparison is exact.  Sizes span several sort tiles (3072 rows) and join
 tiles (4096 rows) with ragged tails; edge cases cover empty inputs, a single
 row, all-equal keys (no radix pass), disjoint key ranges, extreme and negative
 keys, duplicate-heavy fan-out, S sparse against R (the out-of-chip R range
@@ -35,8 +35,8 @@ def test_uniform_int32_1e6_full_size():
 
 
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
-@pytest.mark.parametrize("nr,ns", [(1, 1), (1, 5000), (4097, 1), (2047, 2049), (4096, 4096),
-                                   (4097, 12289), (100003, 77777)])
+@pytest.mark.parametrize("nr,ns", [(1, 1), (1, 5000), (4097, 1), (2047, 2049), (3072, 3073),
+                                   (4096, 4096), (4097, 12289), (100003, 77777)])
 def test_ragged_sizes(dtype, nr, ns):
     dom = max(4, (nr + ns) // 2)
     kr, ir, ks, is_ = datagen.uniform_pair(nr, ns, -dom, dom, 17 + nr + ns, dtype)
