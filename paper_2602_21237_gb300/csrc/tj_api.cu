@@ -693,7 +693,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     bool beyond = bkt == kRouteBuckets;
     if (bkt < 32) {
       start = (uint64_t)bkt;
-    } else if (bkt <= 192) {
+    } else if (bkt <= 6 * 32) {
       start = 32;
     } else {
       const int e = bkt >> 5, mnt = bkt & 31;
@@ -706,6 +706,13 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       const K sk = (K)(lo_bits<K>(lo) + start);
       tab[(size_t)bkt] = (uint16_t)(std::lower_bound(cuts.begin(), cuts.end(), sk) - cuts.begin());
     }
+  }
+  int route_steps = 0;  // halvings that empty the largest bucket
+  {
+    int widest = 0;
+    for (int bkt = 0; bkt < kRouteBuckets; ++bkt)
+      widest = std::max(widest, (int)tab[(size_t)bkt + 1] - (int)tab[(size_t)bkt]);
+    while ((1 << route_steps) <= widest) ++route_steps;
   }
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
@@ -782,6 +789,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     x.cuts = stg.at<K>(o_cuts);
     x.ncuts = ncuts;
     x.route_tab = stg.at<uint16_t>(o_tab);
+    x.route_steps = route_steps;
   }
   for (auto& g : cgroups) {
     int64_t t = 0, lbw = 0;

@@ -84,8 +84,11 @@ struct RadixJob {
   // Log-scale index over the cuts: with x = key - lo, bucket b(x) = x for
   // x < 32, else 32 * bitlen(x) + the 5 bits below x's leading one; bucket b
   // holds cuts [route_tab[b], route_tab[b + 1]).  Fine-grained at every
-  // magnitude, so clustered keys still find their cut in a few steps.
+  // magnitude, so clustered keys still find their cut in a few steps;
+  // route_steps = ceil(log2(largest bucket + 1)) halvings always suffice, so
+  // every lane runs the same number of them.
   const uint16_t* route_tab;  // kRouteBuckets + 1 entries
+  int32_t route_steps;
 };
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).

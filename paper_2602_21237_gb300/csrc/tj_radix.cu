@@ -65,34 +65,23 @@ __device__ __forceinline__ uint32_t digit_of(K key, typename UnsignedOf<K>::type
   return (uint32_t)((((U)key) - lo) >> shift) & mask;
 }
 
-// Number of cut keys <= key in a sorted table padded to kMaxCuts entries with
-// the key type's maximum (branch-free binary search; pads only count for the
-// maximum key and are clipped by ncuts).
-template <typename K>
-__device__ __forceinline__ uint32_t route_of(K key, const K* s_cuts, int ncuts) {
-  int pos = 0;
-#pragma unroll
-  for (int step = kMaxCuts / 2; step >= 1; step >>= 1)
-    if (s_cuts[pos + step - 1] <= key) pos += step;
-  return (uint32_t)min(pos, ncuts);
-}
-
 // Route through the radix index: the cuts <= key are all cuts before the key's
-// bucket plus those of its bucket that are <= key (a short binary search).
+// bucket plus those of its bucket that are <= key, found by `steps` halvings
+// of the bucket (the same count on every lane: no divergence).
 template <typename K>
 __device__ __forceinline__ uint32_t route_idx(K key, typename UnsignedOf<K>::type lo,
-                                              const K* s_cuts, const uint16_t* s_tab) {
+                                              const K* s_cuts, const uint16_t* s_tab, int steps) {
   using U = typename UnsignedOf<K>::type;
   const unsigned long long x = (unsigned long long)(U)((U)key - lo);
   const int nb = 64 - __clzll(x);  // significant bits of x
   const uint32_t b = nb < 6 ? (uint32_t)x : (uint32_t)((nb << 5) | ((x >> (nb - 6)) & 31ull));
-  int a = s_tab[b], e = s_tab[b + 1];
-  while (a < e) {
-    const int mid = (a + e) >> 1;
-    if (s_cuts[mid] <= key)
-      a = mid + 1;
-    else
-      e = mid;
+  int a = s_tab[b];
+  int n = (int)s_tab[b + 1] - a;
+  for (int i = 0; i < steps; ++i) {
+    const int half = n >> 1;
+    const bool go = n > 0 && s_cuts[a + half] <= key;  // a + half < ncuts when n > 0
+    a = go ? a + half + 1 : a;
+    n = go ? n - half - 1 : half;
   }
   return (uint32_t)a;
 }
@@ -186,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
   __shared__ uint32_t s_mask[kMaxPasses];
   __shared__ K s_cuts[kMaxCuts];
   __shared__ uint16_t s_tab[kRouteBuckets + 1];
-  int cur = -1, passes = 0, ncuts = -1, hs = 0;
+  int cur = -1, passes = 0, ncuts = -1, hs = 0, rsteps = 0;
   U lo = 0;
   int sh[kMaxPasses];
   uint32_t mk[kMaxPasses];
@@ -213,6 +202,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
       passes = jobs[j].passes;
       lo = (U)jobs[j].lo;
       ncuts = jobs[j].cuts ? jobs[j].ncuts : -1;
+      rsteps = jobs[j].route_steps;
       int mb = 0;
       for (int p = 0; p < passes; ++p) mb = max(mb, jobs[j].bits[p]);
       hs = 1 << mb;
@@ -249,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
       const int r = threadIdx.x + u * kThreads;
       if (r < row1) {
         if (ncuts >= 0) {
-          atomicAdd(&s_h[route_idx<K>(kv[u], lo, s_cuts, s_tab)], 1u);
+          atomicAdd(&s_h[route_idx<K>(kv[u], lo, s_cuts, s_tab, rsteps)], 1u);
         } else {
           const U x = (U)kv[u] - lo;
 #pragma unroll
@@ -297,14 +287,15 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 //   warp counters[kSortWarps][hb] u32   two 16-bit digit counters per word
 //   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
 //   [route passes only: cut keys[bins] K | radix index[kRouteBuckets + 8] u16 |
-//    digit of each tile-sorted slot[tile] u16]   (a route pass has < bins cuts)
+//    digit of each tile-sorted slot[tile] u8 (<= 256 bins) or u16]
+//   (a route pass has fewer than bins cuts)
 template <typename K>
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile) {
   return 2 * sizeof(K) * (size_t)tile + sizeof(uint16_t) * (size_t)tile +
          sizeof(uint32_t) * (size_t)kSortWarps * (size_t)((bins + 1) / 2) +
          sizeof(uint32_t) * 2 * (size_t)bins + sizeof(long long) * (size_t)bins +
          (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
-                      sizeof(uint16_t) * (size_t)tile
+                      (bins <= 256 ? 1 : 2) * (size_t)tile
                 : 0);
 }
 
@@ -492,7 +483,9 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   long long* s_gbase = reinterpret_cast<long long*>(s_excl + bins);
   K* s_cuts = reinterpret_cast<K*>(s_gbase + bins);
   uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_cuts + bins);
-  uint16_t* s_dig = s_tab + (kRouteBuckets + 8);
+  uint16_t* s_dig = s_tab + (kRouteBuckets + 8);  // u16 slots; u8 when bins <= 256
+  uint8_t* s_dig8 = reinterpret_cast<uint8_t*>(s_dig);
+  const bool dig8 = bins <= 256;
   const bool route = J->cuts != nullptr;
 
   // 1. tile -> shared memory (asynchronous), counters zeroed meanwhile
@@ -513,7 +506,8 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const K k = s_keys[wbase + i * 32 + lane];  // padding rows: unused values
-    dr[i] = route ? route_idx<K>(k, lo, s_cuts, s_tab) : digit_of<K>(k, lo, shift, mask);
+    dr[i] = route ? route_idx<K>(k, lo, s_cuts, s_tab, J->route_steps)
+                  : digit_of<K>(k, lo, shift, mask);
   }
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i)
@@ -572,7 +566,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
         const uint32_t wpre = (wx[d >> 1] >> ((d & 1u) * 16u)) & 0xFFFFu;
         const uint32_t pos = s_excl[d] + wpre + (dr[i] >> 16);
         s_src[pos] = (uint16_t)r;
-        if (route) s_dig[pos] = (uint16_t)d;
+        if (route) {
+          if (dig8)
+            s_dig8[pos] = (uint8_t)d;
+          else
+            s_dig[pos] = (uint16_t)d;
+        }
       }
     }
   }
@@ -615,7 +614,8 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   for (int q = tid; q < nvalid; q += kSortThreads) {
     const int r = s_src[q];
     const K k = s_keys[r];
-    const uint32_t d = route ? (uint32_t)s_dig[q] : digit_of<K>(k, lo, shift, mask);
+    const uint32_t d = route ? (dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q])
+                             : digit_of<K>(k, lo, shift, mask);
     const long long g = s_gbase[d] + q;
     dst_k[g] = k;
     dst_v[g] = s_vals[r];
