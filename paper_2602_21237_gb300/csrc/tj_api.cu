@@ -749,7 +749,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   const size_t o_cuts = cc.add<K>(kMaxCuts);
   const size_t o_tab = cc.add<uint16_t>(kRouteBuckets + 1);
   const size_t o_hist = cc.add<uint32_t>((size_t)nch * kMaxBins);
-  const size_t o_lb = cc.add<uint32_t>((size_t)(lb_max / 4));
   const size_t o_jobs = cc.add<RadixJob<K>>((size_t)nch * 2);
   const size_t o_misc = cc.add<int64_t>(32);
   Block stg;
@@ -791,12 +790,15 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     x.route_tab = stg.at<uint16_t>(o_tab);
     x.route_steps = route_steps;
   }
+  // route jobs' look-back words live in the working block, allocated once the
+  // groups are known: offsets now, pointers (and a second upload) later
+  std::vector<int64_t> route_lbw((size_t)nch, 0);
   for (auto& g : cgroups) {
     int64_t t = 0, lbw = 0;
     for (int c = g.first; c < g.second; ++c) {
       RadixJob<K> x = hj[(size_t)c];
       x.tile0 = t;
-      x.lookback = stg.at<uint32_t>(o_lb) + lbw;
+      route_lbw[(size_t)c] = lbw;
       t += ceil_div(x.n, kTile);
       lbw += ceil_div(x.n, kTile) << rbits;
       hj[(size_t)nch + c] = x;
@@ -842,25 +844,14 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
   TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_hist), hcount.data(), hcount.size() * 4,
                           cudaMemcpyHostToDevice, st));
-  for (auto& g : cgroups) {
-    int64_t t = 0;
-    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, kTile);
-    TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_lb), 0, (size_t)lb_max, st));
-    TJ_CUDA(cudaMemsetAsync(d_counters + kMaxPasses, 0, sizeof(uint32_t), st));
-    double rows = 0;
-    for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
-    tr.begin("route", 4.0 * w * rows);
-    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
-                               d_counters + kMaxPasses, d_err, st));
-    tr.end();
-  }
-  std::vector<uint32_t> hc2(2 * (size_t)kMaxBins, 0);  // partition sizes per side
-  for (int side = 0; side < 2; ++side)
-    for (int p2 = 0; p2 < nparts; ++p2)
-      hc2[(size_t)side * kMaxBins + p2] = (uint32_t)pcount[(size_t)side * nparts + p2];
-  hcount.swap(hc2);
 
   // ---- 3. batches and groups ----
+  // Memory after the route histogram: the routed copies (staging, reported
+  // apart) | route control (cuts, index, bases, jobs) | one working block
+  // shared by the route pass's look-back words and then every group's sort
+  // and join state | tables (every group's jobs, all digit histograms, the
+  // groups' output bases).  The budget bounds control + working block +
+  // tables, whichever pass runs.
   struct Part {
     int64_t r0, nr, s0, ns;
     K lo, hi;
@@ -870,11 +861,12 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     int np;      // passes (at least 1)
   };
   std::vector<Part> P;
-  int64_t r_at = 0, s_at = 0, maxrows = 0, live_rows = 0;
+  int64_t r_at = 0, s_at = 0, maxrows = 0;
+  size_t hist_words_all = 0;
   for (int j = 0; j < nparts; ++j) {
     Part q;
-    q.nr = hcount[(size_t)j];
-    q.ns = hcount[(size_t)kMaxBins + j];
+    q.nr = pcount[(size_t)j];
+    q.ns = pcount[(size_t)nparts + j];
     q.r0 = r_at;
     q.s0 = s_at;
     r_at += q.nr;
@@ -885,30 +877,35 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     q.hi = j == ncuts ? hi : std::min(hi, (K)(cuts[(size_t)j] - 1));
     q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd);
     // one sort buffer (the passes alternate between it and the batch's routed
-    // copy), one look-back region per pass, join tile state (ra, rb, chained
-    // words, tile map), the radix tile map, histograms, alignment
-    // (a group keeps one look-back region per pass of its deepest batch)
-    const int nb = std::min(q.plan.passes, 1);
+    // copy), one look-back region per pass (a group keeps as many as its
+    // deepest batch), join tile state (ra, rb, chained words, tile map), the
+    // radix tile map, alignment
     const int np = std::max(1, q.plan.passes);
     const int64_t bins = (int64_t)1 << q.plan.max_bits;
     const int64_t rtiles = ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile);
     q.lb = rtiles * bins * 4;
     q.np = np;
-    q.ws = (int64_t)nb * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) + ceil_div(q.ns, kJTile) * 28 +
-           rtiles * 4 + 2 * (int64_t)np * bins * 4 + 4096;
-    live_rows += q.nr + q.ns;
+    q.ws = (int64_t)std::min(q.plan.passes, 1) * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
+           ceil_div(q.ns, kJTile) * 28 + rtiles * 4 + 4096;
+    hist_words_all += 2 * (size_t)np * (size_t)bins;
     P.push_back(q);
   }
   if (r_at != nr || s_at != ns) return set_err(TJ_ERR_INTERNAL, "route counts do not add up");
   stats.max_partition = maxrows;
   stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
-  // route structures (look-back included) and every group's job tables
-  const int64_t fixed = (int64_t)(cc.off - staging) + 4096 +
-                        (int64_t)P.size() * (2 * (int64_t)sizeof(RadixJob<K>) +
-                                             (int64_t)sizeof(JoinJob<K>) + 64);
+  // tables: histogram-pass jobs and group jobs (radix), join jobs, histograms,
+  // output bases (one more than groups; at most one group per batch)
+  const size_t rj1 = P.size() * 2 * sizeof(RadixJob<K>);
+  const size_t t_rj = 0, t_rjh = t_rj + rj1, t_jj = t_rjh + rj1;
+  const size_t t_hist = (t_jj + P.size() * sizeof(JoinJob<K>) + 255) & ~(size_t)255;
+  const size_t t_base = (t_hist + hist_words_all * 4 + 255) & ~(size_t)255;
+  const size_t tbl_bytes = t_base + (P.size() + 1) * sizeof(int64_t);
+  const int64_t control = (int64_t)(cc.off - staging);
+  const int64_t fixed = control + (int64_t)tbl_bytes + 4096;
   const int64_t room = budget ? (int64_t)budget - fixed : INT64_MAX;
-  if (room <= 0) return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes",
-                                budget, (long long)fixed);
+  if (room <= 0 || (budget && lb_max > room))
+    return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes", budget,
+                   (long long)(fixed + lb_max));
   std::vector<std::pair<size_t, size_t>> groups;  // [first, last) into P
   int64_t ws_max = 0;
   for (size_t i = 0; i < P.size();) {
@@ -933,30 +930,51 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     i = j;
   }
   stats.groups = (int)groups.size();
-  stats.scratch_peak = (int64_t)(cc.off - staging) + ws_max;
+  const int64_t wk_bytes = std::max<int64_t>(std::max(ws_max, lb_max), 256);
+  stats.scratch_peak = control + wk_bytes + (int64_t)tbl_bytes;
+  Block wk;
+  TJ_CUDA(wk.alloc((size_t)wk_bytes, st));
+  for (int c = 0; c < nch; ++c)
+    hj[(size_t)nch + c].lookback = wk.at<uint32_t>(0) + route_lbw[(size_t)c];
+  TJ_CUDA(cudaMemcpyAsync(d_rj + nch, hj.data() + nch, (size_t)nch * sizeof(RadixJob<K>),
+                          cudaMemcpyHostToDevice, st));
 
-  // ---- 4. one batched sort + align per group ----
+  // ---- 4. the route pass (look-back words at the start of the working block) ----
+  for (auto& g : cgroups) {
+    int64_t t = 0;
+    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, kTile);
+    TJ_CUDA(cudaMemsetAsync(wk.p, 0, (size_t)lb_max, st));
+    TJ_CUDA(cudaMemsetAsync(d_counters + kMaxPasses, 0, sizeof(uint32_t), st));
+    double rows = 0;
+    for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
+    tr.begin("route", 4.0 * w * rows);
+    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
+                               d_counters + kMaxPasses, d_err, st));
+    tr.end();
+  }
+
+  // ---- 5. group plans: job tables, digit histograms of every batch in one launch ----
   // Group layout in the working block: the sort buffer of every batch | one
-  // zeroed region (tile counters, histograms, one look-back region per pass,
-  // chained join words) | join tile ranges | tile maps.  Every group's job
-  // tables are built first and uploaded once (from pinned memory) together
-  // with the groups' output bases, so the group loop below only enqueues a
-  // memset and six kernels per group.
+  // zeroed region (tile counters, one look-back region per pass, chained join
+  // words) | join tile ranges | tile maps.
   struct GroupPlan {
     size_t first, nj;
     size_t rj_at, jj_at;  // offsets into the uploaded tables
-    size_t o_zero, zero_bytes, o_cnt, o_hist, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
-    size_t hist_words, lb_words;
+    size_t o_zero, zero_bytes, o_cnt, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
+    size_t lb_words;
     int64_t tiles, jtiles;
     int P, maxbits;
     double rows, prow[kMaxPasses];
   };
-  Block wk;
-  TJ_CUDA(wk.alloc((size_t)std::max<int64_t>(ws_max, 256), st));
-  std::vector<RadixJob<K>> all_rj;
+  Block tbl;
+  TJ_CUDA(tbl.alloc(tbl_bytes + 256, st));
+  uint32_t* d_hist_all = reinterpret_cast<uint32_t*>(tbl.p + t_hist);
+  std::vector<RadixJob<K>> all_rj, all_rjh;
   std::vector<JoinJob<K>> all_jj;
   std::vector<GroupPlan> plans;
   int maxp = 0;
+  size_t hist_at = 0;
+  int64_t htiles = 0;
   for (auto& g : groups) {
     GroupPlan gp = {};
     gp.first = g.first;
@@ -973,13 +991,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         o_buf[i * 4 + 3] = gc.add<K>((size_t)q.ns);
       }
     }
-    std::vector<size_t> hist_at(nj * 2), lb_at(nj * 2);
+    std::vector<size_t> lb_at(nj * 2);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
       const size_t bins = (size_t)1 << q.plan.max_bits;
       for (int side = 0; side < 2; ++side) {
-        hist_at[i * 2 + side] = gp.hist_words;
-        gp.hist_words += (size_t)std::max(1, q.plan.passes) * bins;
         lb_at[i * 2 + side] = gp.lb_words;
         gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, kTile) * bins;
       }
@@ -990,7 +1006,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     for (size_t i = 0; i < nj; ++i) gp.jtiles += ceil_div(P[g.first + i].ns, kJTile);
     gp.o_cnt = gc.add<uint32_t>(kMaxPasses + 1);
     gp.o_zero = gp.o_cnt;
-    gp.o_hist = gc.add<uint32_t>(std::max<size_t>(gp.hist_words, 1));
     gp.o_lb = gc.add<uint32_t>(std::max<size_t>(gp.lb_words, 1) * (size_t)std::max(1, gp.P));
     gp.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     gp.zero_bytes = gc.off - gp.o_zero;
@@ -1009,17 +1024,21 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         K* v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
         x.keys = k0;
         x.n = n;
-        x.tile0 = gp.tiles;
-        gp.tiles += ceil_div(n, kTile);
         set_job_plan(x, q.plan);
         x.hist_stride = 1 << q.plan.max_bits;
-        x.hist = wk.at<uint32_t>(gp.o_hist) + hist_at[i * 2 + side];
+        x.hist = d_hist_all + hist_at;
+        hist_at += (size_t)std::max(1, q.plan.passes) << q.plan.max_bits;
         x.lookback = wk.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
         x.lb_stride = (int64_t)gp.lb_words;
         // passes alternate: routed copy -> buffer -> routed copy -> ...
         K* ak = q.plan.passes > 0 ? wk.at<K>(o_buf[i * 4 + 2 * side]) : nullptr;
         K* av = q.plan.passes > 0 ? wk.at<K>(o_buf[i * 4 + 2 * side + 1]) : nullptr;
         set_job_buffers(x, k0, v0, ak, av, k0, v0, &res[2 * side], &res[2 * side + 1]);
+        x.tile0 = htiles;  // the histogram launch numbers tiles over all groups
+        htiles += ceil_div(n, kTile);
+        all_rjh.push_back(x);
+        x.tile0 = gp.tiles;
+        gp.tiles += ceil_div(n, kTile);
         all_rj.push_back(x);
       }
       JoinJob<K> y;
@@ -1037,33 +1056,38 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     gp.o_rb = gc.add<int64_t>((size_t)gp.jtiles);
     gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
     gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
-    if ((int64_t)gc.off > std::max<int64_t>(ws_max, 256))
+    if ((int64_t)gc.off > wk_bytes)
       return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, working block has %lld", gc.off,
-                     (long long)ws_max);
+                     (long long)wk_bytes);
     maxp = std::max(maxp, gp.P);
     plans.push_back(gp);
   }
-  // one upload of every group's job tables and of the output bases: group g
-  // writes from base[g] on and its last join tile sets base[g + 1]
-  const size_t rj_bytes = all_rj.size() * sizeof(RadixJob<K>);
-  const size_t jj_bytes = all_jj.size() * sizeof(JoinJob<K>);
-  const size_t base_at = (rj_bytes + jj_bytes + 15) & ~(size_t)15;
-  const size_t base_bytes = (plans.size() + 1) * sizeof(int64_t);
-  Block tbl;
-  TJ_CUDA(tbl.alloc(base_at + base_bytes + 256, st));
+  if (hist_at != hist_words_all || all_rj.size() * sizeof(RadixJob<K>) != rj1)
+    return set_err(TJ_ERR_INTERNAL, "group tables do not add up");
+  // one upload of every table (group g writes from base[g] on and its last
+  // join tile sets base[g + 1]), then all digit histograms in one launch
   {
     unsigned char* h = nullptr;
-    TJ_CUDA(pinned_staging(base_at + base_bytes, &h));
-    memcpy(h, all_rj.data(), rj_bytes);
-    memcpy(h + rj_bytes, all_jj.data(), jj_bytes);
-    memset(h + base_at, 0, base_bytes);
-    TJ_CUDA(cudaMemcpyAsync(tbl.p, h, base_at + base_bytes, cudaMemcpyHostToDevice, st));
+    TJ_CUDA(pinned_staging(t_hist, &h));
+    memcpy(h + t_rj, all_rj.data(), rj1);
+    memcpy(h + t_rjh, all_rjh.data(), rj1);
+    memcpy(h + t_jj, all_jj.data(), all_jj.size() * sizeof(JoinJob<K>));
+    TJ_CUDA(cudaMemcpyAsync(tbl.p, h, t_hist, cudaMemcpyHostToDevice, st));
     TJ_CUDA(cudaEventRecord(pinned_event(), st));  // the staging buffer is busy until here
+    TJ_CUDA(cudaMemsetAsync(tbl.p + t_hist, 0, tbl_bytes - t_hist, st));
   }
-  RadixJob<K>* d_rj_all = tbl.at<RadixJob<K>>(0);
-  JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + rj_bytes);
-  int64_t* d_gbase = reinterpret_cast<int64_t*>(tbl.p + base_at);
-  stats.scratch_peak += (int64_t)(base_at + base_bytes);
+  RadixJob<K>* d_rj_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rj);
+  RadixJob<K>* d_rjh_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rjh);
+  JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + t_jj);
+  int64_t* d_gbase = reinterpret_cast<int64_t*>(tbl.p + t_base);
+  if (maxp > 0) {
+    tr.begin("histogram", w * (double)(nr + ns));
+    TJ_CUDA(launch_histogram<K>(d_rjh_all, (int)all_rjh.size(), htiles, st));
+    tr.end();
+    TJ_CUDA(launch_digit_scan<K>(d_rjh_all, (int)all_rjh.size(), maxp, st));
+  }
+
+  // ---- 6. one batched sort + align per group: a memset and five kernels ----
   for (size_t g = 0; g < plans.size(); ++g) {
     const GroupPlan& gp = plans[g];
     const size_t nj = gp.nj;
@@ -1074,17 +1098,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     int32_t* d_jmap = wk.at<int32_t>(gp.o_jmap);
     TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_zero, 0, gp.zero_bytes, st));
     TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, st));
-    if (gp.P > 0) {
-      tr.begin("histogram", w * gp.rows);
-      TJ_CUDA(launch_histogram<K>(d_gj, (int)(2 * nj), gp.tiles, st, d_tmap));
+    for (int p = 0; p < gp.P; ++p) {
+      tr.begin("onesweep", 4.0 * w * gp.prow[p]);
+      TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
+                                 d_gcnt + p, d_err, st, d_tmap));
       tr.end();
-      TJ_CUDA(launch_digit_scan<K>(d_gj, (int)(2 * nj), gp.P, st));
-      for (int p = 0; p < gp.P; ++p) {
-        tr.begin("onesweep", 4.0 * w * gp.prow[p]);
-        TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
-                                   d_gcnt + p, d_err, st, d_tmap));
-        tr.end();
-      }
     }
     TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
                                   wk.at<int64_t>(gp.o_rb), st, d_jmap));

@@ -122,17 +122,14 @@ __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restric
                                                     KeyStats* __restrict__ stats, int tile) {
   __shared__ unsigned long long s_mn[kWarps], s_mx[kWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    const int j = find_job(jobs, num_jobs, t);
-    const K* __restrict__ keys = jobs[j].keys;
-    const int64_t row0 = (t - jobs[j].tile0) * tile;
-    const int64_t row1 = min(jobs[j].n, row0 + tile);
-    unsigned long long mn = ~0ull, mx = 0ull;
-    for (int64_t r = row0 + threadIdx.x; r < row1; r += kThreads) {
-      const unsigned long long u = order_u(keys[r]);
-      mn = u < mn ? u : mn;
-      mx = u > mx ? u : mx;
-    }
+  // a contiguous run of tiles per CTA: one reduction and one pair of atomics
+  // per job the run touches
+  const int64_t per = (total_tiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * per, t1 = min(total_tiles, t0 + per);
+  int cur = -1;
+  int64_t cur_end = 0;  // first tile after the current job
+  unsigned long long mn = ~0ull, mx = 0ull;
+  auto flush = [&]() {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long a = __shfl_xor_sync(0xFFFFFFFFu, mn, o);
@@ -150,11 +147,30 @@ __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restric
         mn = s_mn[w] < mn ? s_mn[w] : mn;
         mx = s_mx[w] > mx ? s_mx[w] : mx;
       }
-      atomicMin(&stats[j].min_u, mn);
-      atomicMin(&stats[j].max_u, ~mx);  // stored inverted so both fields use atomicMin
+      atomicMin(&stats[cur].min_u, mn);
+      atomicMin(&stats[cur].max_u, ~mx);  // stored inverted so both fields use atomicMin
     }
     __syncthreads();
+    mn = ~0ull;
+    mx = 0ull;
+  };
+  for (int64_t t = t0; t < t1; ++t) {
+    if (cur < 0 || t >= cur_end) {
+      if (cur >= 0) flush();
+      cur = find_job(jobs, num_jobs, t);
+      cur_end = jobs[cur].tile0 + (jobs[cur].n + tile - 1) / tile;
+    }
+    const K* __restrict__ keys = jobs[cur].keys;
+    const int64_t row0 = (t - jobs[cur].tile0) * tile;
+    const int64_t row1 = min(jobs[cur].n, row0 + tile);
+#pragma unroll 4
+    for (int64_t r = row0 + threadIdx.x; r < row1; r += kThreads) {
+      const unsigned long long u = order_u(keys[r]);
+      mn = u < mn ? u : mn;
+      mx = u > mx ? u : mx;
+    }
   }
+  if (cur >= 0) flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -192,8 +208,10 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
         if (c) atomicAdd(&jobs[job].hist[p * jobs[job].hist_stride + d], c);
       }
   };
-  // grid-stride over tiles: one flush per job a CTA touched
-  for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+  // a contiguous run of tiles per CTA: one flush per job the run touches
+  const int64_t per = (total_tiles + gridDim.x - 1) / gridDim.x;
+  const int64_t t_end = min(total_tiles, (int64_t)(blockIdx.x + 1) * per);
+  for (int64_t t = (int64_t)blockIdx.x * per; t < t_end; ++t) {
     const int j = tile_job ? tile_job[t] : find_job(jobs, num_jobs, t);
     if (j != cur) {
       if (cur >= 0) flush(cur);
