@@ -425,9 +425,9 @@ __device__ __forceinline__ void rank_items(uint32_t (&dr)[ITEMS], int nv, uint32
     for (int b = 0; b < NB; ++b) {
 #pragma unroll
       for (int h = 0; h < kHalf; ++h) {
-        const bool one = (dr[i0 + h] >> b) & 1u;
-        const uint32_t x = __ballot_sync(0xFFFFFFFFu, one);
-        peers[h] &= one ? x : ~x;
+        const int32_t m = (int32_t)(dr[i0 + h] << (31 - b)) >> 31;  // bit b: -1, else 0
+        const uint32_t x = __ballot_sync(0xFFFFFFFFu, m != 0);
+        peers[h] &= ~(x ^ (uint32_t)m);  // lanes whose bit b equals this lane's
       }
     }
 #pragma unroll
