@@ -49,8 +49,19 @@ constexpr int kSpinLimit = 1 << 22;
 // key-range partitions of one route pass: cuts <= 1023 -> digits of <= 10 bits
 constexpr int kMaxCuts = 1024;
 constexpr int kRouteBuckets = 65 * 32;  // b(x) < 32 * 65
-// predecessors read per look-back round trip
-constexpr int kLookWindow = 8;
+// predecessors a onesweep digit reads per look-back round trip: the first
+// window is issued before the tile's slots are recorded, later ones after.
+// Every word read is a separate L2 sector (one predecessor tile each), so wide
+// windows cost more in load traffic than they save in round trips; 4 and 8
+// measured fastest on GB300 (windows of 16 or 32 were 3-10% slower).
+#ifndef TJ_LB_FIRST
+#define TJ_LB_FIRST 4
+#endif
+#ifndef TJ_LB_WIDE
+#define TJ_LB_WIDE 8
+#endif
+constexpr int kLookWindow = TJ_LB_FIRST;
+constexpr int kLookWide = TJ_LB_WIDE;
 
 template <typename K> struct UnsignedOf;
 template <> struct UnsignedOf<int32_t> { using type = uint32_t; };

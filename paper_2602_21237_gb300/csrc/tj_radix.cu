@@ -467,7 +467,6 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   using U = typename UnsignedOf<K>::type;
   constexpr int TILE = kSortThreads * ITEMS;
   static_assert(TILE <= 65536, "slot indices are 16-bit");
-  constexpr int kLookWide = 16;  // predecessors per round trip after the first
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_warp[kSortWarps];
   __shared__ uint32_t s_t;
