@@ -84,7 +84,7 @@ typedef enum {
 
 typedef struct {
   int32_t router;        /* tj_router */
-  int32_t partitions;    /* key-range batches requested, 2..1024 (0 = 256) */
+  int32_t partitions;    /* key-range batches requested, 2..1024 (0 = 128) */
   int32_t sample_stride; /* sample one row in this many (0 = 100, a 1% sample) */
   int32_t pla_segments;  /* segments of the piecewise-linear CDF (0 = 4096) */
   int32_t mlp_steps;     /* Adam steps of the MLP (0 = 600) */

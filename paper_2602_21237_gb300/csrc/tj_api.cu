@@ -338,7 +338,7 @@ void set_job_buffers(RadixJob<K>& j, const K* in_k, const K* in_v, K* ak, K* av,
 // ---- inner join -------------------------------------------------------------------
 struct Opts {
   int router = TJ_ROUTE_AUTO;
-  int partitions = 256;
+  int partitions = 128;
   int stride = 100;
   int segments = 4096;
   int mlp_steps = 600;

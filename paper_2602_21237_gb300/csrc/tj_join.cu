@@ -16,7 +16,8 @@
 //                     5. write the pairs, ordered by key, S position, R
 //                        position, if they fit the caller's capacity.
 //                   Tiles whose R range exceeds the on-chip chunks (S sparse
-//                   against R) binary-search each key in global memory instead.
+//                   against R) search a strided sample of the range on chip,
+//                   then one stride of R in global memory.
 #include "tj_internal.cuh"
 
 namespace tj {
@@ -30,32 +31,6 @@ __device__ __forceinline__ int find_job_j(const Job* jobs, int num_jobs, int64_t
       lo = mid;
     else
       hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename K>
-__device__ __forceinline__ int64_t lower_bound_g(const K* __restrict__ a, int64_t n, K key) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (a[mid] < key)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
-template <typename K>
-__device__ __forceinline__ int64_t upper_bound_g(const K* __restrict__ a, int64_t n, K key) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (key < a[mid])
-      hi = mid;
-    else
-      lo = mid + 1;
   }
   return lo;
 }
@@ -185,7 +160,8 @@ template <> struct PairOf<int64_t> { using type = longlong2; };
 //      open-addressing table of the chunk's distinct keys is built with
 //      shared-memory atomicCAS (slot -> first and end of the key's run), and
 //      every S row probes it -> match count, run start and the R id of the
-//      first match; wider R ranges are binary-searched in global memory;
+//      first match; wider R ranges are searched through a strided sample
+//      staged on chip, then within one stride in global memory;
 //   3. the tile's total goes to the decoupled look-back chain over all tiles
 //      (warp 0, 32 predecessors per round trip), which yields the tile's
 //      first output index;
@@ -305,17 +281,56 @@ __global__ void __launch_bounds__(kJThreads, 2)
     }
     if (nchunks == 0) asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
+    // Wide R range (S sparse against R): every stride-th R key goes to shared
+    // memory; a row's bound is found among those samples on chip, then inside
+    // one stride of R in global memory, all rows of a thread in lockstep
+    // (independent loads in flight together).
+    const int64_t stride = (nrr + kRCap - 1) / kRCap;
+    const int m = (int)((nrr + stride - 1) / stride);
+    for (int i = tid; i < m; i += kJThreads) s_rk[i] = rk_g[(int64_t)i * stride];
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
+    int steps = 0;  // halvings that empty a range of `stride` rows
+    while (((int64_t)1 << steps) <= stride) ++steps;
 #pragma unroll
-    for (int u = 0; u < kJItems; ++u) {
-      const int q = wbase + u * 32 + lane;
-      if (q >= nv) continue;
-      const K key = s_sk[q];
-      const int64_t lo = lower_bound_g(rk_g, nrr, key);
-      const int64_t hi = upper_bound_g(rk_g, nrr, key);
-      start[u] = (uint32_t)lo;
-      cnt[u] = (uint32_t)(hi - lo);
+    for (int bound = 0; bound < 2; ++bound) {  // 0: first R key >= key, 1: first R key > key
+      int64_t lo[kJItems];
+      int n[kJItems];
+      K key[kJItems];
+#pragma unroll
+      for (int u = 0; u < kJItems; ++u) {
+        const int q = wbase + u * 32 + lane;
+        key[u] = q < nv ? s_sk[q] : K(0);
+        // samples before j satisfy the predicate (sample < key, or <= key)
+        int a = 0, c = m;
+        while (a < c) {
+          const int mid = (a + c) >> 1;
+          const bool pr = bound ? !(key[u] < s_rk[mid]) : (s_rk[mid] < key[u]);
+          a = pr ? mid + 1 : a;
+          c = pr ? c : mid;
+        }
+        // rows up to sample a - 1 satisfy it, sample a (if any) does not
+        lo[u] = a == 0 ? 0 : (int64_t)(a - 1) * stride + 1;
+        const int64_t hi = a == m ? nrr : (int64_t)a * stride;
+        n[u] = (int)(hi - lo[u]);
+      }
+      for (int it = 0; it < steps; ++it) {
+#pragma unroll
+        for (int u = 0; u < kJItems; ++u) {
+          const int half = n[u] >> 1;
+          const K r = rk_g[min(lo[u] + half, nrr - 1)];  // in range even when n == 0
+          const bool go = n[u] > 0 && (bound ? !(key[u] < r) : (r < key[u]));
+          lo[u] = go ? lo[u] + half + 1 : lo[u];
+          n[u] = go ? n[u] - half - 1 : half;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kJItems; ++u) {
+        if (bound == 0)
+          start[u] = (uint32_t)lo[u];
+        else
+          cnt[u] = wbase + u * 32 + lane < nv ? (uint32_t)(lo[u] - (int64_t)start[u]) : 0u;
+      }
     }
   }
 

@@ -92,13 +92,18 @@ def test_duplicate_fanout(dtype):
     assert got.shape[0] > 1_000_000
 
 
-def test_s_sparse_against_r_uses_global_search():
-    # each S tile spans far more than the 4 x 2048 R rows kept on chip
-    kr = torch.arange(300000, dtype=torch.int64)
-    ir = torch.arange(300000, dtype=torch.int64)
-    g = torch.Generator().manual_seed(9)
-    ks = torch.randint(-1000, 301000, (5000,), generator=g, dtype=torch.int64)
-    is_ = torch.arange(5000, dtype=torch.int64)
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
+@pytest.mark.parametrize("dup", [1, 3])
+@pytest.mark.parametrize("n_s", [1, 5000, 20000])
+def test_s_sparse_against_r_uses_sampled_search(dtype, dup, n_s):
+    # each S tile spans far more than the 4 x 2048 R rows kept on chip: the
+    # bounds come from a strided sample of the R range, then one stride of R;
+    # with dup > 1 every matching run has several R rows
+    kr = (torch.arange(300000 * dup, dtype=torch.int64) // dup).to(dtype)
+    ir = torch.arange(kr.numel(), dtype=dtype)
+    g = torch.Generator().manual_seed(9 + n_s)
+    ks = torch.randint(-1000, 301000, (n_s,), generator=g, dtype=torch.int64).to(dtype)
+    is_ = torch.arange(n_s, dtype=dtype)
     check(kr, ir, ks, is_)
 
 
