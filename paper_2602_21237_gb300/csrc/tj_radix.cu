@@ -180,6 +180,30 @@ __global__ void __launch_bounds__(kThreads) k_stats(const RadixJob<K>* __restric
 // 32-bit keys: <= 4 x 2^8 or 3 x 2^10; a route pass: 1 x 2^10)
 constexpr int kHistWords = 4096;
 
+// Counts of every pass's digit for the rows a thread loaded (P passes known at
+// compile time; NARROW: all digits lie in the low 32 bits of key - lo).
+template <typename K, int P, bool NARROW, int N>
+__device__ __forceinline__ void hist_rows(const K (&kv)[N], int row1,
+                                          typename UnsignedOf<K>::type lo, const int (&sh)[kMaxPasses],
+                                          const uint32_t (&mk)[kMaxPasses], uint32_t* s_h, int hs) {
+  using U = typename UnsignedOf<K>::type;
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    if ((int)threadIdx.x + u * kThreads < row1) {
+      if (NARROW) {
+        const uint32_t x = (uint32_t)kv[u] - (uint32_t)lo;
+#pragma unroll
+        for (int p = 0; p < P; ++p) atomicAdd(&s_h[p * hs + ((x >> sh[p]) & mk[p])], 1u);
+      } else {
+        const U x = (U)kv[u] - lo;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          atomicAdd(&s_h[p * hs + ((uint32_t)(x >> sh[p]) & mk[p])], 1u);
+      }
+    }
+  }
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __restrict__ jobs,
                                                         int num_jobs, int64_t total_tiles,
@@ -192,6 +216,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
   __shared__ K s_cuts[kMaxCuts];
   __shared__ uint16_t s_tab[kRouteBuckets + 1];
   int cur = -1, passes = 0, ncuts = -1, hs = 0, rsteps = 0;
+  bool narrow = false;
   U lo = 0;
   int sh[kMaxPasses];
   uint32_t mk[kMaxPasses];
@@ -238,6 +263,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
         sh[p] = p < passes ? jobs[j].shift[p] : 0;
         mk[p] = p < passes ? (1u << jobs[j].bits[p]) - 1u : 0u;
       }
+      narrow = passes > 0 && jobs[j].shift[passes - 1] + jobs[j].bits[passes - 1] <= 32;
       for (int i = threadIdx.x; i < passes * hs; i += kThreads) s_h[i] = 0;
       __syncthreads();
     }
@@ -252,19 +278,31 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
       const int r = threadIdx.x + u * kThreads;
       kv[u] = r < row1 ? kp[r] : K(0);
     }
+    if (ncuts >= 0) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int r = threadIdx.x + u * kThreads;
-      if (r < row1) {
-        if (ncuts >= 0) {
+      for (int u = 0; u < kU; ++u)
+        if ((int)threadIdx.x + u * kThreads < row1)
           atomicAdd(&s_h[route_idx<K>(kv[u], lo, s_cuts, s_tab, rsteps)], 1u);
-        } else {
-          const U x = (U)kv[u] - lo;
-#pragma unroll
-          for (int p = 0; p < kMaxPasses; ++p)
-            if (p < passes) atomicAdd(&s_h[p * hs + ((uint32_t)(x >> sh[p]) & mk[p])], 1u);
-        }
+    } else {
+#define TJ_HIST_CASE(P)                                                   \
+  case P:                                                                 \
+    if (narrow)                                                           \
+      hist_rows<K, P, true>(kv, row1, lo, sh, mk, s_h, hs);               \
+    else                                                                  \
+      hist_rows<K, P, false>(kv, row1, lo, sh, mk, s_h, hs);              \
+    break;
+      switch (passes) {
+        TJ_HIST_CASE(1)
+        TJ_HIST_CASE(2)
+        TJ_HIST_CASE(3)
+        TJ_HIST_CASE(4)
+        TJ_HIST_CASE(5)
+        TJ_HIST_CASE(6)
+        TJ_HIST_CASE(7)
+        TJ_HIST_CASE(8)
+        default: break;
       }
+#undef TJ_HIST_CASE
     }
   }
   if (cur >= 0) flush(cur);
