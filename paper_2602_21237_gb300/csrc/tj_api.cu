@@ -708,11 +708,33 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     }
   }
   int route_steps = 0;  // halvings that empty the largest bucket
+  int route_shift = -1;
   {
-    int widest = 0;
-    for (int bkt = 0; bkt < kRouteBuckets; ++bkt)
-      widest = std::max(widest, (int)tab[(size_t)bkt + 1] - (int)tab[(size_t)bkt]);
-    while ((1 << route_steps) <= widest) ++route_steps;
+    auto steps_for = [](const std::vector<uint16_t>& t, int nb) {
+      int widest = 0, st2 = 0;
+      for (int bkt = 0; bkt < nb; ++bkt)
+        widest = std::max(widest, (int)t[(size_t)bkt + 1] - (int)t[(size_t)bkt]);
+      while ((1 << st2) <= widest) ++st2;
+      return st2;
+    };
+    route_steps = steps_for(tab, kRouteBuckets);
+    // uniform index: bucket b covers x in [b << us, (b + 1) << us)
+    int us = 0;
+    while (us < 64 && (krange >> us) >= (uint64_t)(kRouteBuckets - 1)) ++us;
+    const int ub = (int)(krange >> us) + 1;  // buckets in use (<= kRouteBuckets - 1)
+    std::vector<uint16_t> utab(kRouteBuckets + 1, (uint16_t)ncuts);
+    for (int bkt = 0; bkt <= ub; ++bkt) {
+      const uint64_t start = (uint64_t)bkt << us;
+      if (start > krange) break;
+      const K sk = (K)(lo_bits<K>(lo) + start);
+      utab[(size_t)bkt] = (uint16_t)(std::lower_bound(cuts.begin(), cuts.end(), sk) - cuts.begin());
+    }
+    const int usteps = steps_for(utab, ub);
+    if (usteps < route_steps) {
+      tab.swap(utab);
+      route_steps = usteps;
+      route_shift = us;
+    }
   }
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
@@ -789,6 +811,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     x.ncuts = ncuts;
     x.route_tab = stg.at<uint16_t>(o_tab);
     x.route_steps = route_steps;
+    x.route_shift = route_shift;
   }
   // route jobs' look-back words live in the working block, allocated once the
   // groups are known: offsets now, pointers (and a second upload) later

@@ -98,8 +98,13 @@ struct RadixJob {
   // magnitude, so clustered keys still find their cut in a few steps;
   // route_steps = ceil(log2(largest bucket + 1)) halvings always suffice, so
   // every lane runs the same number of them.
+  // When the cuts are spread evenly enough, the index is uniform instead:
+  // route_shift >= 0 and bucket b(x) = x >> route_shift (at most
+  // kRouteBuckets buckets over the key range); the host keeps whichever index
+  // needs fewer halvings.
   const uint16_t* route_tab;  // kRouteBuckets + 1 entries
   int32_t route_steps;
+  int32_t route_shift;  // -1: log-scale index
 };
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).

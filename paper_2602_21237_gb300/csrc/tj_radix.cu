@@ -70,11 +70,20 @@ __device__ __forceinline__ uint32_t digit_of(K key, typename UnsignedOf<K>::type
 // of the bucket (the same count on every lane: no divergence).
 template <typename K>
 __device__ __forceinline__ uint32_t route_idx(K key, typename UnsignedOf<K>::type lo,
-                                              const K* s_cuts, const uint16_t* s_tab, int steps) {
+                                              const K* s_cuts, const uint16_t* s_tab, int steps,
+                                              int ushift) {
   using U = typename UnsignedOf<K>::type;
   const unsigned long long x = (unsigned long long)(U)((U)key - lo);
-  const int nb = 64 - __clzll(x);  // significant bits of x
-  const uint32_t b = nb < 6 ? (uint32_t)x : (uint32_t)((nb << 5) | ((x >> (nb - 6)) & 31ull));
+  uint32_t b;
+  if (ushift >= 0) {
+    // uniform index; keys of the range give b < kRouteBuckets - 1, the clamp
+    // keeps any other value (a tile's padding rows) inside the table
+    const unsigned long long u = x >> ushift;
+    b = u < (unsigned long long)(kRouteBuckets - 1) ? (uint32_t)u : (uint32_t)(kRouteBuckets - 1);
+  } else {
+    const int nb = 64 - __clzll(x);  // significant bits of x
+    b = nb < 6 ? (uint32_t)x : (uint32_t)((nb << 5) | ((x >> (nb - 6)) & 31ull));
+  }
   int a = s_tab[b];
   int n = (int)s_tab[b + 1] - a;
   for (int i = 0; i < steps; ++i) {
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
   __shared__ uint32_t s_mask[kMaxPasses];
   __shared__ K s_cuts[kMaxCuts];
   __shared__ uint16_t s_tab[kRouteBuckets + 1];
-  int cur = -1, passes = 0, ncuts = -1, hs = 0, rsteps = 0;
+  int cur = -1, passes = 0, ncuts = -1, hs = 0, rsteps = 0, rshift = -1;
   bool narrow = false;
   U lo = 0;
   int sh[kMaxPasses];
@@ -246,6 +255,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
       lo = (U)jobs[j].lo;
       ncuts = jobs[j].cuts ? jobs[j].ncuts : -1;
       rsteps = jobs[j].route_steps;
+      rshift = jobs[j].route_shift;
       int mb = 0;
       for (int p = 0; p < passes; ++p) mb = max(mb, jobs[j].bits[p]);
       hs = 1 << mb;
@@ -282,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_histogram(const RadixJob<K>* __
 #pragma unroll
       for (int u = 0; u < kU; ++u)
         if ((int)threadIdx.x + u * kThreads < row1)
-          atomicAdd(&s_h[route_idx<K>(kv[u], lo, s_cuts, s_tab, rsteps)], 1u);
+          atomicAdd(&s_h[route_idx<K>(kv[u], lo, s_cuts, s_tab, rsteps, rshift)], 1u);
     } else {
 #define TJ_HIST_CASE(P)                                                   \
   case P:                                                                 \
@@ -561,7 +571,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const K k = s_keys[wbase + i * 32 + lane];  // padding rows: unused values
-    dr[i] = route ? route_idx<K>(k, lo, s_cuts, s_tab, J->route_steps)
+    dr[i] = route ? route_idx<K>(k, lo, s_cuts, s_tab, J->route_steps, J->route_shift)
                   : digit_of<K>(k, lo, shift, mask);
   }
 #pragma unroll
