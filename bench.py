@@ -456,6 +456,22 @@ def extra_learned(scale):
                      "radix_passes": st["radix_passes"]}
     res["pairs"] = pairs
     res["radix_balance_estimated_from_sample"] = api.stats()["radix_balance"]
+    # under a device-memory budget the batches must each fit it: equal-width
+    # ranges of this skewed CDF put ~40% of the rows in one batch
+    budget = 1 << 30
+    under = {"mem_budget_bytes": budget}
+    for name in ("radix", "pla", "mlp"):
+        try:
+            ms, r = _events_ms(lambda: api.join_inner(kr, ir, ks, is_, out=out, router=name,
+                                                      partitions=1024, mem_budget_bytes=budget))
+            assert r.shape[0] == pairs
+            st = api.stats()
+            under[name] = {"ms": ms, "tuples_per_s": 2 * n / (ms / 1e3), "groups": st["groups"],
+                           "balance_max_over_mean": st["balance"],
+                           "scratch_peak_bytes": st["scratch_peak"]}
+        except api.TjError as e:
+            under[name] = {"status": f"{e.name}: {e.detail}"}
+    res["under_1GB_budget"] = under
     del kr, ir, ks, is_, out
     torch.cuda.empty_cache()
     return res

@@ -292,16 +292,20 @@ __global__ void __launch_bounds__(kJThreads, 2)
     __syncthreads();
     int steps = 0;  // halvings that empty a range of `stride` rows
     while (((int64_t)1 << steps) <= stride) ++steps;
+    K key[kJItems];
 #pragma unroll
-    for (int bound = 0; bound < 2; ++bound) {  // 0: first R key >= key, 1: first R key > key
-      int64_t lo[kJItems];
+    for (int u = 0; u < kJItems; ++u) {
+      const int q = wbase + u * 32 + lane;
+      key[u] = q < nv ? s_sk[q] : K(0);
+    }
+    // bound 0: first R row with key >= the row's key; 1: first with key >
+    // (offsets into the range: nrr < 2^30)
+    const int nr32 = (int)nrr;
+    auto search = [&](int bound, int (&lo)[kJItems]) {
       int n[kJItems];
-      K key[kJItems];
 #pragma unroll
       for (int u = 0; u < kJItems; ++u) {
-        const int q = wbase + u * 32 + lane;
-        key[u] = q < nv ? s_sk[q] : K(0);
-        // samples before j satisfy the predicate (sample < key, or <= key)
+        // samples before a satisfy the predicate (sample < key, or <= key)
         int a = 0, c = m;
         while (a < c) {
           const int mid = (a + c) >> 1;
@@ -310,27 +314,43 @@ __global__ void __launch_bounds__(kJThreads, 2)
           c = pr ? c : mid;
         }
         // rows up to sample a - 1 satisfy it, sample a (if any) does not
-        lo[u] = a == 0 ? 0 : (int64_t)(a - 1) * stride + 1;
-        const int64_t hi = a == m ? nrr : (int64_t)a * stride;
-        n[u] = (int)(hi - lo[u]);
+        lo[u] = a == 0 ? 0 : (int)((a - 1) * stride + 1);
+        const int hi = a == m ? nr32 : (int)(a * stride);
+        n[u] = hi - lo[u];
       }
       for (int it = 0; it < steps; ++it) {
 #pragma unroll
         for (int u = 0; u < kJItems; ++u) {
           const int half = n[u] >> 1;
-          const K r = rk_g[min(lo[u] + half, nrr - 1)];  // in range even when n == 0
+          const K r = rk_g[min(lo[u] + half, nr32 - 1)];  // in range even when n == 0
           const bool go = n[u] > 0 && (bound ? !(key[u] < r) : (r < key[u]));
           lo[u] = go ? lo[u] + half + 1 : lo[u];
           n[u] = go ? n[u] - half - 1 : half;
         }
       }
+    };
+    int lo[kJItems];
+    search(0, lo);
+    // a match and no equal key right after it: one match (the common case of
+    // unique R keys); otherwise the upper bound is searched too
+    uint32_t more = 0u;
 #pragma unroll
-      for (int u = 0; u < kJItems; ++u) {
-        if (bound == 0)
-          start[u] = (uint32_t)lo[u];
-        else
-          cnt[u] = wbase + u * 32 + lane < nv ? (uint32_t)(lo[u] - (int64_t)start[u]) : 0u;
-      }
+    for (int u = 0; u < kJItems; ++u) {
+      const bool valid = wbase + u * 32 + lane < nv;
+      const K r0 = rk_g[min(lo[u], nr32 - 1)];
+      const K r1 = rk_g[min(lo[u] + 1, nr32 - 1)];
+      const bool e0 = valid && lo[u] < nr32 && r0 == key[u];
+      const bool e1 = e0 && lo[u] + 1 < nr32 && r1 == key[u];
+      start[u] = (uint32_t)lo[u];
+      cnt[u] = e0 ? 1u : 0u;
+      more |= (e1 ? 1u : 0u) << u;
+    }
+    if (__any_sync(0xFFFFFFFFu, more != 0u)) {
+      int hi[kJItems];
+      search(1, hi);
+#pragma unroll
+      for (int u = 0; u < kJItems; ++u)
+        if ((more >> u) & 1u) cnt[u] = (uint32_t)(hi[u] - lo[u]);
     }
   }
 
