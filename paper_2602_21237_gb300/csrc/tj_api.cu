@@ -199,6 +199,10 @@ struct Block {
     st = s;
     return cudaMallocAsync((void**)&p, n ? n : 256, s);
   }
+  void release() {  // stream-ordered: later allocations may reuse the memory
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+  }
   template <typename T>
   T* at(size_t off) const {
     return reinterpret_cast<T*>(p + off);
@@ -345,7 +349,12 @@ struct Opts {
   int mlp_batch = 512;
   float mlp_lr = 3e-3f;
   uint64_t seed = 20260221ull;
+  bool exact_route = false;  // size the batch regions by a histogram, not the sample
 };
+
+// part_join_impl's request to be run again with exact batch sizes (a batch
+// outgrew the region its sample estimate gave it)
+constexpr tj_status kRouteAgain = (tj_status)100;
 
 Opts make_opts(const tj_join_opts* o) {
   Opts x;
@@ -457,6 +466,11 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
     po.router = router;
     tj_status ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, budget, po, out, cap,
                                      out_count, stats, tr, st);
+    if (ps == kRouteAgain) {
+      po.exact_route = true;
+      ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, budget, po, out, cap, out_count,
+                             stats, tr, st);
+    }
     if (ps == TJ_OK || ps == TJ_ERR_CAPACITY) {
       stats.out_count = *out_count;
       g_stats = stats;
@@ -578,6 +592,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   int parts = std::max(2, std::min(o.partitions, kMaxCuts));
   std::vector<K> cuts;
   int router = o.router;
+  std::vector<uint32_t> sample_cnt;  // per side and batch, when regions are sized by the sample
+  int64_t sample_m[2] = {0, 0};
   // ---- 1. cut keys ----
   if (router == TJ_ROUTE_PLA || router == TJ_ROUTE_MLP) {
     const int stride = o.stride;
@@ -591,6 +607,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     const size_t o_k = c.add<K>((size_t)m), o_v = c.add<K>((size_t)m), o_b = c.add<K>((size_t)parts);
     const size_t o_th = c.add<float>(kMlpParams), o_tab = c.add<float>(kMlpTable + 1);
     const size_t o_edges = c.add<int64_t>(kMaxCuts + 2);
+    const size_t o_scuts = c.add<K>(kMaxCuts), o_scnt = c.add<uint32_t>(2 * kMaxBins);
     Block sb;
     TJ_CUDA(sb.alloc(c.off, st));
     TJ_CUDA(launch_sample_gather<K>(kr, m_r, off_r, ks, m_s, off_s, stride, sb.at<K>(o_k),
@@ -657,6 +674,23 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       stats.radix_balance = (double)mx * (double)nb / (double)std::max<int64_t>(1, m);
     }
     cuts = make_cuts<K>(bnd);
+    // batch sizes per side estimated from the sample (regions sized ahead of
+    // the route pass, so it needs no histogram of its own)
+    if (!o.exact_route && cuts.size() <= 255) {
+      std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
+      std::copy(cuts.begin(), cuts.end(), hc.begin());
+      TJ_CUDA(cudaMemcpyAsync(sb.at<K>(o_scuts), hc.data(), kMaxCuts * sizeof(K),
+                              cudaMemcpyHostToDevice, st));
+      TJ_CUDA(cudaMemsetAsync(sb.at<uint32_t>(o_scnt), 0, 2 * kMaxBins * sizeof(uint32_t), st));
+      TJ_CUDA(launch_sample_route_counts<K>(sb.at<K>(o_k), sb.at<K>(o_v), m, m_r, sb.at<K>(o_scuts),
+                                            (int)cuts.size(), sb.at<uint32_t>(o_scnt), st));
+      sample_cnt.assign(2 * (size_t)kMaxBins, 0u);
+      TJ_CUDA(cudaMemcpyAsync(sample_cnt.data(), sb.at<uint32_t>(o_scnt),
+                              sample_cnt.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      TJ_CUDA(cudaStreamSynchronize(st));
+      sample_m[0] = m_r;
+      sample_m[1] = m_s;
+    }
   } else {  // TJ_ROUTE_RADIX
     router = TJ_ROUTE_RADIX;
     const int b = bitlen(range_of<K>(lo, hi));
@@ -742,6 +776,32 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   const int64_t all_tiles = ceil_div(std::max(nr, ns), kTile);
   const int64_t chunk_tiles = std::max<int64_t>(1, std::min(all_tiles, route_lb / lb_per_tile));
   const int64_t chunk_rows = chunk_tiles * kTile;  // <= max(n_r, n_s) rounded up to a tile
+  if ((int64_t)nr + ns >= ((int64_t)1 << 32))
+    return set_err(TJ_ERR_INVALID, "partitioned join needs n_r + n_s < 2^32");
+  // Batch regions in the routed copies: sized from the sample when the router
+  // sampled (est), else by a route histogram.  A sampled batch gets room for
+  // its sample count scaled to the side plus six standard deviations and a
+  // tile; the route pass drops and reports a row past its batch's region, and
+  // the join is then routed again with exact sizes.
+  const bool est = !sample_cnt.empty();
+  std::vector<int64_t> rcap(2 * (size_t)nparts, 0), rstart(2 * (size_t)nparts, 0);
+  int64_t side_rows[2] = {nr, ns};
+  if (est) {
+    for (int side = 0; side < 2; ++side) {
+      const double scale =
+          (double)(side ? ns : nr) / (double)std::max<int64_t>(1, sample_m[side]);
+      int64_t acc = 0;
+      for (int p2 = 0; p2 < nparts; ++p2) {
+        const double c = (double)sample_cnt[(size_t)side * kMaxBins + p2];
+        const int64_t k = (int64_t)std::ceil((c + 6.0 * std::sqrt(c) + 8.0) * scale) + kTile;
+        rcap[(size_t)side * nparts + p2] = k;
+        rstart[(size_t)side * nparts + p2] = acc;
+        acc += k;
+      }
+      side_rows[side] = acc;
+    }
+    if (side_rows[0] >= ((int64_t)1 << 32) || side_rows[1] >= ((int64_t)1 << 32)) return kRouteAgain;
+  }
   struct Chunk {
     int side;
     int64_t r0, n;
@@ -752,25 +812,29 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     for (int64_t r0 = 0; r0 < n; r0 += chunk_rows) chunks.push_back({side, r0, std::min(chunk_rows, n - r0)});
   }
   const int nch = (int)chunks.size();
-  // launch groups of chunks, each group's look-back within route_lb
+  // launch groups of chunks, each group's look-back within route_lb (one chunk
+  // per launch with sampled regions: a chunk starts where the last one ended)
   std::vector<std::pair<int, int>> cgroups;
   int64_t lb_max = 0;
   for (int i = 0; i < nch;) {
     int j = i;
     int64_t acc = 0;
-    while (j < nch && (j == i || acc + ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile <= route_lb))
+    while (j < nch && (j == i || (!est && acc + ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile <=
+                                               route_lb)))
       acc += ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile, ++j;
     cgroups.push_back({i, j});
     lb_max = std::max(lb_max, acc);
     i = j;
   }
   Carve cc;
-  const size_t o_rk = cc.add<K>((size_t)nr), o_rv = cc.add<K>((size_t)nr);
-  const size_t o_sk = cc.add<K>((size_t)ns), o_sv = cc.add<K>((size_t)ns);
+  const size_t o_rk = cc.add<K>((size_t)side_rows[0]), o_rv = cc.add<K>((size_t)side_rows[0]);
+  const size_t o_sk = cc.add<K>((size_t)side_rows[1]), o_sv = cc.add<K>((size_t)side_rows[1]);
   const size_t staging = cc.off;
   const size_t o_cuts = cc.add<K>(kMaxCuts);
   const size_t o_tab = cc.add<uint16_t>(kRouteBuckets + 1);
   const size_t o_hist = cc.add<uint32_t>((size_t)nch * kMaxBins);
+  const size_t o_rend = cc.add<uint32_t>(2 * (size_t)kMaxBins);  // regions' ends (est)
+  const size_t o_fin = cc.add<uint32_t>(2 * (size_t)kMaxBins);   // where the route ended (est)
   const size_t o_jobs = cc.add<RadixJob<K>>((size_t)nch * 2);
   const size_t o_misc = cc.add<int64_t>(32);
   Block stg;
@@ -812,6 +876,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     x.route_tab = stg.at<uint16_t>(o_tab);
     x.route_steps = route_steps;
     x.route_shift = route_shift;
+    x.route_end = est ? stg.at<uint32_t>(o_rend) + (size_t)ch.side * kMaxBins : nullptr;
   }
   // route jobs' look-back words live in the working block, allocated once the
   // groups are known: offsets now, pointers (and a second upload) later
@@ -831,26 +896,28 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   TJ_CUDA(cudaMemsetAsync(stg.p + o_misc, 0, 32 * sizeof(int64_t), st));
   TJ_CUDA(cudaMemcpyAsync(d_rj, hj.data(), hj.size() * sizeof(RadixJob<K>),
                           cudaMemcpyHostToDevice, st));
-  TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_hist), 0, (size_t)nch * kMaxBins * sizeof(uint32_t), st));
-  tr.begin("histogram", w * (nr + ns));
-  TJ_CUDA(launch_histogram<K>(d_rj, nch, tiles_all, st));
-  tr.end();
-  std::vector<uint32_t> hcount((size_t)nch * kMaxBins);
-  TJ_CUDA(cudaMemcpyAsync(hcount.data(), stg.at<uint32_t>(o_hist), hcount.size() * 4,
-                          cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
-  // partition sizes and every chunk's base per partition (partition-major,
-  // chunks in row order: the route is stable)
   std::vector<int64_t> pcount(2 * (size_t)nparts, 0);
-  for (int c = 0; c < nch; ++c)
-    for (int p2 = 0; p2 < nparts; ++p2)
-      pcount[(size_t)chunks[(size_t)c].side * nparts + p2] += hcount[(size_t)c * kMaxBins + p2];
-  {
+  std::vector<uint32_t> hcount((size_t)nch * kMaxBins, 0u);
+  std::vector<uint32_t> rend(2 * (size_t)kMaxBins, 0u), rfin(2 * (size_t)kMaxBins, 0u);
+  if (!est) {
+    TJ_CUDA(cudaMemsetAsync(stg.at<uint32_t>(o_hist), 0, (size_t)nch * kMaxBins * sizeof(uint32_t), st));
+    tr.begin("histogram", w * (nr + ns));
+    TJ_CUDA(launch_histogram<K>(d_rj, nch, tiles_all, st));
+    tr.end();
+    TJ_CUDA(cudaMemcpyAsync(hcount.data(), stg.at<uint32_t>(o_hist), hcount.size() * 4,
+                            cudaMemcpyDeviceToHost, st));
+    TJ_CUDA(cudaStreamSynchronize(st));
+    // partition sizes and every chunk's base per partition (partition-major,
+    // chunks in row order: the route is stable)
+    for (int c = 0; c < nch; ++c)
+      for (int p2 = 0; p2 < nparts; ++p2)
+        pcount[(size_t)chunks[(size_t)c].side * nparts + p2] += hcount[(size_t)c * kMaxBins + p2];
     std::vector<int64_t> run(2 * (size_t)nparts, 0);
     for (int side = 0; side < 2; ++side) {
       int64_t acc = 0;
       for (int p2 = 0; p2 < nparts; ++p2) {
         run[(size_t)side * nparts + p2] = acc;
+        rstart[(size_t)side * nparts + p2] = acc;
         acc += pcount[(size_t)side * nparts + p2];
       }
     }
@@ -862,19 +929,91 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         run[(size_t)side * nparts + p2] += cnt;
       }
     }
-    if ((int64_t)nr + ns >= ((int64_t)1 << 32))
-      return set_err(TJ_ERR_INVALID, "partitioned join needs n_r + n_s < 2^32");
+  } else {
+    // the first chunk of a side starts at its batches' region starts; a later
+    // chunk starts where the one before ended (chained on the device)
+    for (int side = 0; side < 2; ++side)
+      for (int p2 = 0; p2 < nparts; ++p2) {
+        const size_t i = (size_t)side * nparts + p2;
+        rend[(size_t)side * kMaxBins + p2] = (uint32_t)(rstart[i] + rcap[i]);
+        rfin[(size_t)side * kMaxBins + p2] = (uint32_t)rstart[i];
+      }
+    for (int c = 0; c < nch; ++c)
+      if (c == 0 || chunks[(size_t)c - 1].side != chunks[(size_t)c].side)
+        for (int p2 = 0; p2 < nparts; ++p2)
+          hcount[(size_t)c * kMaxBins + p2] =
+              (uint32_t)rstart[(size_t)chunks[(size_t)c].side * nparts + p2];
+    TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_rend), rend.data(), rend.size() * 4,
+                            cudaMemcpyHostToDevice, st));
+    TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_fin), rfin.data(), rfin.size() * 4,
+                            cudaMemcpyHostToDevice, st));
   }
   TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_hist), hcount.data(), hcount.size() * 4,
                           cudaMemcpyHostToDevice, st));
 
-  // ---- 3. batches and groups ----
-  // Memory after the route histogram: the routed copies (staging, reported
-  // apart) | route control (cuts, index, bases, jobs) | one working block
-  // shared by the route pass's look-back words and then every group's sort
-  // and join state | tables (every group's jobs, all digit histograms, the
-  // groups' output bases).  The budget bounds control + working block +
-  // tables, whichever pass runs.
+  // ---- 3. the route pass (look-back words in a block of their own) ----
+  // Memory: the routed copies (staging, reported apart) | route control (cuts,
+  // index, bases, jobs) | the route pass's look-back words, released before
+  // the groups' working block is taken | tables (every group's jobs, all digit
+  // histograms, the groups' output bases).  The budget bounds control + the
+  // larger of the two blocks + tables.
+  const int64_t control = (int64_t)(cc.off - staging);
+  if (budget && control + lb_max + 4096 > (int64_t)budget)
+    return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes", budget,
+                   (long long)(control + lb_max + 4096));
+  Block rlb;
+  TJ_CUDA(rlb.alloc((size_t)std::max<int64_t>(lb_max, 256), st));
+  for (int c = 0; c < nch; ++c)
+    hj[(size_t)nch + c].lookback = rlb.at<uint32_t>(0) + route_lbw[(size_t)c];
+  TJ_CUDA(cudaMemcpyAsync(d_rj + nch, hj.data() + nch, (size_t)nch * sizeof(RadixJob<K>),
+                          cudaMemcpyHostToDevice, st));
+  for (auto& g : cgroups) {
+    int64_t t = 0;
+    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, kTile);
+    TJ_CUDA(cudaMemsetAsync(rlb.p, 0, (size_t)lb_max, st));
+    TJ_CUDA(cudaMemsetAsync(d_counters + kMaxPasses, 0, sizeof(uint32_t), st));
+    double rows = 0;
+    for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
+    tr.begin("route", 4.0 * w * rows);
+    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
+                               d_counters + kMaxPasses, d_err, st, nullptr, kItems, est));
+    tr.end();
+    if (est) {  // where this chunk ended: the next chunk's bases, or the side's end
+      const int c = g.first, side = chunks[(size_t)c].side;
+      uint32_t* next = (c + 1 < nch && chunks[(size_t)c + 1].side == side)
+                           ? stg.at<uint32_t>(o_hist) + (size_t)(c + 1) * kMaxBins
+                           : stg.at<uint32_t>(o_fin) + (size_t)side * kMaxBins;
+      TJ_CUDA(launch_route_chain(stg.at<uint32_t>(o_hist) + (size_t)c * kMaxBins, rlb.at<uint32_t>(0),
+                                 t - 1, 1 << rbits, next, st));
+    }
+  }
+  if (est) {  // exact batch sizes
+    int h_err = 0;
+    TJ_CUDA(cudaMemcpyAsync(rfin.data(), stg.at<uint32_t>(o_fin), rfin.size() * 4,
+                            cudaMemcpyDeviceToHost, st));
+    TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TJ_CUDA(cudaStreamSynchronize(st));
+    if (h_err == TJ_ERR_CAPACITY) return kRouteAgain;
+    if (h_err) return set_err((tj_status)h_err, "device reported %d during the route pass", h_err);
+    for (int side = 0; side < 2; ++side)
+      for (int p2 = 0; p2 < nparts; ++p2) {
+        const size_t i = (size_t)side * nparts + p2;
+        pcount[i] = (int64_t)rfin[(size_t)side * kMaxBins + p2] - rstart[i];
+      }
+  }
+  {
+    int64_t tot[2] = {0, 0}, maxrows = 0;
+    for (int j = 0; j < nparts; ++j) {
+      tot[0] += pcount[(size_t)j];
+      tot[1] += pcount[(size_t)nparts + j];
+      maxrows = std::max<int64_t>(maxrows, pcount[(size_t)j] + pcount[(size_t)nparts + j]);
+    }
+    if (tot[0] != nr || tot[1] != ns) return set_err(TJ_ERR_INTERNAL, "route counts do not add up");
+    stats.max_partition = maxrows;
+    stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
+  }
+
+  // ---- 4. batches and groups ----
   struct Part {
     int64_t r0, nr, s0, ns;
     K lo, hi;
@@ -884,17 +1023,13 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     int np;      // passes (at least 1)
   };
   std::vector<Part> P;
-  int64_t r_at = 0, s_at = 0, maxrows = 0;
   size_t hist_words_all = 0;
   for (int j = 0; j < nparts; ++j) {
     Part q;
     q.nr = pcount[(size_t)j];
     q.ns = pcount[(size_t)nparts + j];
-    q.r0 = r_at;
-    q.s0 = s_at;
-    r_at += q.nr;
-    s_at += q.ns;
-    maxrows = std::max<int64_t>(maxrows, q.nr + q.ns);
+    q.r0 = rstart[(size_t)j];
+    q.s0 = rstart[(size_t)nparts + j];
     if (q.nr == 0 || q.ns == 0) continue;
     q.lo = j == 0 ? lo : std::max(lo, cuts[(size_t)j - 1]);
     q.hi = j == ncuts ? hi : std::min(hi, (K)(cuts[(size_t)j] - 1));
@@ -913,9 +1048,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     hist_words_all += 2 * (size_t)np * (size_t)bins;
     P.push_back(q);
   }
-  if (r_at != nr || s_at != ns) return set_err(TJ_ERR_INTERNAL, "route counts do not add up");
-  stats.max_partition = maxrows;
-  stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
   // tables: histogram-pass jobs and group jobs (radix), join jobs, histograms,
   // output bases (one more than groups; at most one group per batch)
   const size_t rj1 = P.size() * 2 * sizeof(RadixJob<K>);
@@ -923,12 +1055,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   const size_t t_hist = (t_jj + P.size() * sizeof(JoinJob<K>) + 255) & ~(size_t)255;
   const size_t t_base = (t_hist + hist_words_all * 4 + 255) & ~(size_t)255;
   const size_t tbl_bytes = t_base + (P.size() + 1) * sizeof(int64_t);
-  const int64_t control = (int64_t)(cc.off - staging);
   const int64_t fixed = control + (int64_t)tbl_bytes + 4096;
   const int64_t room = budget ? (int64_t)budget - fixed : INT64_MAX;
-  if (room <= 0 || (budget && lb_max > room))
-    return set_err(TJ_ERR_BUDGET, "budget %zu below the route pass's %lld bytes", budget,
-                   (long long)(fixed + lb_max));
+  if (room <= 0)
+    return set_err(TJ_ERR_BUDGET, "budget %zu below the join's tables and control (%lld bytes)",
+                   budget, (long long)fixed);
   std::vector<std::pair<size_t, size_t>> groups;  // [first, last) into P
   int64_t ws_max = 0;
   for (size_t i = 0; i < P.size();) {
@@ -953,28 +1084,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     i = j;
   }
   stats.groups = (int)groups.size();
-  const int64_t wk_bytes = std::max<int64_t>(std::max(ws_max, lb_max), 256);
-  stats.scratch_peak = control + wk_bytes + (int64_t)tbl_bytes;
+  const int64_t wk_bytes = std::max<int64_t>(ws_max, 256);
+  stats.scratch_peak = control + std::max<int64_t>(lb_max, wk_bytes + (int64_t)tbl_bytes);
+  rlb.release();
   Block wk;
   TJ_CUDA(wk.alloc((size_t)wk_bytes, st));
-  for (int c = 0; c < nch; ++c)
-    hj[(size_t)nch + c].lookback = wk.at<uint32_t>(0) + route_lbw[(size_t)c];
-  TJ_CUDA(cudaMemcpyAsync(d_rj + nch, hj.data() + nch, (size_t)nch * sizeof(RadixJob<K>),
-                          cudaMemcpyHostToDevice, st));
-
-  // ---- 4. the route pass (look-back words at the start of the working block) ----
-  for (auto& g : cgroups) {
-    int64_t t = 0;
-    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, kTile);
-    TJ_CUDA(cudaMemsetAsync(wk.p, 0, (size_t)lb_max, st));
-    TJ_CUDA(cudaMemsetAsync(d_counters + kMaxPasses, 0, sizeof(uint32_t), st));
-    double rows = 0;
-    for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
-    tr.begin("route", 4.0 * w * rows);
-    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
-                               d_counters + kMaxPasses, d_err, st));
-    tr.end();
-  }
 
   // ---- 5. group plans: job tables, digit histograms of every batch in one launch ----
   // Group layout in the working block: the sort buffer of every batch | one
@@ -1085,15 +1199,18 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     maxp = std::max(maxp, gp.P);
     plans.push_back(gp);
   }
-  if (hist_at != hist_words_all || all_rj.size() * sizeof(RadixJob<K>) != rj1)
+  // (tables were sized for every planned batch; batches found empty after a
+  // sampled route take no room)
+  const size_t rj_used = all_rj.size() * sizeof(RadixJob<K>);
+  if (hist_at > hist_words_all || rj_used > rj1)
     return set_err(TJ_ERR_INTERNAL, "group tables do not add up");
   // one upload of every table (group g writes from base[g] on and its last
   // join tile sets base[g + 1]), then all digit histograms in one launch
   {
     unsigned char* h = nullptr;
     TJ_CUDA(pinned_staging(t_hist, &h));
-    memcpy(h + t_rj, all_rj.data(), rj1);
-    memcpy(h + t_rjh, all_rjh.data(), rj1);
+    memcpy(h + t_rj, all_rj.data(), rj_used);
+    memcpy(h + t_rjh, all_rjh.data(), rj_used);
     memcpy(h + t_jj, all_jj.data(), all_jj.size() * sizeof(JoinJob<K>));
     TJ_CUDA(cudaMemcpyAsync(tbl.p, h, t_hist, cudaMemcpyHostToDevice, st));
     TJ_CUDA(cudaEventRecord(pinned_event(), st));  // the staging buffer is busy until here

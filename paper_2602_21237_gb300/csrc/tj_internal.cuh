@@ -105,6 +105,10 @@ struct RadixJob {
   const uint16_t* route_tab;  // kRouteBuckets + 1 entries
   int32_t route_steps;
   int32_t route_shift;  // -1: log-scale index
+  // Batch regions sized in advance (optional): rows of batch d go below
+  // route_end[d]; a row that would not is dropped and the pass reports
+  // TJ_ERR_CAPACITY, after which the caller routes again with exact sizes.
+  const uint32_t* route_end;
 };
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).
@@ -151,7 +155,7 @@ template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                             int pass, int max_bits, bool route, uint32_t* d_tile_counter,
                             int* d_err, cudaStream_t st, const int32_t* d_tile_job = nullptr,
-                            int items = kItems);
+                            int items = kItems, bool guard = false);
 
 // ---- launchers (tj_join.cu) -------------------------------------------------
 cudaError_t join_init_attributes();
@@ -181,6 +185,15 @@ cudaError_t launch_quantiles(const K* sorted, int64_t m, int G, int first, int l
 template <typename K>
 cudaError_t launch_sorted_bucket_edges(const K* sorted, int64_t m, uint64_t lo, int shift, int nb,
                                        int64_t* edges, cudaStream_t st);
+// counts[side * kMaxBins + p] += sample rows of the side (index < m_r: R) in batch p
+template <typename K>
+cudaError_t launch_sample_route_counts(const K* keys, const K* idx, int64_t m, int64_t m_r,
+                                       const K* cuts, int ncuts, uint32_t* counts,
+                                       cudaStream_t st);
+// next[d] = base[d] + the inclusive count of digit d over a route launch's
+// tiles (the last tile's look-back word), d < bins
+cudaError_t launch_route_chain(const uint32_t* base, const uint32_t* lookback, int64_t last_tile,
+                               int bins, uint32_t* next, cudaStream_t st);
 template <typename K>
 cudaError_t launch_fix_job_out(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                                int64_t* d_job_out, const int64_t* d_total, cudaStream_t st);

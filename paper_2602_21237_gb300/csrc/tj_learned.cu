@@ -9,6 +9,8 @@
 //                     linear CDF model; its partition boundaries for P | G are
 //                     the knots t_{(G/P) p}).
 //   MLP kernels     : see tj_mlp.cu.
+#include <algorithm>
+
 #include "tj_internal.cuh"
 
 namespace tj {
@@ -64,6 +66,45 @@ __global__ void k_sorted_bucket_edges(const K* __restrict__ sorted, int64_t m, u
   edges[d] = a;
 }
 
+// counts[side * kMaxBins + p]: sample rows of each side (sample index < m_r:
+// R) whose key lies in batch p (p = number of cuts <= key)
+template <typename K>
+__global__ void k_sample_route_counts(const K* __restrict__ keys, const K* __restrict__ idx,
+                                      int64_t m, int64_t m_r, const K* __restrict__ cuts,
+                                      int ncuts, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_c[2 * kMaxBins];
+  for (int i = threadIdx.x; i < 2 * kMaxBins; i += blockDim.x) s_c[i] = 0u;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const K key = keys[i];
+    int a = 0, b = ncuts;  // first cut > key
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (cuts[mid] <= key)
+        a = mid + 1;
+      else
+        b = mid;
+    }
+    const int side = (int64_t)idx[i] < m_r ? 0 : 1;
+    atomicAdd(&s_c[side * kMaxBins + a], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * kMaxBins; i += blockDim.x)
+    if (s_c[i]) atomicAdd(&counts[i], s_c[i]);
+}
+
+template <typename K>
+cudaError_t launch_sample_route_counts(const K* keys, const K* idx, int64_t m, int64_t m_r,
+                                       const K* cuts, int ncuts, uint32_t* counts,
+                                       cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>((m + kThreads - 1) / kThreads, 152 * 4);
+  k_sample_route_counts<K><<<(unsigned)grid, kThreads, 0, st>>>(keys, idx, m, m_r, cuts, ncuts,
+                                                                 counts);
+  return cudaGetLastError();
+}
+
 template <typename K>
 cudaError_t launch_sorted_bucket_edges(const K* sorted, int64_t m, uint64_t lo, int shift, int nb,
                                        int64_t* edges, cudaStream_t st) {
@@ -97,7 +138,9 @@ cudaError_t launch_quantiles(const K* sorted, int64_t m, int G, int first, int l
                                                int64_t, int, K*, K*, cudaStream_t);              \
   template cudaError_t launch_quantiles<K>(const K*, int64_t, int, int, int, int, K*, cudaStream_t); \
   template cudaError_t launch_sorted_bucket_edges<K>(const K*, int64_t, uint64_t, int, int,      \
-                                                     int64_t*, cudaStream_t);
+                                                     int64_t*, cudaStream_t);                   \
+  template cudaError_t launch_sample_route_counts<K>(const K*, const K*, int64_t, int64_t,       \
+                                                     const K*, int, uint32_t*, cudaStream_t);
 TJ_INSTANTIATE_LEARNED(int32_t)
 TJ_INSTANTIATE_LEARNED(int64_t)
 

@@ -353,15 +353,18 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 //   warp counters[kSortWarps][hb] u32   two 16-bit digit counters per word
 //   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
 //   [route passes only: cut keys[bins] K | radix index[kRouteBuckets + 8] u16 |
-//    digit of each tile-sorted slot[tile] u8 (<= 256 bins) or u16]
+//    digit of each tile-sorted slot[tile] u8 (<= 256 bins) or u16 |
+//    [end of each batch's region[bins] u32, when the regions are sized ahead]]
 //   (a route pass has fewer than bins cuts)
 template <typename K>
-__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile) {
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile,
+                                                         bool guard = false) {
   return 2 * sizeof(K) * (size_t)tile + sizeof(uint16_t) * (size_t)tile +
          sizeof(uint32_t) * (size_t)kSortWarps * (size_t)((bins + 1) / 2) +
          sizeof(uint32_t) * 2 * (size_t)bins + sizeof(long long) * (size_t)bins +
          (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
-                      (bins <= 256 ? 1 : 2) * (size_t)tile
+                      (bins <= 256 ? 1 : 2) * (size_t)tile +
+                      (guard ? sizeof(uint32_t) * (size_t)bins : 0)
                 : 0);
 }
 
@@ -550,6 +553,8 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_cuts + bins);
   uint16_t* s_dig = s_tab + (kRouteBuckets + 8);  // u16 slots; u8 when bins <= 256
   uint8_t* s_dig8 = reinterpret_cast<uint8_t*>(s_dig);
+  uint32_t* s_rend =  // end of each batch's region (route passes with sized regions)
+      reinterpret_cast<uint32_t*>(s_dig8 + (bins <= 256 ? 1 : 2) * TILE);
   const bool dig8 = bins <= 256;
   const bool route = J->cuts != nullptr;
 
@@ -557,9 +562,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   copy_rows_async<K>(s_keys, J->src_k[pass] + row0, nvalid);
   copy_rows_async<K>(s_vals, J->src_v[pass] + row0, nvalid);
   asm volatile("cp.async.commit_group;" ::: "memory");
+  const bool guard = route && J->route_end != nullptr;
   if (route) {
     for (int i = tid; i < bins; i += kSortThreads) s_cuts[i] = J->cuts[i];
     for (int i = tid; i <= kRouteBuckets; i += kSortThreads) s_tab[i] = J->route_tab[i];
+    if (guard)
+      for (int i = tid; i < bins; i += kSortThreads) s_rend[i] = J->route_end[i];
   }
   for (int i = tid; i < kSortWarps * hb + bins; i += kSortThreads) s_whist[i] = 0u;
   asm volatile("cp.async.wait_all;" ::: "memory");
@@ -675,6 +683,24 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   // 5. slots in order -> global
   K* __restrict__ dst_k = J->dst_k[pass];
   K* __restrict__ dst_v = J->dst_v[pass];
+  if (guard) {
+    // batch regions sized in advance: a row past its region's end is dropped
+    // and reported (the caller then routes again with exact sizes)
+    bool over = false;
+    for (int q = tid; q < nvalid; q += kSortThreads) {
+      const int r = s_src[q];
+      const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
+      const long long g = s_gbase[d] + q;
+      if (g >= (long long)s_rend[d]) {
+        over = true;
+        continue;
+      }
+      dst_k[g] = s_keys[r];
+      dst_v[g] = s_vals[r];
+    }
+    if (over) atomicCAS(err, 0, (int)TJ_ERR_CAPACITY);
+    return;
+  }
 #pragma unroll 4
   for (int q = tid; q < nvalid; q += kSortThreads) {
     const int r = s_src[q];
@@ -685,6 +711,22 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     dst_k[g] = k;
     dst_v[g] = s_vals[r];
   }
+}
+
+// next[d] = base[d] + inclusive count of digit d over one route launch's tiles
+__global__ void k_route_chain(const uint32_t* __restrict__ base,
+                              const uint32_t* __restrict__ lookback, int64_t last_tile, int bins,
+                              uint32_t* __restrict__ next) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= bins) return;
+  next[d] = base[d] + (lookback[last_tile * bins + d] & kValMask);
+}
+
+cudaError_t launch_route_chain(const uint32_t* base, const uint32_t* lookback, int64_t last_tile,
+                               int bins, uint32_t* next, cudaStream_t st) {
+  k_route_chain<<<(bins + kThreads - 1) / kThreads, kThreads, 0, st>>>(base, lookback, last_tile,
+                                                                       bins, next);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -739,14 +781,15 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                             int pass, int max_bits, bool route, uint32_t* d_tile_counter,
-                            int* d_err, cudaStream_t st, const int32_t* d_tile_job, int items) {
+                            int* d_err, cudaStream_t st, const int32_t* d_tile_job, int items,
+                            bool guard) {
   if (total_tiles <= 0) return cudaSuccess;
   if (items == 4) {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4);
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4, guard);
     k_onesweep<K, 4><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   } else {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route);
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTile, guard);
     k_onesweep<K, kItems><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   }
@@ -756,17 +799,17 @@ cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t tot
 cudaError_t radix_init_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_onesweep<int32_t, kItems>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)onesweep_smem_bytes<int32_t>(kMaxBins, true));
+                                       (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTile, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_onesweep<int64_t, kItems>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<int64_t>(kMaxBins, true));
+                           (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTile, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_onesweep<int32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kSortThreads * 4));
+                           (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kSortThreads * 4, true));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_onesweep<int64_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kSortThreads * 4));
+                              (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kSortThreads * 4, true));
 }
 
 #define TJ_INSTANTIATE_RADIX(K)                                                                 \
@@ -778,7 +821,8 @@ cudaError_t radix_init_attributes() {
                                                int);                                            \
   template cudaError_t launch_digit_scan<K>(const RadixJob<K>*, int, int, cudaStream_t);        \
   template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, bool,    \
-                                          uint32_t*, int*, cudaStream_t, const int32_t*, int);
+                                          uint32_t*, int*, cudaStream_t, const int32_t*, int,   \
+                                          bool);
 TJ_INSTANTIATE_RADIX(int32_t)
 TJ_INSTANTIATE_RADIX(int64_t)
 
