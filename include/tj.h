@@ -59,7 +59,9 @@ typedef struct {
   int64_t scratch_peak;    /* peak bytes of library working set live at once */
   int64_t staging_bytes;   /* bytes of the key-range batches (partitioned copies) */
   int64_t out_count;       /* pairs produced (join) */
-  int32_t used_hbm_table;  /* 1 if the HBM hash table path ran */
+  int32_t route_regions;   /* batch regions of the route pass: 0 none (single pass),
+                              1 sized by a route histogram, 2 sized from the sample,
+                              3 sized from the sample, then routed again exactly */
   int32_t learned;         /* router used: tj_router value; +100 if it fell back to radix */
   int32_t partitions;      /* key-range batches of the route pass (0 = single pass) */
   int32_t heavy_keys;      /* keys that got a batch of their own */

@@ -35,7 +35,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("key_bits", ctypes.c_int32), ("radix_passes", ctypes.c_int32),
                 ("digit_bits", ctypes.c_int32), ("groups", ctypes.c_int32),
                 ("scratch_peak", ctypes.c_int64), ("staging_bytes", ctypes.c_int64),
-                ("out_count", ctypes.c_int64), ("used_hbm_table", ctypes.c_int32),
+                ("out_count", ctypes.c_int64), ("route_regions", ctypes.c_int32),
                 ("learned", ctypes.c_int32), ("partitions", ctypes.c_int32),
                 ("heavy_keys", ctypes.c_int32), ("max_partition", ctypes.c_int64),
                 ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double),

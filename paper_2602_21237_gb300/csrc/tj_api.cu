@@ -470,6 +470,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
       po.exact_route = true;
       ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, budget, po, out, cap, out_count,
                              stats, tr, st);
+      stats.route_regions = 3;
     }
     if (ps == TJ_OK || ps == TJ_ERR_CAPACITY) {
       stats.out_count = *out_count;
@@ -784,6 +785,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   // tile; the route pass drops and reports a row past its batch's region, and
   // the join is then routed again with exact sizes.
   const bool est = !sample_cnt.empty();
+  stats.route_regions = est ? 2 : 1;
   std::vector<int64_t> rcap(2 * (size_t)nparts, 0), rstart(2 * (size_t)nparts, 0);
   int64_t side_rows[2] = {nr, ns};
   if (est) {

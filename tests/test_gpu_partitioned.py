@@ -29,6 +29,35 @@ def test_router_unbounded(router, dtype):
     assert st["learned"] == api.ROUTERS[router]
 
 
+@pytest.mark.parametrize("router", ["radix", "pla"])
+def test_route_regions_sampled_or_histogram(router):
+    # learned routers size the batch regions from their sample; equal-width
+    # ranges take a route histogram
+    kr, ir, ks, is_ = datagen.uniform_pair(200_000, 300_003, 0, 1 << 20, 33, torch.int64)
+    st = check(kr, ir, ks, is_, router=router, partitions=64)
+    assert st["route_regions"] == (2 if router == "pla" else 1)
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
+def test_sampled_regions_fall_back_to_exact_routing(dtype):
+    # the keys at the sampled positions are all small, the others large: the
+    # sample gives the large-key batch almost no room, the route pass reports
+    # the overflow and the join is routed again with exact batch sizes
+    n, stride, seed = 200_000, 10, 5
+    off_r = (((seed * 0x9E3779B97F4A7C15) % (1 << 64)) >> 33) % stride
+    off_s = (((seed * 0xBF58476D1CE4E5B9) % (1 << 64)) >> 33) % stride
+    g = torch.Generator().manual_seed(3)
+    kr = torch.randint(1 << 20, 1 << 21, (n,), generator=g)
+    ks = torch.randint(1 << 20, 1 << 21, (n,), generator=g)
+    kr[off_r::stride] = torch.randint(0, 1000, (len(range(off_r, n, stride)),), generator=g)
+    ks[off_s::stride] = torch.randint(0, 1000, (len(range(off_s, n, stride)),), generator=g)
+    kr, ks = kr.to(dtype), ks.to(dtype)
+    ir = torch.arange(n, dtype=dtype)
+    is_ = torch.arange(n, dtype=dtype)
+    st = check(kr, ir, ks, is_, router="pla", partitions=64, sample_stride=stride, seed=seed)
+    assert st["route_regions"] == 3
+
+
 @pytest.mark.parametrize("s", [0.0, 1.2])
 def test_pla_budgeted_fk_zipf(s):
     kr, ir, ks, is_ = datagen.fk_zipf(200_000, 800_000, s, 41)
