@@ -1102,7 +1102,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     size_t o_zero, zero_bytes, o_cnt, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
     size_t lb_words;
     int64_t tiles, jtiles;
-    int P, maxbits;
+    int P, maxbits, items;
     double rows, prow[kMaxPasses];
   };
   Block tbl;
@@ -1130,16 +1130,19 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         o_buf[i * 4 + 3] = gc.add<K>((size_t)q.ns);
       }
     }
+    // onesweep tile of the group: the wider one when every digit is narrow
+    for (size_t i = 0; i < nj; ++i) gp.maxbits = std::max(gp.maxbits, P[g.first + i].plan.max_bits);
+    gp.items = gp.maxbits <= kWideBits ? kItemsWide : kItems;
+    const int64_t otile = (int64_t)kSortThreads * gp.items;
     std::vector<size_t> lb_at(nj * 2);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
       const size_t bins = (size_t)1 << q.plan.max_bits;
       for (int side = 0; side < 2; ++side) {
         lb_at[i * 2 + side] = gp.lb_words;
-        gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, kTile) * bins;
+        gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, otile) * bins;
       }
       gp.P = std::max(gp.P, q.plan.passes);
-      gp.maxbits = std::max(gp.maxbits, q.plan.max_bits);
       for (int p = 0; p < q.plan.passes; ++p) gp.prow[p] += (double)(q.nr + q.ns);
     }
     for (size_t i = 0; i < nj; ++i) gp.jtiles += ceil_div(P[g.first + i].ns, kJTile);
@@ -1177,7 +1180,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         htiles += ceil_div(n, kTile);
         all_rjh.push_back(x);
         x.tile0 = gp.tiles;
-        gp.tiles += ceil_div(n, kTile);
+        gp.tiles += ceil_div(n, otile);
         all_rj.push_back(x);
       }
       JoinJob<K> y;
@@ -1239,11 +1242,12 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     int32_t* d_tmap = wk.at<int32_t>(gp.o_tmap);
     int32_t* d_jmap = wk.at<int32_t>(gp.o_jmap);
     TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_zero, 0, gp.zero_bytes, st));
-    TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, st));
+    TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, st,
+                                 kSortThreads * gp.items));
     for (int p = 0; p < gp.P; ++p) {
       tr.begin("onesweep", 4.0 * w * gp.prow[p]);
       TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
-                                 d_gcnt + p, d_err, st, d_tmap));
+                                 d_gcnt + p, d_err, st, d_tmap, gp.items));
       tr.end();
     }
     TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
@@ -1323,11 +1327,14 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
     return TJ_OK;
   }
   const int64_t bins_max = (int64_t)1 << plan.max_bits;
+  // onesweep tiles (narrow digits: the wider tile); the histogram keeps kTile
+  const int items = plan.max_bits <= kWideBits ? kItemsWide : kItems;
+  const int64_t otiles = ceil_div(n, (int64_t)kSortThreads * items);
   Carve bc;
   const size_t o_bk = bc.add<K>(n);
   const size_t o_bv = bc.add<K>(n);
   const size_t o_hist = bc.add<uint32_t>(kMaxPasses * kMaxBins);
-  const size_t o_lb = bc.add<uint32_t>((size_t)tiles * bins_max);
+  const size_t o_lb = bc.add<uint32_t>((size_t)otiles * bins_max);
   Block big;
   TJ_CUDA(big.alloc(bc.off, st));
   stats.scratch_peak = (int64_t)(bc.off + cc.off);
@@ -1346,9 +1353,10 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   tr2.end();
   TJ_CUDA(launch_digit_scan<K>(d_jobs, 1, plan.passes, st));
   for (int p = 0; p < plan.passes; ++p) {
-    TJ_CUDA(cudaMemsetAsync(hj.lookback, 0, (size_t)tiles * bins_max * sizeof(uint32_t), st));
+    TJ_CUDA(cudaMemsetAsync(hj.lookback, 0, (size_t)otiles * bins_max * sizeof(uint32_t), st));
     tr2.begin("onesweep", 4.0 * w * n);
-    TJ_CUDA(launch_onesweep<K>(d_jobs, 1, tiles, p, plan.max_bits, false, d_counters + p, d_err, st));
+    TJ_CUDA(launch_onesweep<K>(d_jobs, 1, otiles, p, plan.max_bits, false, d_counters + p, d_err,
+                               st, nullptr, items));
     tr2.end();
   }
   int h_err = 0;

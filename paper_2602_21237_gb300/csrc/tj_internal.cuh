@@ -28,6 +28,12 @@ constexpr int kSortThreads = TJ_SORT_THREADS;  // threads per onesweep CTA
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = TJ_SORT_ITEMS;          // rows per thread in a sort tile
 constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (3072)
+// Rows per thread of sorts whose digits have at most kWideBits bits: 10, a
+// 3840-row tile (its shared memory still lets three CTAs share an SM; about
+// 8% faster than 8 rows per thread for 7-bit digits, measured).
+constexpr int kItemsWide = 10;
+constexpr int kWideBits = 7;
+constexpr int kTileWide = kSortThreads * kItemsWide;
 constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass
@@ -173,7 +179,7 @@ cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_ti
 template <typename K>
 cudaError_t launch_group_maps(const RadixJob<K>* d_rjobs, int nr, int32_t* d_rmap,
                               const JoinJob<K>* d_jjobs, int nj, int32_t* d_jmap,
-                              cudaStream_t st);
+                              cudaStream_t st, int tile = kTile);
 
 // ---- launchers (tj_learned.cu) ----------------------------------------------
 template <typename K>

@@ -535,11 +535,11 @@ cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t t
 template <typename K>
 __global__ void k_group_maps(const RadixJob<K>* __restrict__ rjobs, int nr,
                              int32_t* __restrict__ rmap, const JoinJob<K>* __restrict__ jjobs,
-                             int32_t* __restrict__ jmap) {
+                             int32_t* __restrict__ jmap, int tile) {
   const int b = blockIdx.x;
   if (b < nr) {
     const int64_t t0 = rjobs[b].tile0;
-    const int64_t nt = (rjobs[b].n + kTile - 1) / kTile;
+    const int64_t nt = (rjobs[b].n + tile - 1) / tile;
     for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) rmap[t0 + t] = b;
   } else {
     const int j = b - nr;
@@ -552,9 +552,9 @@ __global__ void k_group_maps(const RadixJob<K>* __restrict__ rjobs, int nr,
 template <typename K>
 cudaError_t launch_group_maps(const RadixJob<K>* d_rjobs, int nr, int32_t* d_rmap,
                               const JoinJob<K>* d_jjobs, int nj, int32_t* d_jmap,
-                              cudaStream_t st) {
+                              cudaStream_t st, int tile) {
   if (nr + nj <= 0) return cudaSuccess;
-  k_group_maps<K><<<nr + nj, 256, 0, st>>>(d_rjobs, nr, d_rmap, d_jjobs, d_jmap);
+  k_group_maps<K><<<nr + nj, 256, 0, st>>>(d_rjobs, nr, d_rmap, d_jjobs, d_jmap, tile);
   return cudaGetLastError();
 }
 
@@ -640,7 +640,7 @@ cudaError_t join_init_attributes() {
   template cudaError_t launch_fix_job_out<K>(const JoinJob<K>*, int, int64_t, int64_t*,          \
                                              const int64_t*, cudaStream_t);                     \
   template cudaError_t launch_group_maps<K>(const RadixJob<K>*, int, int32_t*, const JoinJob<K>*, \
-                                            int, int32_t*, cudaStream_t);
+                                            int, int32_t*, cudaStream_t, int);
 TJ_INSTANTIATE_JOIN(int32_t)
 TJ_INSTANTIATE_JOIN(int64_t)
 

@@ -462,7 +462,7 @@ template <int NB, int ITEMS>
 __device__ __forceinline__ void rank_items(uint32_t (&dr)[ITEMS], int nv, uint32_t* wh) {
   const int lane = threadIdx.x & 31;
   const uint32_t ltm = lanemask_lt();
-  constexpr int kHalf = ITEMS >= 4 ? 4 : ITEMS;
+  constexpr int kHalf = ITEMS % 4 == 0 ? 4 : (ITEMS % 2 == 0 ? 2 : 1);
 #pragma unroll
   for (int i0 = 0; i0 < ITEMS; i0 += kHalf) {
     uint32_t peers[kHalf];
@@ -788,6 +788,10 @@ cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t tot
     const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4, guard);
     k_onesweep<K, 4><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  } else if (items == kItemsWide) {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTileWide, guard);
+    k_onesweep<K, kItemsWide><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   } else {
     const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTile, guard);
     k_onesweep<K, kItems><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
@@ -804,6 +808,14 @@ cudaError_t radix_init_attributes() {
   e = cudaFuncSetAttribute(k_onesweep<int64_t, kItems>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTile, true));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_onesweep<int32_t, kItemsWide>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTileWide, true));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_onesweep<int64_t, kItemsWide>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTileWide, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_onesweep<int32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kSortThreads * 4, true));

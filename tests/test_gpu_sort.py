@@ -19,7 +19,8 @@ def check(keys, ids):
 
 
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
-@pytest.mark.parametrize("n", [1, 2, 3071, 3072, 3073, 4095, 4096, 4097, 6145, 100003, 1_000_000])
+@pytest.mark.parametrize("n", [1, 2, 3071, 3072, 3073, 3839, 3840, 3841, 4095, 4096, 4097, 6145,
+                               7681, 100003, 1_000_000])
 @pytest.mark.parametrize("dist", ["full", "narrow", "dups"])
 def test_sort_matches_oracle(dtype, n, dist):
     info = torch.iinfo(dtype)
