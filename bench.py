@@ -399,7 +399,8 @@ def run_tj(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_extras:
         del kr, ir, rels, sort_src_k, sort_src_i, out, sk, si
         torch.cuda.empty_cache()
-        extras = {"learned_vs_radix": extra_learned(args.scale),
+        extras = {"small_int32_1e6": extra_small(),
+                  "learned_vs_radix": extra_learned(args.scale),
                   "batched_vs_one_at_a_time": extra_batched(args.scale),
                   "serving": extra_serving(args.scale)}
     if rank == 0:
@@ -427,6 +428,32 @@ def _events_ms(fn, reps=3, warm=1):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps, r
+
+
+def extra_small():
+    """R and S of 10^6 rows each, int32 keys uniform in [0, 2^20), ids =
+    positions: join (about 9.5e5 pairs) and sort of R, latency per call."""
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    kr, ir, ks, is_ = datagen.uniform_pair(10**6, 10**6, 0, 1 << 20, 20260221,
+                                           torch.int32, device="cuda")
+    out = torch.empty((2 * 10**6, 2), dtype=torch.int32, device="cuda")
+    ms_join, r = _events_ms(lambda: api.join_inner(kr, ir, ks, is_, out=out), reps=20, warm=3)
+    sk, si = kr.clone(), ir.clone()
+
+    def srt():
+        sk.copy_(kr)
+        si.copy_(ir)
+        return api.sort(sk, si)
+
+    ms_copy, _ = _events_ms(lambda: (sk.copy_(kr), si.copy_(ir)), reps=20, warm=3)
+    ms_sort, _ = _events_ms(srt, reps=20, warm=3)
+    ms_sort = max(0.0, ms_sort - ms_copy)
+    return {"workload": "uniform_int32_1e6x1e6_keys_2^20", "pairs": int(r.shape[0]),
+            "join_us": 1e3 * ms_join, "join_tuples_per_s": 2e6 / (ms_join / 1e3),
+            "sort_us": 1e3 * ms_sort, "sort_keys_per_s": 1e6 / (ms_sort / 1e3)}
 
 
 def extra_learned(scale):
