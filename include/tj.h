@@ -70,6 +70,8 @@ typedef struct {
   double radix_balance;    /* the same for equal-width key ranges, from the sample */
   int32_t tile_rows;       /* batched join: rows per onesweep tile used */
   int32_t digit_cap;       /* batched join: widest radix digit allowed */
+  int32_t lanes;           /* streams the groups alternate between (2 when the budget
+                              needs several groups: each lane gets half of it) */
 } tj_stats;
 
 /*

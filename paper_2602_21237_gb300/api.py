@@ -39,7 +39,8 @@ class _Stats(ctypes.Structure):
                 ("learned", ctypes.c_int32), ("partitions", ctypes.c_int32),
                 ("heavy_keys", ctypes.c_int32), ("max_partition", ctypes.c_int64),
                 ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double),
-                ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32)]
+                ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32),
+                ("lanes", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):

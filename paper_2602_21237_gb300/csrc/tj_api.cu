@@ -92,11 +92,15 @@ class Tracer {
       pool_put(p.e1);
     }
   }
-  void begin(const char* name, double bytes) {
+  // `s`: the launch's stream when it is not the call's own; `launches`: the
+  // kernels between begin and end (one unless a phase is traced as a whole)
+  void begin(const char* name, double bytes, cudaStream_t s = nullptr, int launches = 1) {
     if (!on_) return;
     Pending p;
     p.name = name;
     p.bytes = bytes;
+    p.launches = launches;
+    p.st = s ? s : st_;
     p.e0 = pool_get();
     p.e1 = pool_get();
     if (!p.e0 || !p.e1) {
@@ -104,13 +108,13 @@ class Tracer {
       pool_put(p.e1);
       return;
     }
-    cudaEventRecord(p.e0, st_);
+    cudaEventRecord(p.e0, p.st);
     pend_.push_back(p);
     open_ = true;
   }
   void end() {
     if (!on_ || !open_) return;
-    cudaEventRecord(pend_.back().e1, st_);
+    cudaEventRecord(pend_.back().e1, pend_.back().st);
     open_ = false;
   }
   // the bytes of the last traced launch named `name` (known only afterwards)
@@ -137,7 +141,7 @@ class Tracer {
         g_trace.push_back(r);
         row = &g_trace.back();
       }
-      row->launches += 1;
+      row->launches += p.launches;
       row->ms += ms;
       row->bytes += p.bytes;
     }
@@ -148,6 +152,8 @@ class Tracer {
   struct Pending {
     const char* name;
     double bytes;
+    int launches;
+    cudaStream_t st;
     cudaEvent_t e0, e1;
   };
   cudaStream_t st_;
@@ -209,6 +215,15 @@ struct Block {
   }
 };
 
+// A part of a block (not owned).
+struct View {
+  char* p;
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(p + off);
+  }
+};
+
 // ---- pinned host staging for job-table uploads (one per thread, grows) ------
 struct Pinned {
   unsigned char* p = nullptr;
@@ -244,6 +259,60 @@ cudaError_t pinned_staging(size_t n, unsigned char** out) {
   *out = g_pinned.p;
   return cudaSuccess;
 }
+
+// ---- a second stream per host thread ---------------------------------------------
+// The groups of a partitioned join alternate between the caller's stream and
+// this one, so one group's sort passes fill the tails of the other's launches.
+struct SideStream {
+  int dev = -1;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  void reset() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e), e = nullptr;
+    if (s) cudaStreamDestroy(s);
+    s = nullptr;
+    dev = -1;
+  }
+  ~SideStream() { reset(); }
+};
+thread_local SideStream g_side;
+
+// The side stream of the current device and three events to order work
+// between it and the caller's stream.
+cudaError_t side_stream(SideStream** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (g_side.s && g_side.dev != dev) g_side.reset();
+  if (!g_side.s) {
+    e = cudaStreamCreateWithFlags(&g_side.s, cudaStreamNonBlocking);
+    for (auto& x : g_side.ev)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      g_side.reset();
+      return e;
+    }
+    g_side.dev = dev;
+  }
+  *out = &g_side;
+  return cudaSuccess;
+}
+
+// Makes `st` wait for everything enqueued on `side` so far when it goes out of
+// scope (declared after the blocks the side stream uses, so it runs before
+// their stream-ordered frees, on every return path).
+struct JoinBack {
+  cudaStream_t st = nullptr, side = nullptr;
+  cudaEvent_t ev = nullptr;
+  void now() {
+    if (!side) return;
+    cudaEventRecord(ev, side);
+    cudaStreamWaitEvent(st, ev, 0);
+    side = nullptr;
+  }
+  ~JoinBack() { now(); }
+};
 
 // ---- digit plan -----------------------------------------------------------------
 struct Plan {
@@ -771,12 +840,13 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       route_shift = us;
     }
   }
+  const int64_t rtile = kTile;  // route pass tiles
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
                                   : INT64_MAX;
-  const int64_t all_tiles = ceil_div(std::max(nr, ns), kTile);
+  const int64_t all_tiles = ceil_div(std::max(nr, ns), rtile);
   const int64_t chunk_tiles = std::max<int64_t>(1, std::min(all_tiles, route_lb / lb_per_tile));
-  const int64_t chunk_rows = chunk_tiles * kTile;  // <= max(n_r, n_s) rounded up to a tile
+  const int64_t chunk_rows = chunk_tiles * rtile;  // <= max(n_r, n_s) rounded up to a tile
   if ((int64_t)nr + ns >= ((int64_t)1 << 32))
     return set_err(TJ_ERR_INVALID, "partitioned join needs n_r + n_s < 2^32");
   // Batch regions in the routed copies: sized from the sample when the router
@@ -795,7 +865,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       int64_t acc = 0;
       for (int p2 = 0; p2 < nparts; ++p2) {
         const double c = (double)sample_cnt[(size_t)side * kMaxBins + p2];
-        const int64_t k = (int64_t)std::ceil((c + 6.0 * std::sqrt(c) + 8.0) * scale) + kTile;
+        const int64_t k = (int64_t)std::ceil((c + 6.0 * std::sqrt(c) + 8.0) * scale) + rtile;
         rcap[(size_t)side * nparts + p2] = k;
         rstart[(size_t)side * nparts + p2] = acc;
         acc += k;
@@ -821,9 +891,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   for (int i = 0; i < nch;) {
     int j = i;
     int64_t acc = 0;
-    while (j < nch && (j == i || (!est && acc + ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile <=
+    while (j < nch && (j == i || (!est && acc + ceil_div(chunks[(size_t)j].n, rtile) * lb_per_tile <=
                                                route_lb)))
-      acc += ceil_div(chunks[(size_t)j].n, kTile) * lb_per_tile, ++j;
+      acc += ceil_div(chunks[(size_t)j].n, rtile) * lb_per_tile, ++j;
     cgroups.push_back({i, j});
     lb_max = std::max(lb_max, acc);
     i = j;
@@ -889,8 +959,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       RadixJob<K> x = hj[(size_t)c];
       x.tile0 = t;
       route_lbw[(size_t)c] = lbw;
-      t += ceil_div(x.n, kTile);
-      lbw += ceil_div(x.n, kTile) << rbits;
+      t += ceil_div(x.n, rtile);
+      lbw += ceil_div(x.n, rtile) << rbits;
       hj[(size_t)nch + c] = x;
     }
   }
@@ -971,7 +1041,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
                           cudaMemcpyHostToDevice, st));
   for (auto& g : cgroups) {
     int64_t t = 0;
-    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, kTile);
+    for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, rtile);
     TJ_CUDA(cudaMemsetAsync(rlb.p, 0, (size_t)lb_max, st));
     TJ_CUDA(cudaMemsetAsync(d_counters + kMaxPasses, 0, sizeof(uint32_t), st));
     double rows = 0;
@@ -1062,31 +1132,56 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   if (room <= 0)
     return set_err(TJ_ERR_BUDGET, "budget %zu below the join's tables and control (%lld bytes)",
                    budget, (long long)fixed);
+  // Consecutive batches form a group while the group's working set fits `lim`.
+  // When the budget needs more than one group, groups are planned against half
+  // of it and alternate between two streams (lanes), each with its own half.
   std::vector<std::pair<size_t, size_t>> groups;  // [first, last) into P
   int64_t ws_max = 0;
-  for (size_t i = 0; i < P.size();) {
-    const int64_t need_i = P[i].ws + P[i].lb * P[i].np;
-    if (need_i > room)
+  auto need_of = [&](size_t i) { return P[i].ws + P[i].lb * P[i].np; };
+  auto make_groups = [&](int64_t lim) -> int64_t {  // -1, or a batch that needs more
+    groups.clear();
+    ws_max = 0;
+    for (size_t i = 0; i < P.size();) {
+      if (need_of(i) > lim) return (int64_t)i;
+      size_t j = i;
+      int64_t ws = 0, lb = 0, acc = 0;
+      int np = 1;
+      while (j < P.size()) {
+        const int np2 = std::max(np, P[j].np);
+        const int64_t acc2 = ws + P[j].ws + (lb + P[j].lb) * np2;
+        if (acc2 > lim) break;
+        ws += P[j].ws, lb += P[j].lb, np = np2, acc = acc2, ++j;
+      }
+      groups.push_back({i, j});
+      ws_max = std::max(ws_max, acc);
+      i = j;
+    }
+    return -1;
+  };
+  {
+    const int64_t bad = make_groups(room);
+    if (bad >= 0)
       return set_err(TJ_ERR_BUDGET,
                      "batch of keys [%lld, %lld] needs %lld bytes of working set, budget "
                      "leaves %lld (raise the budget or the number of batches)",
-                     (long long)P[i].lo, (long long)P[i].hi, (long long)need_i,
-                     (long long)room);
-    size_t j = i;
-    int64_t ws = 0, lb = 0, acc = 0;
-    int np = 1;
-    while (j < P.size()) {
-      const int np2 = std::max(np, P[j].np);
-      const int64_t acc2 = ws + P[j].ws + (lb + P[j].lb) * np2;
-      if (acc2 > room) break;
-      ws += P[j].ws, lb += P[j].lb, np = np2, acc = acc2, ++j;
+                     (long long)P[(size_t)bad].lo, (long long)P[(size_t)bad].hi,
+                     (long long)need_of((size_t)bad), (long long)room);
+  }
+  int lanes = 1;
+  if (groups.size() > 1) {
+    const auto one = groups;
+    const int64_t one_max = ws_max;
+    if (make_groups(room / 2) < 0) {
+      lanes = 2;
+    } else {
+      groups = one;
+      ws_max = one_max;
     }
-    groups.push_back({i, j});
-    ws_max = std::max(ws_max, acc);
-    i = j;
   }
   stats.groups = (int)groups.size();
-  const int64_t wk_bytes = std::max<int64_t>(ws_max, 256);
+  stats.lanes = lanes;
+  const size_t lane_bytes = ((size_t)std::max<int64_t>(ws_max, 256) + 255) & ~(size_t)255;
+  const int64_t wk_bytes = (int64_t)(lane_bytes * (size_t)lanes);
   stats.scratch_peak = control + std::max<int64_t>(lb_max, wk_bytes + (int64_t)tbl_bytes);
   rlb.release();
   Block wk;
@@ -1102,7 +1197,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     size_t o_zero, zero_bytes, o_cnt, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
     size_t lb_words;
     int64_t tiles, jtiles;
-    int P, maxbits, items;
+    int P, maxbits, items, lane;
     double rows, prow[kMaxPasses];
   };
   Block tbl;
@@ -1116,6 +1211,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   int64_t htiles = 0;
   for (auto& g : groups) {
     GroupPlan gp = {};
+    gp.lane = (int)(plans.size() % (size_t)lanes);
+    const View lw{wk.p + (size_t)gp.lane * lane_bytes};  // the group's lane of wk
     gp.first = g.first;
     gp.nj = g.second - g.first;
     const size_t nj = gp.nj;
@@ -1170,11 +1267,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         x.hist_stride = 1 << q.plan.max_bits;
         x.hist = d_hist_all + hist_at;
         hist_at += (size_t)std::max(1, q.plan.passes) << q.plan.max_bits;
-        x.lookback = wk.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
+        x.lookback = lw.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
         x.lb_stride = (int64_t)gp.lb_words;
         // passes alternate: routed copy -> buffer -> routed copy -> ...
-        K* ak = q.plan.passes > 0 ? wk.at<K>(o_buf[i * 4 + 2 * side]) : nullptr;
-        K* av = q.plan.passes > 0 ? wk.at<K>(o_buf[i * 4 + 2 * side + 1]) : nullptr;
+        K* ak = q.plan.passes > 0 ? lw.at<K>(o_buf[i * 4 + 2 * side]) : nullptr;
+        K* av = q.plan.passes > 0 ? lw.at<K>(o_buf[i * 4 + 2 * side + 1]) : nullptr;
         set_job_buffers(x, k0, v0, ak, av, k0, v0, &res[2 * side], &res[2 * side + 1]);
         x.tile0 = htiles;  // the histogram launch numbers tiles over all groups
         htiles += ceil_div(n, kTile);
@@ -1198,9 +1295,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     gp.o_rb = gc.add<int64_t>((size_t)gp.jtiles);
     gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
     gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
-    if ((int64_t)gc.off > wk_bytes)
-      return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, working block has %lld", gc.off,
-                     (long long)wk_bytes);
+    if (gc.off > lane_bytes)
+      return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, its lane has %zu", gc.off,
+                     lane_bytes);
     maxp = std::max(maxp, gp.P);
     plans.push_back(gp);
   }
@@ -1233,32 +1330,62 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
 
   // ---- 6. one batched sort + align per group: a memset and five kernels ----
+  // With two lanes, group g runs on lane g % 2's stream; a group's join waits
+  // for the previous group's join (it writes from the base that join leaves).
+  cudaStream_t lane_st[2] = {st, st};
+  SideStream* side = nullptr;
+  JoinBack back;
+  if (lanes > 1) {
+    TJ_CUDA(side_stream(&side));
+    lane_st[1] = side->s;
+    TJ_CUDA(cudaEventRecord(side->ev[0], st));  // tables, histograms, scans
+    TJ_CUDA(cudaStreamWaitEvent(side->s, side->ev[0], 0));
+    back.st = st;
+    back.side = side->s;
+    back.ev = side->ev[2];
+  }
   for (size_t g = 0; g < plans.size(); ++g) {
     const GroupPlan& gp = plans[g];
     const size_t nj = gp.nj;
+    const cudaStream_t gs = lane_st[gp.lane];
+    const View lw{wk.p + (size_t)gp.lane * lane_bytes};
     RadixJob<K>* d_gj = d_rj_all + gp.rj_at;
     JoinJob<K>* d_gjj = d_jj_all + gp.jj_at;
-    uint32_t* d_gcnt = wk.at<uint32_t>(gp.o_cnt);
-    int32_t* d_tmap = wk.at<int32_t>(gp.o_tmap);
-    int32_t* d_jmap = wk.at<int32_t>(gp.o_jmap);
-    TJ_CUDA(cudaMemsetAsync(wk.p + gp.o_zero, 0, gp.zero_bytes, st));
-    TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, st,
+    uint32_t* d_gcnt = lw.at<uint32_t>(gp.o_cnt);
+    int32_t* d_tmap = lw.at<int32_t>(gp.o_tmap);
+    int32_t* d_jmap = lw.at<int32_t>(gp.o_jmap);
+    // One lane: every kernel traced.  Two lanes: the launches of the lanes
+    // overlap, so a group is traced as a whole ("group/lanes": its sort
+    // passes and join, launches counted) with two events instead of two per
+    // kernel.
+    const bool whole = lanes > 1;
+    if (whole) {
+      double by = 2.0 * w * gp.rows;  // join input (the output is added at the end)
+      for (int p = 0; p < gp.P; ++p) by += 4.0 * w * gp.prow[p];
+      tr.begin("group/lanes", by, gs, gp.P + 3);
+    }
+    TJ_CUDA(cudaMemsetAsync(lw.p + gp.o_zero, 0, gp.zero_bytes, gs));
+    TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, gs,
                                  kSortThreads * gp.items));
     for (int p = 0; p < gp.P; ++p) {
-      tr.begin("onesweep", 4.0 * w * gp.prow[p]);
+      if (!whole) tr.begin("onesweep", 4.0 * w * gp.prow[p], gs);
       TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
-                                 d_gcnt + p, d_err, st, d_tmap, gp.items));
-      tr.end();
+                                 d_gcnt + p, d_err, gs, d_tmap, gp.items));
+      if (!whole) tr.end();
     }
-    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
-                                  wk.at<int64_t>(gp.o_rb), st, d_jmap));
-    tr.begin("join", 2.0 * w * gp.rows);
-    TJ_CUDA(launch_join<K>(d_gjj, (int)nj, gp.jtiles, wk.at<int64_t>(gp.o_ra),
-                           wk.at<int64_t>(gp.o_rb), wk.at<uint64_t>(gp.o_jlb),
+    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, lw.at<int64_t>(gp.o_ra),
+                                  lw.at<int64_t>(gp.o_rb), gs, d_jmap));
+    if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
+    if (!whole) tr.begin("join", 2.0 * w * gp.rows, gs);
+    TJ_CUDA(launch_join<K>(d_gjj, (int)nj, gp.jtiles, lw.at<int64_t>(gp.o_ra),
+                           lw.at<int64_t>(gp.o_rb), lw.at<uint64_t>(gp.o_jlb),
                            d_gcnt + kMaxPasses, out, cap, d_gbase + g, nullptr, d_gbase + g + 1,
-                           d_err, st, d_jmap));
+                           d_err, gs, d_jmap));
     tr.end();
+    // (the next group's wait is enqueued before this event is recorded again)
+    if (lanes > 1) TJ_CUDA(cudaEventRecord(side->ev[1], gs));
   }
+  back.now();
   stats.radix_passes = maxp;
   int64_t h_total = 0;
   int h_err = 0;
@@ -1266,7 +1393,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
                           cudaMemcpyDeviceToHost, st));
   TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   TJ_CUDA(cudaStreamSynchronize(st));
-  if (h_total <= cap) tr.add_bytes("join", 2.0 * w * (double)h_total);
+  if (h_total <= cap) tr.add_bytes(lanes > 1 ? "group/lanes" : "join", 2.0 * w * (double)h_total);
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
   *out_count = h_total;

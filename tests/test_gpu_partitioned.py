@@ -113,3 +113,39 @@ def test_single_router_respects_budget():
         api.join_inner(kr.to(DEV), ir.to(DEV), ks.to(DEV), is_.to(DEV), mem_budget_bytes=1 << 20,
                        router="single")
     assert ei.value.status == api.TJ_ERR_BUDGET
+
+
+def test_groups_alternate_between_two_lanes():
+    # several groups under the budget: groups alternate between two streams,
+    # each with half of the budget's working set; the pairs of a group follow
+    # the previous group's, whichever stream ran it
+    kr, ir, ks, is_ = datagen.fk_zipf(200_000, 800_000, 0.8, 47)
+    budget = 6 << 20
+    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256)
+    assert st["groups"] >= 4 and st["lanes"] == 2
+    assert st["scratch_peak"] <= budget
+    st = check(kr, ir, ks, is_, router="pla", partitions=256)  # unbounded: one group
+    assert st["groups"] == 1 and st["lanes"] == 1
+
+
+def test_two_lanes_many_to_many_on_a_side_stream():
+    # many matches per key across groups, called on a stream that is still
+    # writing the inputs: the second lane must wait for the caller's stream
+    g = torch.Generator().manual_seed(14)
+    n = 400_000
+    kr = torch.randint(0, 50_000, (n,), generator=g, dtype=torch.int64)
+    ks = torch.randint(0, 50_000, (n,), generator=g, dtype=torch.int64)
+    ir = torch.arange(n, dtype=torch.int64)
+    is_ = torch.arange(n, dtype=torch.int64) * 3
+    exp = oracle.join_inner(kr.numpy(), ir.numpy(), ks.numpy(), is_.numpy())
+    s = torch.cuda.Stream()
+    h = [t.pin_memory() for t in (kr, ir, ks, is_)]
+    with torch.cuda.stream(s):
+        d = [torch.empty_like(t, device=DEV) for t in h]
+        for dst, src in zip(d, h):
+            dst.copy_(src, non_blocking=True)
+        got = api.join_inner(*d, mem_budget_bytes=6 << 20, router="pla", partitions=128)
+        st = api.stats()
+    s.synchronize()
+    assert st["groups"] > 1 and st["lanes"] == 2
+    assert_pairs_equal(got, exp)
