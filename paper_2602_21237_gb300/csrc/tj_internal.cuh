@@ -37,10 +37,14 @@ constexpr int kTileWide = kSortThreads * kItemsWide;
 constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass
-constexpr int kJTile = 4096;                // S rows per join tile
-constexpr int kRCap = 2048;                 // R rows a join tile keeps on chip at once
+#ifndef TJ_JTILE
+#define TJ_JTILE 4096
+#endif
+constexpr int kJTile = TJ_JTILE;            // S rows per join tile (a power of two)
+constexpr int kRCap = kJTile / 2;           // R rows a join tile keeps on chip at once
 constexpr int kMaxChunks = 4;               // R chunks a join tile aligns on chip
-constexpr int kHTSlots = 4096;              // on-chip hash table slots (load <= 0.5)
+constexpr int kHTSlots = kJTile;            // on-chip hash table slots (load <= 0.5)
+static_assert((kJTile & (kJTile - 1)) == 0 && kJTile >= 1024, "join tile: a power of two");
 
 // ---- decoupled look-back words (30-bit counts) ----------------------------
 constexpr uint32_t kFlagAgg = 1u << 30;

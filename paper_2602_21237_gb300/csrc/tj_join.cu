@@ -35,13 +35,15 @@ __device__ __forceinline__ int find_job_j(const Job* jobs, int num_jobs, int64_t
   return lo;
 }
 
+// multiplicative hashing onto the table's log2(kHTSlots) bits
+constexpr int kHTBits = kHTSlots == 1024 ? 10 : kHTSlots == 2048 ? 11 : kHTSlots == 4096 ? 12 : 13;
+static_assert((1 << kHTBits) == kHTSlots, "hash table slots: 2^10 .. 2^13");
 __device__ __forceinline__ uint32_t ht_hash(int32_t k) {
-  return ((uint32_t)k * 0x9E3779B9u) >> (32 - 12);
+  return ((uint32_t)k * 0x9E3779B9u) >> (32 - kHTBits);
 }
 __device__ __forceinline__ uint32_t ht_hash(int64_t k) {
-  return (uint32_t)(((uint64_t)k * 0x9E3779B97F4A7C15ull) >> (64 - 12));
+  return (uint32_t)(((uint64_t)k * 0x9E3779B97F4A7C15ull) >> (64 - kHTBits));
 }
-static_assert(kHTSlots == 4096, "ht_hash assumes 4096 slots");
 static_assert(kRCap < 0xFFFF, "run bounds are packed in 16 bits");
 
 constexpr uint32_t kHTEmpty = 0xFFFFFFFFu;
@@ -110,42 +112,63 @@ __global__ void k_tile_ranges(const JoinJob<K>* __restrict__ jobs, int num_jobs,
 }
 
 // ---------------------------------------------------------------------------
-constexpr int kJThreads = 512;                  // threads per join CTA (16 warps)
+#ifndef TJ_JTHREADS
+#define TJ_JTHREADS 512
+#endif
+#ifndef TJ_JMINB
+#define TJ_JMINB 2
+#endif
+constexpr int kJThreads = TJ_JTHREADS;          // threads per join CTA
 constexpr int kJWarps = kJThreads / 32;
 constexpr int kJItems = kJTile / kJThreads;     // S rows per thread
 static_assert(kJItems * kJThreads == kJTile, "join tile = threads x items");
 
-// Shared memory: S keys[kJTile] | S ids[kJTile] | R keys[kRCap] | R ids[kRCap]
-// | hash table[kHTSlots] u32.  After the probe the many-matches write path
-// (which reads ids from global memory) keeps per-row offsets (u64) and run
-// starts (u32) from the start of it.
+// Shared memory: S keys | S ids (kJTile + kPad each) | R keys | R ids (kRCap +
+// kPad each) | hash table[kHTSlots] u32.  Each staged array starts up to kPad
+// elements into its area (its first element keeps the source's address modulo
+// 16, so that all but a head and a tail move in 16-byte copies).  After the
+// probe the many-matches write path (which reads ids from global memory)
+// keeps per-row offsets (u64) and run starts (u32) from the start of it.
+template <typename K>
+__host__ __device__ constexpr int join_pad() {
+  return 16 / (int)sizeof(K);
+}
 template <typename K>
 constexpr size_t join_smem_bytes() {
-  return sizeof(K) * (size_t)(2 * kJTile + 2 * kRCap) + sizeof(uint32_t) * kHTSlots;
+  return sizeof(K) * (size_t)(2 * (kJTile + join_pad<K>()) + 2 * (kRCap + join_pad<K>())) +
+         sizeof(uint32_t) * kHTSlots;
 }
-static_assert(sizeof(int32_t) * (2 * kJTile + 2 * kRCap) + sizeof(uint32_t) * kHTSlots >=
+static_assert(sizeof(int32_t) * (2 * kJTile + 2 * kRCap) >=
                   (sizeof(uint64_t) + sizeof(uint32_t)) * kJTile,
               "offsets and run starts fit in the join's shared memory");
 
-// Asynchronous global -> shared copy of n elements (16-byte chunks when the
-// source allows it, else one element per copy); every thread of the CTA calls it.
+// Asynchronous global -> shared copy of n elements into dst (16-byte aligned,
+// kPad elements of slack): returns where the copy starts, dst plus the
+// source's misalignment, so both sides agree modulo 16; the head and tail
+// elements around the 16-byte chunks are copied one by one.  Every thread of
+// the CTA calls it.
 template <typename K>
-__device__ __forceinline__ void join_copy_async(K* dst, const K* __restrict__ src, int n) {
-  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
-  int done = 0;
-  if ((((uintptr_t)src) & 15u) == 0) {
-    constexpr int kPer = 16 / (int)sizeof(K);
-    const int chunks = n / kPer;
-    for (int c = threadIdx.x; c < chunks; c += kJThreads)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst + 16u * c),
-                   "l"(src + c * kPer)
-                   : "memory");
-    done = chunks * kPer;
-  }
-  for (int i = done + threadIdx.x; i < n; i += kJThreads)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sdst + (uint32_t)(i * sizeof(K))),
+__device__ __forceinline__ K* join_copy_async(K* dst, const K* __restrict__ src, int n) {
+  const uint32_t mis = (uint32_t)((uintptr_t)src & 15u);  // a multiple of sizeof(K)
+  K* d = dst + mis / sizeof(K);
+  const uint32_t sd = (uint32_t)__cvta_generic_to_shared(d);
+  constexpr int kPer = 16 / (int)sizeof(K);
+  const int head = min(n, mis ? (int)((16u - mis) / sizeof(K)) : 0);
+  const int chunks = (n - head) / kPer;
+  for (int i = threadIdx.x; i < head; i += kJThreads)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sd + (uint32_t)(i * sizeof(K))),
                  "l"(src + i), "n"(sizeof(K))
                  : "memory");
+  for (int c = threadIdx.x; c < chunks; c += kJThreads)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sd + (uint32_t)(head * sizeof(K)) +
+                                                                   16u * c),
+                 "l"(src + head + c * kPer)
+                 : "memory");
+  for (int i = head + chunks * kPer + threadIdx.x; i < n; i += kJThreads)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sd + (uint32_t)(i * sizeof(K))),
+                 "l"(src + i), "n"(sizeof(K))
+                 : "memory");
+  return d;
 }
 
 template <typename K> struct PairOf;
@@ -170,7 +193,7 @@ template <> struct PairOf<int64_t> { using type = longlong2; };
 //      tile's counts are scanned and each output index finds its S row.
 // Output order: key, then S position, then R position.
 template <typename K>
-__global__ void __launch_bounds__(kJThreads, 2)
+__global__ void __launch_bounds__(kJThreads, TJ_JMINB)
     k_join(const JoinJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles,
            const int64_t* __restrict__ ra, const int64_t* __restrict__ rb,
            uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter,
@@ -178,11 +201,12 @@ __global__ void __launch_bounds__(kJThreads, 2)
            int64_t* __restrict__ job_out, int64_t* __restrict__ total, int* __restrict__ err,
            const int32_t* __restrict__ tile_job) {
   extern __shared__ __align__(16) unsigned char smem[];
-  K* s_sk = reinterpret_cast<K*>(smem);
-  K* s_sv = s_sk + kJTile;
-  K* s_rk = s_sv + kJTile;
-  K* s_rv = s_rk + kRCap;
-  uint32_t* s_ht = reinterpret_cast<uint32_t*>(s_rv + kRCap);
+  constexpr int kPad = join_pad<K>();
+  K* const b_sk = reinterpret_cast<K*>(smem);  // staging areas (16-byte aligned)
+  K* const b_sv = b_sk + kJTile + kPad;
+  K* const b_rk = b_sv + kJTile + kPad;
+  K* const b_rv = b_rk + kRCap + kPad;
+  uint32_t* s_ht = reinterpret_cast<uint32_t*>(b_rv + kRCap + kPad);
   __shared__ uint64_t s_wsum[kJWarps];
   __shared__ uint64_t s_base;
   __shared__ uint32_t s_t;
@@ -205,12 +229,14 @@ __global__ void __launch_bounds__(kJThreads, 2)
   const bool onchip = nchunks <= kMaxChunks;
 
   // 1. stage S and the first R chunk
-  join_copy_async<K>(s_sk, J.sk + row0, nv);
-  join_copy_async<K>(s_sv, J.sv + row0, nv);
+  const K* s_sk = join_copy_async<K>(b_sk, J.sk + row0, nv);
+  const K* s_sv = join_copy_async<K>(b_sv, J.sv + row0, nv);
+  K* s_rk = b_rk;  // the staged R chunk (where its copy starts)
+  K* s_rv = b_rv;
   if (onchip && nchunks > 0) {
     const int nc0 = (int)min((int64_t)kRCap, nrr);
-    join_copy_async<K>(s_rk, rk_g, nc0);
-    join_copy_async<K>(s_rv, rv_g, nc0);
+    s_rk = join_copy_async<K>(b_rk, rk_g, nc0);
+    s_rv = join_copy_async<K>(b_rv, rv_g, nc0);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 
@@ -225,8 +251,8 @@ __global__ void __launch_bounds__(kJThreads, 2)
       const int nc = (int)min((int64_t)kRCap, nrr - c0);
       if (c > 0) {
         __syncthreads();  // the previous chunk's probes are done
-        join_copy_async<K>(s_rk, rk_g + c0, nc);
-        join_copy_async<K>(s_rv, rv_g + c0, nc);
+        s_rk = join_copy_async<K>(b_rk, rk_g + c0, nc);
+        s_rv = join_copy_async<K>(b_rv, rv_g + c0, nc);
         asm volatile("cp.async.commit_group;" ::: "memory");
       }
       for (int i = tid; i < kHTSlots; i += kJThreads) s_ht[i] = kHTEmpty;
