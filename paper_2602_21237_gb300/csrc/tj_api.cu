@@ -522,8 +522,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   }
   const size_t o_hist = bc.add<uint32_t>(2 * kMaxPasses * kMaxBins);
   const size_t o_lb = bc.add<uint32_t>((size_t)(tiles_r + tiles_s) * bins_max);
-  const size_t o_ra = bc.add<int64_t>(jtiles);
-  const size_t o_rb = bc.add<int64_t>(jtiles);
+  const size_t o_tiles = bc.add<JTile<K>>(jtiles);
   const size_t o_jlb = bc.add<uint64_t>(jtiles);
   const size_t need = bc.off + cc.off;
   int router = opts.router;
@@ -598,15 +597,14 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   jj.sv = res_sv;
   jj.ns = ns;
   jj.tile0 = 0;
-  int64_t* d_ra = big.at<int64_t>(o_ra);
-  int64_t* d_rb = big.at<int64_t>(o_rb);
+  JTile<K>* d_tiles = big.at<JTile<K>>(o_tiles);
   uint64_t* d_jlb = big.at<uint64_t>(o_jlb);
   TJ_CUDA(cudaMemcpyAsync(d_jj, &jj, sizeof(jj), cudaMemcpyHostToDevice, st));
-  TJ_CUDA(launch_tile_ranges<K>(d_jj, 1, jtiles, d_ra, d_rb, st));
+  TJ_CUDA(launch_tile_ranges<K>(d_jj, 1, jtiles, d_tiles, st));
   TJ_CUDA(cudaMemsetAsync(d_jlb, 0, jtiles * sizeof(uint64_t), st));
   tr.begin("join", 2.0 * w * (nr + ns));
-  TJ_CUDA(launch_join<K>(d_jj, 1, jtiles, d_ra, d_rb, d_jlb, d_counters + kMaxPasses, out, cap,
-                         nullptr, nullptr, d_total, d_err, st));
+  TJ_CUDA(launch_join<K>(jtiles, d_tiles, d_jlb, d_counters + kMaxPasses, out, cap, nullptr,
+                         nullptr, d_total, d_err, st));
   tr.end();
   int64_t h_misc[2] = {0, 0};
   int h_err = 0;
@@ -1108,7 +1106,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd);
     // one sort buffer (the passes alternate between it and the batch's routed
     // copy), one look-back region per pass (a group keeps as many as its
-    // deepest batch), join tile state (ra, rb, chained words, tile map), the
+    // deepest batch), join tile state (tile descriptors, chained words, tile map), the
     // radix tile map, alignment
     const int np = std::max(1, q.plan.passes);
     const int64_t bins = (int64_t)1 << q.plan.max_bits;
@@ -1116,7 +1114,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     q.lb = rtiles * bins * 4;
     q.np = np;
     q.ws = (int64_t)std::min(q.plan.passes, 1) * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
-           ceil_div(q.ns, kJTile) * 28 + rtiles * 4 + 4096;
+           ceil_div(q.ns, kJTile) * (int64_t)(sizeof(JTile<K>) + 12) + rtiles * 4 + 4096;
     hist_words_all += 2 * (size_t)np * (size_t)bins;
     P.push_back(q);
   }
@@ -1190,11 +1188,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   // ---- 5. group plans: job tables, digit histograms of every batch in one launch ----
   // Group layout in the working block: the sort buffer of every batch | one
   // zeroed region (tile counters, one look-back region per pass, chained join
-  // words) | join tile ranges | tile maps.
+  // words) | join tile descriptors | tile maps.
   struct GroupPlan {
     size_t first, nj;
     size_t rj_at, jj_at;  // offsets into the uploaded tables
-    size_t o_zero, zero_bytes, o_cnt, o_lb, o_ra, o_rb, o_jlb, o_tmap, o_jmap;
+    size_t o_zero, zero_bytes, o_cnt, o_lb, o_jt, o_jlb, o_tmap, o_jmap;
     size_t lb_words;
     int64_t tiles, jtiles;
     int P, maxbits, items, lane;
@@ -1291,8 +1289,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       jt += ceil_div(q.ns, kJTile);
       all_jj.push_back(y);
     }
-    gp.o_ra = gc.add<int64_t>((size_t)gp.jtiles);
-    gp.o_rb = gc.add<int64_t>((size_t)gp.jtiles);
+    gp.o_jt = gc.add<JTile<K>>((size_t)gp.jtiles);
     gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
     gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     if (gc.off > lane_bytes)
@@ -1373,14 +1370,13 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
                                  d_gcnt + p, d_err, gs, d_tmap, gp.items));
       if (!whole) tr.end();
     }
-    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, lw.at<int64_t>(gp.o_ra),
-                                  lw.at<int64_t>(gp.o_rb), gs, d_jmap));
+    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, lw.at<JTile<K>>(gp.o_jt), gs,
+                                  d_jmap));
     if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
     if (!whole) tr.begin("join", 2.0 * w * gp.rows, gs);
-    TJ_CUDA(launch_join<K>(d_gjj, (int)nj, gp.jtiles, lw.at<int64_t>(gp.o_ra),
-                           lw.at<int64_t>(gp.o_rb), lw.at<uint64_t>(gp.o_jlb),
+    TJ_CUDA(launch_join<K>(gp.jtiles, lw.at<JTile<K>>(gp.o_jt), lw.at<uint64_t>(gp.o_jlb),
                            d_gcnt + kMaxPasses, out, cap, d_gbase + g, nullptr, d_gbase + g + 1,
-                           d_err, gs, d_jmap));
+                           d_err, gs));
     tr.end();
     // (the next group's wait is enqueued before this event is recorded again)
     if (lanes > 1) TJ_CUDA(cudaEventRecord(side->ev[1], gs));
@@ -1607,8 +1603,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   }
   const size_t o_hist = bc.add<uint32_t>((size_t)std::max<int64_t>(hist_words, 1));
   const size_t o_lb = bc.add<uint32_t>((size_t)std::max<int64_t>(lb_words, 1));
-  const size_t o_ra = bc.add<int64_t>((size_t)std::max<int64_t>(jtiles, 1));
-  const size_t o_rb = bc.add<int64_t>((size_t)std::max<int64_t>(jtiles, 1));
+  const size_t o_jt = bc.add<JTile<K>>((size_t)std::max<int64_t>(jtiles, 1));
   const size_t o_jlb = bc.add<uint64_t>((size_t)std::max<int64_t>(jtiles, 1));
   const size_t o_tmap = bc.add<int32_t>((size_t)std::max<int64_t>(tiles, 1));
   const size_t o_jmap = bc.add<int32_t>((size_t)std::max<int64_t>(jtiles, 1));
@@ -1677,13 +1672,11 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
                               d_err, st, d_tmap, items));
     }
   }
-  step(launch_tile_ranges<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra),
-                             big.at<int64_t>(o_rb), st, d_jmap));
+  step(launch_tile_ranges<K>(d_jj, (int)nj, jtiles, big.at<JTile<K>>(o_jt), st, d_jmap));
   step(cudaMemsetAsync(big.at<uint64_t>(o_jlb), 0,
                        (size_t)std::max<int64_t>(jtiles, 1) * sizeof(uint64_t), st));
-  step(launch_join<K>(d_jj, (int)nj, jtiles, big.at<int64_t>(o_ra), big.at<int64_t>(o_rb),
-                      big.at<uint64_t>(o_jlb), d_counters + kMaxPasses, out, cap, nullptr,
-                      d_out_off, d_total, d_err, st, d_jmap));
+  step(launch_join<K>(jtiles, big.at<JTile<K>>(o_jt), big.at<uint64_t>(o_jlb),
+                      d_counters + kMaxPasses, out, cap, nullptr, d_out_off, d_total, d_err, st));
   step(launch_fix_job_out<K>(d_jj, (int)nj, jtiles, d_out_off, d_total, st));
   if (use_graph) {
     cudaError_t e2 = cudaStreamEndCapture(st, &graph);

@@ -140,6 +140,22 @@ struct JoinJob {
   int64_t tile0;        // first global join tile (kJTile S rows per tile)
 };
 
+// One join tile as k_tile_ranges leaves it for k_join (one 64-byte load): its
+// S rows and the R rows whose keys lie between its first and last key.
+template <typename K>
+struct alignas(16) JTile {
+  const K* sk;   // the tile's first S row (keys, ids)
+  const K* sv;
+  const K* rk;   // the first R row of its range (keys, ids)
+  const K* rv;
+  int64_t lt;    // tile index within its job
+  int64_t nrr;   // R rows in the range
+  int32_t nv;    // S rows of the tile
+  int32_t j;     // its job
+  int64_t pad;
+};
+static_assert(sizeof(JTile<int64_t>) == 64 && sizeof(JTile<int32_t>) == 64, "64-byte tiles");
+
 // ---- launchers (tj_radix.cu) -----------------------------------------------
 cudaError_t radix_init_attributes();
 // Tiles of the radix kernels have `tile` rows (kTile, or kSortThreads * items
@@ -171,14 +187,13 @@ cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t tot
 cudaError_t join_init_attributes();
 template <typename K>
 cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st,
+                               JTile<K>* d_tiles, cudaStream_t st,
                                const int32_t* d_tile_job = nullptr);
 template <typename K>
-cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                        const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
+cudaError_t launch_join(int64_t total_tiles, const JTile<K>* d_tiles, uint64_t* d_lookback,
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
                         const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
-                        int* d_err, cudaStream_t st, const int32_t* d_tile_job = nullptr);
+                        int* d_err, cudaStream_t st);
 // tile -> job maps of a group's radix jobs (tile of kTile rows) and join jobs
 template <typename K>
 cudaError_t launch_group_maps(const RadixJob<K>* d_rjobs, int nr, int32_t* d_rmap,

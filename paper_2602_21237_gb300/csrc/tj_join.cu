@@ -1,12 +1,14 @@
 // Join of two key-sorted relations on their common key axis (paper Sec. 4.1)
 // with a single final materialisation of (r_id, s_id) pairs (Sec. 3.1).
 //
-//   k_tile_ranges : for every tile of 4096 sorted S rows, the range [a, b) of
-//                   sorted R rows whose keys lie between the tile's first and
-//                   last key (two binary searches per tile).
+//   k_tile_ranges : for every tile of kJTile sorted S rows, the range [a, b)
+//                   of sorted R rows whose keys lie between the tile's first
+//                   and last key (two searches per tile), written with the
+//                   tile's rows and job as one 64-byte descriptor;
 //   k_join        : per S tile, fused count -> scan -> write:
-//                     1. stage the tile's S rows and its R range (in chunks of
-//                        2048 rows, up to 4) in shared memory with cp.async;
+//                     1. read the tile's descriptor, stage its S rows and its
+//                        R range (in chunks of kRCap rows, up to 4) in shared
+//                        memory with cp.async;
 //                     2. build an open-addressing hash table of each chunk's
 //                        distinct keys with shared-memory atomicCAS: slot ->
 //                        (first, end) of the key's run of R rows;
@@ -66,11 +68,12 @@ __device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
 // ---------------------------------------------------------------------------
 // k_tile_ranges: one warp per S tile.  Lanes 0-15 find the first R row with
 // key >= the tile's first key, lanes 16-31 the first R row with key > the
-// tile's last key, each by a 16-ary search (16 probes per round trip).
+// tile's last key, each by a 16-ary search (16 probes per round trip); lane 0
+// writes the tile's descriptor, so a join tile needs one load to start.
 template <typename K>
 __global__ void k_tile_ranges(const JoinJob<K>* __restrict__ jobs, int num_jobs,
-                              int64_t total_tiles, int64_t* __restrict__ ra,
-                              int64_t* __restrict__ rb, const int32_t* __restrict__ tile_job) {
+                              int64_t total_tiles, JTile<K>* __restrict__ tiles,
+                              const int32_t* __restrict__ tile_job) {
   const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= total_tiles) return;  // whole warps leave together
   const int lane = threadIdx.x & 31, sub = lane & 15;
@@ -103,11 +106,19 @@ __global__ void k_tile_ranges(const JoinJob<K>* __restrict__ jobs, int num_jobs,
   const int64_t p = lo + sub;
   const bool pred = p < hi && (upper ? !(key < r[p]) : (r[p] < key));
   const int64_t res = lo + __popc(__ballot_sync(0xFFFFFFFFu, pred) & half);
-  if (sub == 0) {
-    if (upper)
-      rb[t] = res;
-    else
-      ra[t] = res;
+  const int64_t b = __shfl_sync(0xFFFFFFFFu, res, 16);
+  if (lane == 0) {
+    JTile<K> d;
+    d.sk = J->sk + row0;
+    d.sv = J->sv + row0;
+    d.rk = J->rk + res;
+    d.rv = J->rv + res;
+    d.lt = t - J->tile0;
+    d.nrr = b - res;
+    d.nv = (int32_t)(row1 - row0);
+    d.j = j;
+    d.pad = 0;
+    tiles[t] = d;
   }
 }
 
@@ -175,7 +186,7 @@ template <typename K> struct PairOf;
 template <> struct PairOf<int32_t> { using type = int2; };
 template <> struct PairOf<int64_t> { using type = longlong2; };
 
-// One join tile: 4096 consecutive rows of sorted S against the range [a, b)
+// One join tile: kJTile consecutive rows of sorted S against the range [a, b)
 // of sorted R whose keys lie between the tile's first and last key.
 //   1. S keys and ids and the first chunk of the R range go to shared memory
 //      (cp.async); warp w owns S rows [w*32*kJItems, ...), item u = 32 rows;
@@ -194,12 +205,10 @@ template <> struct PairOf<int64_t> { using type = longlong2; };
 // Output order: key, then S position, then R position.
 template <typename K>
 __global__ void __launch_bounds__(kJThreads, TJ_JMINB)
-    k_join(const JoinJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles,
-           const int64_t* __restrict__ ra, const int64_t* __restrict__ rb,
+    k_join(int64_t total_tiles, const JTile<K>* __restrict__ tiles,
            uint64_t* __restrict__ lookback, uint32_t* __restrict__ tile_counter,
            K* __restrict__ out, int64_t capacity, const int64_t* __restrict__ out_base,
-           int64_t* __restrict__ job_out, int64_t* __restrict__ total, int* __restrict__ err,
-           const int32_t* __restrict__ tile_job) {
+           int64_t* __restrict__ job_out, int64_t* __restrict__ total, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kPad = join_pad<K>();
   K* const b_sk = reinterpret_cast<K*>(smem);  // staging areas (16-byte aligned)
@@ -216,21 +225,19 @@ __global__ void __launch_bounds__(kJThreads, TJ_JMINB)
   __syncthreads();
   const int64_t t = s_t;
   if (t >= total_tiles) return;
-  const int j = tile_job ? tile_job[t] : find_job_j(jobs, num_jobs, t);
-  const JoinJob<K> J = jobs[j];
-  const int64_t a = ra[t];
-  const int64_t nrr = rb[t] - a;
-  const int64_t lt = t - J.tile0;
-  const int64_t row0 = lt * kJTile;
-  const int nv = (int)min((int64_t)kJTile, J.ns - row0);
-  const K* __restrict__ rk_g = J.rk + a;
-  const K* __restrict__ rv_g = J.rv + a;
+  const JTile<K> T = tiles[t];
+  const int j = T.j;
+  const int64_t nrr = T.nrr;
+  const int64_t lt = T.lt;
+  const int nv = T.nv;
+  const K* __restrict__ rk_g = T.rk;
+  const K* __restrict__ rv_g = T.rv;
   const int64_t nchunks = (nrr + kRCap - 1) / kRCap;
   const bool onchip = nchunks <= kMaxChunks;
 
   // 1. stage S and the first R chunk
-  const K* s_sk = join_copy_async<K>(b_sk, J.sk + row0, nv);
-  const K* s_sv = join_copy_async<K>(b_sv, J.sv + row0, nv);
+  const K* s_sk = join_copy_async<K>(b_sk, T.sk, nv);
+  const K* s_sv = join_copy_async<K>(b_sv, T.sv, nv);
   K* s_rk = b_rk;  // the staged R chunk (where its copy starts)
   K* s_rv = b_rv;
   if (onchip && nchunks > 0) {
@@ -465,8 +472,8 @@ __global__ void __launch_bounds__(kJThreads, TJ_JMINB)
       const uint32_t m = __ballot_sync(0xFFFFFFFFu, cnt[u] != 0u);
       if (cnt[u] != 0u) {
         const uint64_t o = off + __popc(m & ltm);
-        const K sid = s_sv[wbase + u * 32 + lane];
         const int64_t st0 = (int64_t)start[u];
+        const K sid = s_sv[wbase + u * 32 + lane];
         const K rid = st0 >= cres ? s_rv[st0 - cres] : rv_g[st0];
         if (vec) {
           P pr;
@@ -526,7 +533,7 @@ __global__ void __launch_bounds__(kJThreads, TJ_JMINB)
       }
     }
     __syncthreads();
-    const K* __restrict__ sv_g = J.sv + row0;
+    const K* __restrict__ sv_g = T.sv;
     K* __restrict__ o = out + 2 * E;
     for (uint64_t x = tid; x < C; x += kJThreads) {
       int lo = 0, hi = nv - 1;  // last q with s_off[q] <= x
@@ -547,11 +554,10 @@ __global__ void __launch_bounds__(kJThreads, TJ_JMINB)
 // ---------------------------------------------------------------------------
 template <typename K>
 cudaError_t launch_tile_ranges(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                               int64_t* d_ra, int64_t* d_rb, cudaStream_t st,
-                               const int32_t* d_tile_job) {
+                               JTile<K>* d_tiles, cudaStream_t st, const int32_t* d_tile_job) {
   if (total_tiles <= 0) return cudaSuccess;
   const int64_t grid = (total_tiles * 32 + kThreads - 1) / kThreads;
-  k_tile_ranges<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_ra, d_rb,
+  k_tile_ranges<K><<<(unsigned)grid, kThreads, 0, st>>>(d_jobs, num_jobs, total_tiles, d_tiles,
                                                         d_tile_job);
   return cudaGetLastError();
 }
@@ -602,16 +608,15 @@ cudaError_t launch_fill_join_tile_job(const JoinJob<K>* d_jobs, int num_jobs, in
 }
 
 template <typename K>
-cudaError_t launch_join(const JoinJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                        const int64_t* d_ra, const int64_t* d_rb, uint64_t* d_lookback,
+cudaError_t launch_join(int64_t total_tiles, const JTile<K>* d_tiles, uint64_t* d_lookback,
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
                         const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
-                        int* d_err, cudaStream_t st, const int32_t* d_tile_job) {
+                        int* d_err, cudaStream_t st) {
   if (total_tiles <= 0) return cudaSuccess;
   const size_t smem = join_smem_bytes<K>();
   k_join<K><<<(unsigned)total_tiles, kJThreads, smem, st>>>(
-      d_jobs, num_jobs, total_tiles, d_ra, d_rb, d_lookback, d_tile_counter, out, capacity,
-      d_out_base, d_job_out, d_total, d_err, d_tile_job);
+      total_tiles, d_tiles, d_lookback, d_tile_counter, out, capacity, d_out_base, d_job_out,
+      d_total, d_err);
   return cudaGetLastError();
 }
 
@@ -655,14 +660,13 @@ cudaError_t join_init_attributes() {
 }
 
 #define TJ_INSTANTIATE_JOIN(K)                                                                  \
-  template cudaError_t launch_tile_ranges<K>(const JoinJob<K>*, int, int64_t, int64_t*, int64_t*, \
+  template cudaError_t launch_tile_ranges<K>(const JoinJob<K>*, int, int64_t, JTile<K>*,        \
                                              cudaStream_t, const int32_t*);                     \
   template cudaError_t launch_fill_join_tile_job<K>(const JoinJob<K>*, int, int32_t*,            \
                                                     cudaStream_t);                              \
-  template cudaError_t launch_join<K>(const JoinJob<K>*, int, int64_t, const int64_t*,           \
-                                      const int64_t*, uint64_t*, uint32_t*, K*, int64_t,          \
-                                      const int64_t*, int64_t*, int64_t*, int*, cudaStream_t,     \
-                                      const int32_t*);                                            \
+  template cudaError_t launch_join<K>(int64_t, const JTile<K>*, uint64_t*, uint32_t*, K*,        \
+                                      int64_t, const int64_t*, int64_t*, int64_t*, int*,          \
+                                      cudaStream_t);                                              \
   template cudaError_t launch_fix_job_out<K>(const JoinJob<K>*, int, int64_t, int64_t*,          \
                                              const int64_t*, cudaStream_t);                     \
   template cudaError_t launch_group_maps<K>(const RadixJob<K>*, int, int32_t*, const JoinJob<K>*, \
