@@ -378,8 +378,9 @@ def run_tj(args, ws, rank, local):
     # k_onesweep dominates the step.  The groups of a budgeted join alternate
     # between two streams and are traced per group ("group/lanes": sort passes
     # and join), since their launches overlap: the kernel's figure comes from
-    # its launches that ran alone (the route pass and tj_sort's passes), the
-    # whole step's from all traced bytes over the step time.
+    # its launches that ran alone (the route passes, tj_sort's passes and the
+    # learned router's sample sorts), the whole step's from all traced bytes
+    # over the step time.
     solo = [trace[k] for k in ("route", "onesweep") if k in trace]
     if solo:
         by = sum(d["bytes"] for d in solo)
@@ -390,7 +391,9 @@ def run_tj(args, ws, rank, local):
         per_launch_alg = by / n_l
         step_bytes = sum(v["bytes"] for v in trace.values()) / len(step_ms)
         step_ach = step_bytes / (ms_step / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_onesweep (launches that ran alone: route, tj_sort)",
+        roof = {"bound": "hbm",
+                "kernel": "k_onesweep (launches that ran alone: route passes, tj_sort, the "
+                          "router's sample sorts)",
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
                 "traffic": (per_launch_alg * ratio) if ratio else None,
