@@ -426,6 +426,9 @@ def run_tj(args, ws, rank, local):
         extras = {"small_int32_1e6": extra_small(),
                   "learned_vs_radix": extra_learned(args.scale),
                   "batched_vs_one_at_a_time": extra_batched(args.scale),
+                  "regime_shift": extra_regime(args.scale),
+                  "late_materialisation": extra_payload(args.scale),
+                  "sort_single_vs_multi_key": extra_sort_multi(args.scale),
                   "serving": extra_serving(args.scale)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -480,6 +483,109 @@ def extra_small():
             "sort_us": 1e3 * ms_sort, "sort_keys_per_s": 1e6 / (ms_sort / 1e3)}
 
 
+def extra_regime(scale, budget_mb=256):
+    """Time against size at a fixed device budget: FK joins (R = N/5 unique
+    int64 keys, S = 4N/5 Zipf(0.8) foreign keys) for N from 1.25e6 to 3.2e8,
+    under a 256 MiB budget and unbounded.  The paper's relational path pays a
+    spill term once N outgrows its working memory (Sec. 6); here every size
+    stays within the budget, so the cost per tuple should not jump."""
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    rows = []
+    for n in (1_250_000, 5_000_000, 20_000_000, 80_000_000, 320_000_000):
+        n = max(1000, int(n * scale))
+        n_r, n_s = n // 5, n - n // 5
+        kr, ir, ks, is_ = datagen.fk_zipf(n_r, n_s, 0.8, 20260231, device="cuda")
+        out = torch.empty((n_s, 2), dtype=torch.int64, device="cuda")
+        row = {"n": n, "n_r": n_r, "n_s": n_s}
+        for name, budget in (("budget", budget_mb << 20), ("unbounded", 0)):
+            ms, r = _events_ms(lambda: api.join_inner(kr, ir, ks, is_, out=out,
+                                                      mem_budget_bytes=budget), reps=3, warm=2)
+            assert r.shape[0] == n_s
+            st = api.stats()
+            row[name] = {"ms": ms, "ns_per_tuple": 1e6 * ms / n, "tuples_per_s": n / (ms / 1e3),
+                         "groups": st["groups"], "lanes": st["lanes"],
+                         "scratch_peak_bytes": st["scratch_peak"]}
+        rows.append(row)
+        del kr, ir, ks, is_, out
+        torch.cuda.empty_cache()
+    return {"workload": "fk_zipf0.8_int64_R=N/5_S=4N/5", "mem_budget_bytes": budget_mb << 20,
+            "sizes": rows}
+
+
+def extra_payload(scale):
+    """Late materialisation (paper Sec. 3.1, Sec. 3.2): the C1 join at Zipf 0.8
+    (R = 10^8, S = 4x10^8 int64 keys, 256 MiB budget), then two int64 payload
+    columns of R and two of S gathered through its 4x10^8 (r_id, s_id) pairs."""
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    n_r, n_s = max(1000, int(10**8 * scale)), max(4000, int(4 * 10**8 * scale))
+    kr, ir, ks, is_ = datagen.fk_zipf(n_r, n_s, 0.8, 20260232, device="cuda")
+    pairs = api.join_inner(kr, ir, ks, is_, mem_budget_bytes=256 << 20)
+    del kr, ks
+    g = torch.Generator(device="cuda").manual_seed(7)
+    rc = [torch.randint(0, 1 << 62, (n_r,), generator=g, device="cuda") for _ in range(2)]
+    sc = [torch.randint(0, 1 << 62, (n_s,), generator=g, device="cuda") for _ in range(2)]
+    ms, (ro, so) = _events_ms(lambda: api.gather_pairs(pairs, rc, sc), reps=3, warm=1)
+    n = pairs.shape[0]
+    alg = n * (16 + 4 * 16)  # pair read + per column 8 B read and 8 B written
+    res = {"workload": "fk_join_1e8x4e8_zipf0.8_int64 + 2 R and 2 S int64 payload columns",
+           "pairs": int(n), "gather_ms": ms, "pairs_per_s": n / (ms / 1e3),
+           "alg_bytes": alg, "alg_gbs": alg / (ms / 1e3) / 1e9,
+           "note": "the payload reads are at data-dependent rows: one 32-byte sector per "
+                   "8-byte element unless neighbouring pairs share it"}
+    del pairs, rc, sc, ro, so, ir, is_
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_sort_multi(scale):
+    """Single-key versus multi-attribute sort keys (paper Sec. 3.2 and Sec. 5.3,
+    Fig. 5) and forced versus selected paths (Sec. 5.4): int64 columns k0 in
+    [0, 2^20), k1 in [0, 2^30), k2 in [0, 2^10), ids = positions; ORDER BY k1
+    alone, by (k0, k1) and by (k0, k1, k2), each multi-key order sorted per
+    column, folded into one key, and on the path tj_sort_multi selects.  At
+    10^8 rows and at the paper's 10^6."""
+    import torch
+
+    from paper_2602_21237_gb300 import api
+
+    res = {}
+    for n in (max(1000, int(10**8 * scale)), 10**6):
+        g = torch.Generator(device="cuda").manual_seed(11)
+        k0 = torch.randint(0, 1 << 20, (n,), generator=g, device="cuda")
+        k1 = torch.randint(0, 1 << 30, (n,), generator=g, device="cuda")
+        k2 = torch.randint(0, 1 << 10, (n,), generator=g, device="cuda")
+        ids = torch.arange(n, device="cuda")
+        w = [torch.empty_like(k0) for _ in range(4)]
+
+        def load(srcs):
+            for d, x in zip(w, list(srcs) + [ids]):
+                d.copy_(x)
+
+        def timed(srcs, fn):
+            ms_copy, _ = _events_ms(lambda: load(srcs), reps=3, warm=1)
+            ms, _ = _events_ms(lambda: (load(srcs), fn()), reps=3, warm=1)
+            return max(0.0, ms - ms_copy)
+
+        row = {"rows": n, "single_key_ms": timed([k1], lambda: api.sort(w[0], w[1]))}
+        for name, cols in (("two_keys", [k0, k1]), ("three_keys", [k0, k1, k2])):
+            m = len(cols)
+            for path in ("per_column", "packed", "auto"):
+                row[f"{name}_{path}_ms"] = timed(
+                    cols, lambda p=path, m=m: api.sort_multi(w[:m], w[m], path=p))
+            row[f"{name}_auto_packed"] = bool(api.stats()["packed_keys"])
+        res[f"n={n}"] = row
+        del k0, k1, k2, ids, w
+        torch.cuda.empty_cache()
+    return {"workload": "int64 k0 in [0,2^20), k1 in [0,2^30), k2 in [0,2^10), ids = positions",
+            "sizes": res}
+
+
 def extra_learned(scale):
     """Learned partitioning (PLA, MLP) versus equal-width radix ranges on the
     log-normal mixture workload: 2^28 int64 keys per side, 1024 batches."""
@@ -522,6 +628,17 @@ def extra_learned(scale):
                            "scratch_peak_bytes": st["scratch_peak"]}
         except api.TjError as e:
             under[name] = {"status": f"{e.name}: {e.detail}"}
+    # the path selected at execution time (Sec. 3.3) against the forced ones
+    # (Sec. 5.4): unbounded, and under the 1 GB budget
+    for label, budget_b in (("auto_unbounded", 0), ("auto_under_1GB_budget", budget)):
+        ms, r = _events_ms(lambda: api.join_inner(kr, ir, ks, is_, out=out, router="auto",
+                                                  partitions=1024, mem_budget_bytes=budget_b))
+        assert r.shape[0] == pairs
+        st = api.stats()
+        res[label] = {"ms": ms, "tuples_per_s": 2 * n / (ms / 1e3),
+                      "path": "single_pass" if st["partitions"] == 0 else
+                      {2: "radix", 3: "pla", 4: "mlp"}.get(st["learned"] % 100, "?"),
+                      "groups": st["groups"]}
     res["under_1GB_budget"] = under
     del kr, ir, ks, is_, out
     torch.cuda.empty_cache()

@@ -71,7 +71,10 @@ typedef struct {
   int32_t tile_rows;       /* batched join: rows per onesweep tile used */
   int32_t digit_cap;       /* batched join: widest radix digit allowed */
   int32_t lanes;           /* streams the groups alternate between (2 when the budget
-                              needs several groups: each lane gets half of it) */
+                              needs several groups: each lane gets half of it; 0 for
+                              the single pass) */
+  int32_t packed_keys;     /* tj_sort_multi: 1 if the key columns were folded into one
+                              key (their significant bits fit it), 0 if sorted per column */
 } tj_stats;
 
 /*
@@ -143,6 +146,31 @@ tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, i
 tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream);
 
 /*
+ * ORDER BY several key columns, k_0 first (Sec. 3.2: a multi-attribute sort
+ * key relocates rows along each attribute's axis instead of folding the
+ * attributes into one linear order; Sec. 4.2: sorting as relocation).  Rows
+ * are ordered by k_0, ties by k_1, and so on; rows equal in every key keep
+ * their input order (stable).  The path is chosen at execution time from the
+ * columns' key statistics (Sec. 3.3): when the significant bits of all
+ * columns (max - min of each) fit one key of type dt (63 or 31 bits), the
+ * columns are folded into that key, sorted once and unfolded; otherwise one
+ * stable radix sort per column, last column first, carries the row
+ * permutation, and every column and `ids` are permuted once at the end.
+ * tj_stats.packed_keys reports the path; `path` forces one (Sec. 5.4
+ * compares forced paths with the one selected at execution time):
+ * 0 = selected from the statistics, 1 = per column, 2 = folded
+ * (TJ_ERR_INVALID if the bits do not fit).
+ *
+ * cols : HOST array of n_cols DEVICE key columns of n elements of type dt
+ *   (signed two's-complement), sorted in place.
+ * ids  : DEVICE array of n elements of type dt, permuted along (may be NULL).
+ * n_cols = 0 or n <= 1 leaves everything as it is; at most 16 columns.
+ * Synchronises `stream` (after the key statistics, and once per sort).
+ */
+tj_status tj_sort_multi(tj_dtype dt, void* const* cols, int32_t n_cols, void* ids, int64_t n,
+                        int32_t path, void* stream);
+
+/*
  * tj_sort for callers that cannot allocate device memory (the paper has no
  * counterpart).  Some callers cannot call cudaMalloc, cudaMallocAsync or any
  * allocator when they sort: code that runs while an outer framework owns the
@@ -162,6 +190,34 @@ tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream);
  * Arguments, ordering of the result and synchronisation are those of tj_sort.
  */
 tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream);
+
+/*
+ * Late materialisation of payload columns.  Sec. 3.1 keeps rows in their
+ * multi-attribute form until materialisation is needed; Sec. 3.2 joins
+ * R(A, B, C) with S(B, D, E) by aligning both on the axis of B.  tj_join_inner
+ * aligns the key axis and yields (r_id, s_id) pairs; this call then gathers the
+ * other attributes once, at the end: for every pair i and column c,
+ *   cols[c].dst[i] = cols[c].src[pairs[2i + cols[c].side]].
+ *
+ * id_dt : width of the ids in `pairs` (TJ_I32 or TJ_I64).  Ids are row
+ *   positions: 0 <= r_id < n_r, 0 <= s_id < n_s.
+ * pairs : DEVICE array of n (r_id, s_id) pairs, as tj_join_inner writes them.
+ * cols  : HOST array of n_cols column descriptors: src is a DEVICE column of
+ *   the relation named by side (0 = R, n_r elements; 1 = S, n_s elements), dst
+ *   a DEVICE column of n elements, elem_bytes 4 or 8 (any 4- or 8-byte type:
+ *   bytes are copied).  All memory is caller-owned; src is not modified.
+ * Returns TJ_ERR_INVALID for a bad argument, or when an id is out of range
+ * (the rows with such ids are not written).  Synchronises `stream` once (one
+ * device-to-host read of an error word).
+ */
+typedef struct {
+  const void* src;
+  void* dst;
+  int32_t side;
+  int32_t elem_bytes;
+} tj_column;
+tj_status tj_gather_pairs(tj_dtype id_dt, const void* pairs, int64_t n, int64_t n_r,
+                          int64_t n_s, const tj_column* cols, int32_t n_cols, void* stream);
 
 /*
  * Many independent inner joins in one batch (no counterpart in the paper; it

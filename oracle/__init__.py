@@ -123,3 +123,36 @@ def join_batch(r_off, s_off, keys_r, ids_r, keys_s, ids_s):
                                 off.ctypes.data)
     assert got == total
     return out, off
+
+
+def gather_pairs(pairs, r_cols=(), s_cols=()):
+    """Late materialisation (Sec. 3.1; the multi-attribute join of Sec. 3.2,
+    R(A, B, C) with S(B, D, E) on B): row i of every output column is the R
+    column at r_id = pairs[i, 0], or the S column at s_id = pairs[i, 1].  Ids
+    are row positions; one outside its relation raises ValueError.  Returns
+    (R outputs, S outputs) as lists of numpy arrays."""
+    p = np.asarray(pairs).reshape(-1, 2)
+    outs = []
+    for side, cols in ((0, r_cols), (1, s_cols)):
+        res = []
+        for c in cols:
+            c = np.asarray(c)
+            ids = p[:, side]
+            if ids.size and (ids.min() < 0 or ids.max() >= c.size):
+                raise ValueError("oracle: an id is not a row of its relation")
+            res.append(c[ids])
+        outs.append(res)
+    return outs[0], outs[1]
+
+
+def sort_multi(cols, ids=None):
+    """ORDER BY several key columns, cols[0] first (Sec. 3.2's multi-attribute
+    sort key; Sec. 4.2), stable: rows equal in every key keep their input
+    order.  Returns (sorted copies of the columns, ids permuted along)."""
+    cols = [np.asarray(c) for c in cols]
+    n = cols[0].size if cols else (0 if ids is None else np.asarray(ids).size)
+    if not cols or n <= 1:
+        return [c.copy() for c in cols], None if ids is None else np.array(ids, copy=True)
+    # np.lexsort: the last key given is the primary one; the sort is stable
+    perm = np.lexsort(tuple(reversed(cols)))
+    return [c[perm] for c in cols], None if ids is None else np.asarray(ids)[perm]

@@ -40,7 +40,7 @@ class _Stats(ctypes.Structure):
                 ("heavy_keys", ctypes.c_int32), ("max_partition", ctypes.c_int64),
                 ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double),
                 ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32),
-                ("lanes", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("packed_keys", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):
@@ -48,6 +48,11 @@ class _Opts(ctypes.Structure):
                 ("sample_stride", ctypes.c_int32), ("pla_segments", ctypes.c_int32),
                 ("mlp_steps", ctypes.c_int32), ("mlp_batch", ctypes.c_int32),
                 ("mlp_lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class _Column(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("side", ctypes.c_int32),
+                ("elem_bytes", ctypes.c_int32)]
 
 
 ROUTERS = {"auto": 0, "single": 1, "radix": 2, "pla": 3, "mlp": 4}
@@ -73,6 +78,12 @@ def _load():
                                          ctypes.POINTER(_Opts), vp, i64, p64, vp]
         lib.tj_join_inner_ex.restype = ci
         lib.tj_sort.argtypes = [ci, vp, vp, i64, vp]
+        lib.tj_gather_pairs.argtypes = [ci, vp, i64, i64, i64, ctypes.POINTER(_Column),
+                                        ctypes.c_int32, vp]
+        lib.tj_gather_pairs.restype = ci
+        lib.tj_sort_multi.argtypes = [ci, ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, vp,
+                                      i64, ctypes.c_int32, vp]
+        lib.tj_sort_multi.restype = ci
         lib.tj_sort.restype = ci
         lib.tj_sort_noalloc.argtypes = [ci, vp, vp, i64, vp]
         lib.tj_sort_noalloc.restype = ci
@@ -255,6 +266,74 @@ def sort(keys, ids, stream=None):
         _check(lib, lib.tj_sort(dt, keys.data_ptr(), ids.data_ptr(), keys.numel(),
                                 _stream(stream)))
     return keys, ids
+
+
+SORT_PATHS = {"auto": 0, "per_column": 1, "packed": 2}
+
+
+def sort_multi(cols, ids=None, stream=None, path: str = "auto"):
+    """ORDER BY several key columns, cols[0] first (paper Sec. 3.2's
+    multi-attribute sort key, Sec. 4.2), stable, in place.  `path`: 'auto'
+    (chosen from the columns' key statistics, Sec. 3.3), 'per_column' (one
+    radix sort per column carrying the row permutation) or 'packed' (the
+    columns folded into one key; TjError if their bits do not fit).  Columns
+    and ids: 1-D contiguous CUDA tensors of one int dtype, same length.
+    Returns (cols, ids)."""
+    lib = _load()
+    cols = list(cols)
+    if not cols:
+        return cols, ids
+    dt = _dt(cols[0])
+    n = cols[0].numel()
+    for i, c in enumerate(cols):
+        _need(c, cols[0].dtype, cols[0].device, f"cols[{i}]")
+        if c.numel() != n:
+            raise ValueError("key columns must have the same length")
+    if ids is not None:
+        _need(ids, cols[0].dtype, cols[0].device, "ids")
+        if ids.numel() != n:
+            raise ValueError("ids must have the columns' length")
+    ptrs = (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols])
+    with torch.cuda.device(cols[0].device):
+        _check(lib, lib.tj_sort_multi(dt, ptrs, len(cols), None if ids is None else ids.data_ptr(),
+                                      n, SORT_PATHS[path], _stream(stream)))
+    return cols, ids
+
+
+def gather_pairs(pairs, r_cols=(), s_cols=(), n_r=None, n_s=None, stream=None):
+    """Late materialisation (paper Sec. 3.1, Sec. 3.2): for a (n, 2) tensor of
+    (r_id, s_id) pairs, as join_inner returns them, gather every column of R
+    at r_id and of S at s_id.  Columns are 1-D contiguous CUDA tensors of a
+    4- or 8-byte dtype, all of R's n_r rows long and all of S's n_s (n_r and
+    n_s default to the columns' length).  Returns (R outputs, S outputs), lists
+    of n-element tensors of the columns' dtypes."""
+    lib = _load()
+    if pairs.dim() != 2 or pairs.shape[1] != 2 or not pairs.is_contiguous() or not pairs.is_cuda:
+        raise ValueError("pairs must be a contiguous (n, 2) CUDA tensor")
+    dt = _dt(pairs)
+    dev = pairs.device
+    n = pairs.shape[0]
+    r_cols, s_cols = list(r_cols), list(s_cols)
+    sizes = {}
+    for side, cols, given in ((0, r_cols, n_r), (1, s_cols, n_s)):
+        rows = given if given is not None else (cols[0].numel() if cols else 0)
+        for c in cols:
+            if not isinstance(c, torch.Tensor) or not c.is_cuda or c.device != dev:
+                raise TypeError("columns must be CUDA tensors on the pairs' device")
+            if c.dim() != 1 or not c.is_contiguous() or c.numel() != rows:
+                raise ValueError("columns of a side must be 1-D, contiguous and of its length")
+            if c.element_size() not in (4, 8):
+                raise TypeError("columns must have 4- or 8-byte elements")
+        sizes[side] = rows
+    outs = [torch.empty(n, dtype=c.dtype, device=dev) for c in r_cols + s_cols]
+    desc = (_Column * max(1, len(outs)))()
+    for i, (c, o) in enumerate(zip(r_cols + s_cols, outs)):
+        desc[i] = _Column(c.data_ptr(), o.data_ptr(), 0 if i < len(r_cols) else 1,
+                          c.element_size())
+    with torch.cuda.device(dev):
+        _check(lib, lib.tj_gather_pairs(dt, pairs.data_ptr(), n, sizes[0], sizes[1], desc,
+                                        len(outs), _stream(stream)))
+    return outs[:len(r_cols)], outs[len(r_cols):]
 
 
 def join_batch(r_off, s_off, keys_r, ids_r, keys_s, ids_s, out=None, stream=None,

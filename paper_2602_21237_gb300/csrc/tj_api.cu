@@ -1492,6 +1492,123 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   return TJ_OK;
 }
 
+// ---- multi-column sort ----------------------------------------------------------------
+// Key statistics of every column first (one launch).  If the columns'
+// significant bits fit one key of type K (without its sign bit), they are
+// folded into it (k_0 highest), sorted once with the ids and unfolded.
+// Otherwise stable LSD over the columns, the last one first: the row
+// permutation idx starts as the identity; per column c, key[i] =
+// cols[c][idx[i]] and (key, idx) is sorted stably by key, so rows equal in
+// column c keep the order the later columns gave them; then every column and
+// the ids are permuted by idx (column 0 is already sorted in `key`).
+template <typename K>
+tj_status sort_multi_impl(K* const* cols, int ncols, K* ids, int64_t n, int path,
+                          cudaStream_t st) {
+  tj_stats stats = {};
+  stats.groups = 1;
+  g_stats = stats;
+  if (n <= 1 || ncols == 0) return TJ_OK;
+  if (ncols > kGatherCols) return set_err(TJ_ERR_INVALID, "at most %d key columns", kGatherCols);
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  int dev = 0, sms = 0;
+  TJ_CUDA(cudaGetDevice(&dev));
+  TJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t tiles = ceil_div(n, kTile);
+  Carve c;
+  const size_t o_jobs = c.add<RadixJob<K>>((size_t)ncols);
+  const size_t o_stats = c.add<KeyStats>((size_t)ncols);
+  const size_t o_idx = c.add<K>((size_t)n), o_key = c.add<K>((size_t)n),
+               o_tmp = c.add<K>((size_t)n);
+  Block blk;
+  TJ_CUDA(blk.alloc(c.off, st));
+  K* idx = blk.at<K>(o_idx);
+  K* key = blk.at<K>(o_key);
+  K* tmp = blk.at<K>(o_tmp);
+  Tracer tr(st);
+  const double w = (double)sizeof(K);
+  // 1. key statistics of every column
+  std::vector<RadixJob<K>> hj((size_t)ncols);
+  for (int col = 0; col < ncols; ++col) {
+    memset(&hj[(size_t)col], 0, sizeof(RadixJob<K>));
+    hj[(size_t)col].keys = cols[col];
+    hj[(size_t)col].n = n;
+    hj[(size_t)col].tile0 = col * tiles;
+  }
+  TJ_CUDA(cudaMemcpyAsync(blk.at<RadixJob<K>>(o_jobs), hj.data(), hj.size() * sizeof(RadixJob<K>),
+                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(cudaMemsetAsync(blk.at<KeyStats>(o_stats), 0xFF, (size_t)ncols * sizeof(KeyStats), st));
+  tr.begin("stats", w * n * ncols);
+  TJ_CUDA(launch_stats<K>(blk.at<RadixJob<K>>(o_jobs), ncols, tiles * ncols,
+                          blk.at<KeyStats>(o_stats), st));
+  tr.end();
+  std::vector<KeyStats> hs((size_t)ncols);
+  TJ_CUDA(cudaMemcpyAsync(hs.data(), blk.at<KeyStats>(o_stats), hs.size() * sizeof(KeyStats),
+                          cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  tr.flush();
+  PackArgs<K> pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.n = ncols;
+  int total_bits = 0;
+  for (int col = ncols - 1; col >= 0; --col) {
+    const K lo = key_of<K>(hs[(size_t)col].min_u), hi = key_of<K>(~hs[(size_t)col].max_u);
+    const int b = bitlen(range_of<K>(lo, hi));
+    pa.col[col] = cols[col];
+    pa.lo[col] = lo;
+    pa.bits[col] = b;
+    pa.shift[col] = std::min(total_bits, 8 * (int)sizeof(K) - 1);
+    total_bits += b;
+  }
+  stats.key_bits = total_bits;
+  const bool fits = total_bits <= 8 * (int)sizeof(K) - 1;
+  if (path == 2 && !fits)
+    return set_err(TJ_ERR_INVALID, "%d key bits do not fit one %d-bit key", total_bits,
+                   8 * (int)sizeof(K));
+  if (fits && path != 1) {
+    // 2a. one key: fold, sort with the ids (or a scratch array), unfold
+    tr.begin("pack", 2.0 * w * n * ncols);
+    TJ_CUDA(launch_pack<K>(pa, key, n, false, sms, st));
+    tr.end();
+    tr.flush();
+    s = sort_impl<K>(key, ids ? ids : idx, n, st);
+    if (s != TJ_OK) return s;
+    tr.begin("pack", 2.0 * w * n * ncols);
+    TJ_CUDA(launch_pack<K>(pa, key, n, true, sms, st));
+    tr.end();
+    stats.packed_keys = 1;
+  } else {
+    // 2b. one sort per column, carrying the row permutation
+    TJ_CUDA(launch_iota<K>(idx, n, sms, st));
+    for (int col = ncols - 1; col >= 0; --col) {
+      tr.begin("gather", 3.0 * w * n);
+      TJ_CUDA(launch_gather_idx<K>(cols[col], idx, key, n, sms, st));
+      tr.end();
+      tr.flush();
+      s = sort_impl<K>(key, idx, n, st);
+      if (s != TJ_OK) return s;
+    }
+    for (int col = 1; col < ncols; ++col) {
+      tr.begin("gather", 3.0 * w * n);
+      TJ_CUDA(launch_gather_idx<K>(cols[col], idx, tmp, n, sms, st));
+      tr.end();
+      TJ_CUDA(cudaMemcpyAsync(cols[col], tmp, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st));
+    }
+    TJ_CUDA(cudaMemcpyAsync(cols[0], key, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st));
+    if (ids) {
+      tr.begin("gather", 3.0 * w * n);
+      TJ_CUDA(launch_gather_idx<K>(ids, idx, tmp, n, sms, st));
+      tr.end();
+      TJ_CUDA(cudaMemcpyAsync(ids, tmp, (size_t)n * sizeof(K), cudaMemcpyDeviceToDevice, st));
+    }
+    stats.groups = ncols;
+  }
+  TJ_CUDA(cudaStreamSynchronize(st));
+  tr.flush();
+  g_stats = stats;
+  return TJ_OK;
+}
+
 // ---- batch of joins -------------------------------------------------------------------
 // Job j joins R rows [r_off[j], r_off[j+1]) with S rows [s_off[j], s_off[j+1]).
 // Radix jobs are laid out R_0, S_0, R_1, S_1, ...; every pair shares its own
@@ -1957,6 +2074,25 @@ tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* s
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
 }
 
+tj_status tj_sort_multi(tj_dtype dt, void* const* cols, int32_t n_cols, void* ids, int64_t n,
+                        int32_t path, void* stream) {
+  g_err[0] = 0;
+  if (n < 0 || n_cols < 0) return set_err(TJ_ERR_INVALID, "negative size");
+  if (path < 0 || path > 2) return set_err(TJ_ERR_INVALID, "path %d (0, 1 or 2)", path);
+  if (n >= kMaxRows) return set_err(TJ_ERR_INVALID, "n >= 2^30 rows is not supported");
+  if (n_cols > 0 && !cols) return set_err(TJ_ERR_INVALID, "cols is NULL");
+  for (int32_t c = 0; c < n_cols; ++c)
+    if (bad_ptr(cols[c], n)) return set_err(TJ_ERR_INVALID, "column %d is NULL", c);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == TJ_I32)
+    return sort_multi_impl<int32_t>(reinterpret_cast<int32_t* const*>(cols), n_cols,
+                                    (int32_t*)ids, n, path, st);
+  if (dt == TJ_I64)
+    return sort_multi_impl<int64_t>(reinterpret_cast<int64_t* const*>(cols), n_cols,
+                                    (int64_t*)ids, n, path, st);
+  return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
 tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
   g_err[0] = 0;
   if (n < 0) return set_err(TJ_ERR_INVALID, "negative size");
@@ -1967,6 +2103,64 @@ tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
   if (dt == TJ_I32) return sort_impl<int32_t>((int32_t*)keys, (int32_t*)ids, n, st);
   if (dt == TJ_I64) return sort_impl<int64_t>((int64_t*)keys, (int64_t*)ids, n, st);
   return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+}
+
+tj_status tj_gather_pairs(tj_dtype id_dt, const void* pairs, int64_t n, int64_t n_r,
+                          int64_t n_s, const tj_column* cols, int32_t n_cols, void* stream) {
+  g_err[0] = 0;
+  if (n < 0 || n_r < 0 || n_s < 0 || n_cols < 0) return set_err(TJ_ERR_INVALID, "negative size");
+  if (id_dt != TJ_I32 && id_dt != TJ_I64) return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)id_dt);
+  if (n_cols > 0 && !cols) return set_err(TJ_ERR_INVALID, "cols is NULL");
+  const size_t idw = id_dt == TJ_I32 ? 4 : 8;
+  if (bad_ptr(pairs, n) || (n > 0 && ((uintptr_t)pairs % (2 * idw)) != 0))
+    return set_err(TJ_ERR_INVALID, "pairs: NULL or not aligned to a pair");
+  for (int32_t c = 0; c < n_cols; ++c) {
+    const tj_column& x = cols[c];
+    if (x.side != 0 && x.side != 1) return set_err(TJ_ERR_INVALID, "column %d: side %d", c, x.side);
+    if (x.elem_bytes != 4 && x.elem_bytes != 8)
+      return set_err(TJ_ERR_INVALID, "column %d: elem_bytes %d (4 or 8)", c, x.elem_bytes);
+    const int64_t rows = x.side ? n_s : n_r;
+    if (bad_ptr(x.src, rows) || bad_ptr(x.dst, n) ||
+        ((uintptr_t)x.src % (uintptr_t)x.elem_bytes) != 0 ||
+        ((uintptr_t)x.dst % (uintptr_t)x.elem_bytes) != 0)
+      return set_err(TJ_ERR_INVALID, "column %d: NULL or misaligned pointer", c);
+  }
+  if (n == 0 || n_cols == 0) return TJ_OK;
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  TJ_CUDA(cudaGetDevice(&dev));
+  TJ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  Block eb;
+  TJ_CUDA(eb.alloc(256, st));
+  TJ_CUDA(cudaMemsetAsync(eb.p, 0, sizeof(int), st));
+  Tracer tr(st);
+  for (int32_t c0 = 0; c0 < n_cols; c0 += kGatherCols) {
+    GatherArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = std::min<int32_t>(kGatherCols, n_cols - c0);
+    double by = 2.0 * (double)idw * (double)n;
+    for (int i = 0; i < a.n; ++i) {
+      const tj_column& x = cols[c0 + i];
+      a.c[i] = GatherCol{x.src, x.dst, x.side, x.elem_bytes};
+      by += 2.0 * (double)x.elem_bytes * (double)n;
+    }
+    tr.begin("gather", by);
+    if (id_dt == TJ_I32)
+      TJ_CUDA(launch_gather_pairs<int32_t>((const int32_t*)pairs, n, n_r, n_s, a, eb.at<int>(0),
+                                           sms, st));
+    else
+      TJ_CUDA(launch_gather_pairs<int64_t>((const int64_t*)pairs, n, n_r, n_s, a, eb.at<int>(0),
+                                           sms, st));
+    tr.end();
+  }
+  int h_err = 0;
+  TJ_CUDA(cudaMemcpyAsync(&h_err, eb.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TJ_CUDA(cudaStreamSynchronize(st));
+  tr.flush();
+  if (h_err) return set_err((tj_status)h_err, "an id of `pairs` is out of range");
+  return TJ_OK;
 }
 
 static tj_status batch_entry(tj_dtype dt, int64_t n_jobs, const int64_t* r_off,

@@ -156,6 +156,40 @@ struct alignas(16) JTile {
 };
 static_assert(sizeof(JTile<int64_t>) == 64 && sizeof(JTile<int32_t>) == 64, "64-byte tiles");
 
+// ---- late materialisation (tj_gather.cu) ------------------------------------
+constexpr int kGatherCols = 16;  // columns per gather launch
+struct GatherCol {
+  const void* src;  // column of R (side 0) or S (side 1)
+  void* dst;        // one element per pair
+  int32_t side;
+  int32_t bytes;    // 4 or 8
+};
+struct GatherArgs {
+  GatherCol c[kGatherCols];
+  int32_t n;
+};
+template <typename I>
+cudaError_t launch_gather_pairs(const I* pairs, int64_t n, int64_t n_r, int64_t n_s,
+                                const GatherArgs& a, int* d_err, int sms, cudaStream_t st);
+// dst[i] = src[idx[i]] (idx a permutation of [0, n)); out[i] = i
+template <typename K>
+cudaError_t launch_gather_idx(const K* src, const K* idx, K* dst, int64_t n, int sms,
+                              cudaStream_t st);
+template <typename K>
+cudaError_t launch_iota(K* out, int64_t n, int sms, cudaStream_t st);
+// key columns folded into one key (pack) and back (unpack)
+template <typename K>
+struct PackArgs {
+  K* col[kGatherCols];
+  K lo[kGatherCols];
+  int32_t shift[kGatherCols];
+  int32_t bits[kGatherCols];
+  int32_t n;
+};
+template <typename K>
+cudaError_t launch_pack(const PackArgs<K>& a, K* packed, int64_t n, bool unpack, int sms,
+                        cudaStream_t st);
+
 // ---- launchers (tj_radix.cu) -----------------------------------------------
 cudaError_t radix_init_attributes();
 // Tiles of the radix kernels have `tile` rows (kTile, or kSortThreads * items

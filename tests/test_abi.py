@@ -70,6 +70,32 @@ def test_host_side_argument_checks(lib):
         api.TJ_OK
 
 
+def test_gather_and_multi_sort_argument_checks(lib):
+    l = api._load()
+    col = api._Column(8, 16, 0, 8)
+    # negative size, unknown dtype, bad element width or side, null column
+    assert l.tj_gather_pairs(1, 16, -1, 4, 4, ctypes.byref(col), 1, 0) == api.TJ_ERR_INVALID
+    assert l.tj_gather_pairs(5, 16, 1, 4, 4, ctypes.byref(col), 1, 0) == api.TJ_ERR_INVALID
+    assert l.tj_gather_pairs(1, 16, 1, 4, 4, ctypes.byref(api._Column(8, 16, 0, 3)), 1, 0) == \
+        api.TJ_ERR_INVALID
+    assert l.tj_gather_pairs(1, 16, 1, 4, 4, ctypes.byref(api._Column(8, 16, 2, 8)), 1, 0) == \
+        api.TJ_ERR_INVALID
+    assert l.tj_gather_pairs(1, 16, 1, 4, 4, ctypes.byref(api._Column(0, 16, 0, 8)), 1, 0) == \
+        api.TJ_ERR_INVALID
+    # pairs off the pair grid (int64 ids: 16-byte pairs)
+    assert l.tj_gather_pairs(1, 8, 1, 4, 4, ctypes.byref(col), 1, 0) == api.TJ_ERR_INVALID
+    # nothing to gather needs no device work
+    assert l.tj_gather_pairs(1, 0, 0, 4, 4, ctypes.byref(col), 1, 0) == api.TJ_OK
+    assert l.tj_gather_pairs(1, 16, 3, 4, 4, None, 0, 0) == api.TJ_OK
+    ptrs = (ctypes.c_void_p * 1)(None)
+    assert l.tj_sort_multi(1, ptrs, -1, None, 4, 0, 0) == api.TJ_ERR_INVALID
+    assert l.tj_sort_multi(1, None, 1, None, 4, 0, 0) == api.TJ_ERR_INVALID
+    assert l.tj_sort_multi(1, ptrs, 1, None, 4, 0, 0) == api.TJ_ERR_INVALID  # NULL column
+    assert l.tj_sort_multi(1, ptrs, 1, None, 1, 0, 0) == api.TJ_ERR_INVALID
+    assert l.tj_sort_multi(1, ptrs, 0, None, 4, 3, 0) == api.TJ_ERR_INVALID  # unknown path
+    assert l.tj_sort_multi(1, ptrs, 0, None, 4, 0, 0) == api.TJ_OK
+
+
 def test_trace_table_is_empty_without_calls(lib):
     api.trace_reset()
     assert api.trace_table() == {}

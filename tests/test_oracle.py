@@ -209,12 +209,61 @@ def test_golden_join(name):
     assert np.array_equal(got, exp)
 
 
+def test_golden_multi_attribute_join_with_late_gather():
+    # R(A, B, C) joined with S(B, D, E) on B, the other attributes gathered
+    # through the (r_id, s_id) pairs at the end (hand-worked fixture)
+    g = _read_golden("join_payload_rabc_sbde.txt")
+    R = np.array(g["R"], np.int64).reshape(-1, 3)
+    S = np.array(g["S"], np.int64).reshape(-1, 3)
+    exp = np.array(g["J"], np.int64).reshape(-1, 5)
+    pairs = oracle.join_inner(R[:, 1], np.arange(len(R)), S[:, 0], np.arange(len(S)))
+    (a, b, c), (d, e) = oracle.gather_pairs(pairs, [R[:, 0], R[:, 1], R[:, 2]],
+                                            [S[:, 1], S[:, 2]])
+    assert np.array_equal(np.stack([a, b, c, d, e], 1), exp)
+    # a gather that takes an S column at r_id (sides swapped) is caught
+    (d_wrong,), _ = oracle.gather_pairs(pairs, [S[:4, 1]], [])
+    assert not np.array_equal(d_wrong, exp[:, 3])
+
+
+def test_gather_rejects_ids_outside_the_relation():
+    col = np.arange(5, dtype=np.int64)
+    for bad in ([[5, 0]], [[-1, 0]]):
+        with pytest.raises(ValueError):
+            oracle.gather_pairs(np.array(bad, np.int64), [col], [])
+    r, s = oracle.gather_pairs(np.zeros((0, 2), np.int64), [col], [col])
+    assert r[0].size == 0 and s[0].size == 0
+
+
 def test_golden_sort():
     g = _read_golden("sort_stable.txt")
     inp = np.array(g["IN"], np.int64).reshape(-1, 2)
     exp = np.array(g["OUT"], np.int64).reshape(-1, 2)
     k, i = oracle.sort(inp[:, 0], inp[:, 1])
     assert np.array_equal(np.stack([k, i], 1), exp)
+
+
+def test_golden_sort_multi():
+    g = _read_golden("sort_multi.txt")
+    inp = np.array(g["IN"], np.int64).reshape(-1, 3)
+    exp = np.array(g["OUT"], np.int64).reshape(-1, 3)
+    (k0, k1), ids = oracle.sort_multi([inp[:, 0], inp[:, 1]], inp[:, 2])
+    assert np.array_equal(np.stack([k0, k1, ids], 1), exp)
+    # the keys in the wrong priority (k1 first) give another order
+    (a, b), _ = oracle.sort_multi([inp[:, 1], inp[:, 0]], inp[:, 2])
+    assert not np.array_equal(np.stack([b, a], 1), exp[:, :2])
+
+
+def test_sort_multi_matches_brute_force():
+    # brute force: Python's stable sorted() on the key tuples
+    rng = np.random.default_rng(4)
+    for n, m in ((1, 2), (50, 2), (200, 3)):
+        cols = [rng.integers(-3, 4, n).astype(np.int64) for _ in range(m)]
+        ids = rng.integers(0, 1 << 40, n).astype(np.int64)
+        order = sorted(range(n), key=lambda i: tuple(int(c[i]) for c in cols))
+        got, gids = oracle.sort_multi(cols, ids)
+        for c, gc in zip(cols, got):
+            assert np.array_equal(gc, c[order])
+        assert np.array_equal(gids, ids[order])
 
 
 def test_pins_catch_planted_mistakes():
