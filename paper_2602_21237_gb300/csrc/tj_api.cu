@@ -25,7 +25,16 @@ namespace {
 thread_local char g_err[512] = {0};
 thread_local tj_stats g_stats = {};
 
+// device -> host reads waiting for the next sync_stream() (see put_small)
+struct PendingRead {
+  void* dst;
+  const unsigned char* src;
+  size_t n;
+};
+thread_local std::vector<PendingRead> g_reads;
+
 tj_status set_err(tj_status s, const char* fmt, ...) {
+  g_reads.clear();  // an error return leaves no read behind for a later sync
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
@@ -260,6 +269,81 @@ cudaError_t pinned_staging(size_t n, unsigned char** out) {
   return cudaSuccess;
 }
 
+// ---- small host <-> device transfers without the copy engines --------------------
+// Tables going to the device and counts or statistics coming back move
+// through a per-thread arena of pinned host memory that the device maps, by a
+// copy kernel on the call's stream (launch_copy_bytes): a copy engine runs
+// copies of one direction in order, so a small read queued behind a caller's
+// multi-gigabyte transfer would stall the call for all of it.  A read lands
+// in the arena and reaches its destination at the next sync_stream().  The
+// arena is reused from the start by every API call (the previous call on the
+// thread has synchronised its stream); a buffer outgrown within a call is
+// kept until then.
+struct Arena {
+  unsigned char* p = nullptr;
+  size_t cap = 0, off = 0;
+  std::vector<unsigned char*> old;
+  ~Arena() {
+    for (auto* q : old) cudaFreeHost(q);
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local Arena g_arena;
+
+void arena_reset() {
+  for (auto* q : g_arena.old) cudaFreeHost(q);
+  g_arena.old.clear();
+  g_arena.off = 0;
+  g_reads.clear();
+}
+
+cudaError_t arena_take(size_t n, unsigned char** out) {
+  const size_t need = (n + 255) & ~(size_t)255;
+  if (g_arena.off + need > g_arena.cap) {
+    const size_t cap = std::max<size_t>({need, 2 * g_arena.cap, (size_t)4 << 20});
+    unsigned char* q = nullptr;
+    cudaError_t e = cudaMallocHost((void**)&q, cap);
+    if (e != cudaSuccess) return e;
+    if (g_arena.p) g_arena.old.push_back(g_arena.p);  // still read by queued kernels
+    g_arena.p = q;
+    g_arena.cap = cap;
+    g_arena.off = 0;
+  }
+  *out = g_arena.p + g_arena.off;
+  g_arena.off += need;
+  return cudaSuccess;
+}
+
+// host -> device: the bytes are taken now (the caller may reuse `src`)
+cudaError_t put_small(void* dst, const void* src, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  unsigned char* a = nullptr;
+  cudaError_t e = arena_take(n, &a);
+  if (e != cudaSuccess) return e;
+  memcpy(a, src, n);
+  return launch_copy_bytes(dst, a, n, st);
+}
+
+// device -> host: `dst` holds the bytes after the next sync_stream()
+cudaError_t get_small(void* dst, const void* src, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  unsigned char* a = nullptr;
+  cudaError_t e = arena_take(n, &a);
+  if (e != cudaSuccess) return e;
+  e = launch_copy_bytes(a, src, n, st);
+  if (e != cudaSuccess) return e;
+  g_reads.push_back({dst, a, n});
+  return cudaSuccess;
+}
+
+cudaError_t sync_stream(cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  for (auto& r : g_reads) memcpy(r.dst, r.src, r.n);
+  g_reads.clear();
+  return cudaSuccess;
+}
+
 // ---- a second stream per host thread ---------------------------------------------
 // The groups of a partitioned join alternate between the caller's stream and
 // this one, so one group's sort passes fill the tails of the other's launches.
@@ -486,15 +570,15 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   hj[1].tile0 = tiles_r;
   TJ_CUDA(cudaMemsetAsync(ctl.p + o_misc, 0, 32 * sizeof(int64_t), st));
   TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, 2 * sizeof(KeyStats), st));
-  TJ_CUDA(cudaMemcpyAsync(d_jobs, hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_jobs, hj, sizeof(hj), st));
   Tracer tr(st);
   const double w = (double)sizeof(K);
   tr.begin("stats", w * (nr + ns));
   TJ_CUDA(launch_stats<K>(d_jobs, 2, tiles_r + tiles_s, d_stats, st));
   tr.end();
   KeyStats hs[2];
-  TJ_CUDA(cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(hs, d_stats, sizeof(hs), st));
+  TJ_CUDA(sync_stream(st));
 
   const K min_r = key_of<K>(hs[0].min_u), max_r = key_of<K>(~hs[0].max_u);
   const K min_s = key_of<K>(hs[1].min_u), max_s = key_of<K>(~hs[1].max_u);
@@ -573,7 +657,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
                     &res_rv);
     set_job_buffers(hj[1], ks, is, big.at<K>(o_s[0]), big.at<K>(o_s[1]), sb_k, sb_v, &res_sk,
                     &res_sv);
-    TJ_CUDA(cudaMemcpyAsync(d_jobs, hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+    TJ_CUDA(put_small(d_jobs, hj, sizeof(hj), st));
     TJ_CUDA(cudaMemsetAsync(hj[0].hist, 0, 2 * kMaxPasses * kMaxBins * sizeof(uint32_t), st));
     tr.begin("histogram", w * (nr + ns));
     TJ_CUDA(launch_histogram<K>(d_jobs, 2, tiles_r + tiles_s, st));
@@ -599,7 +683,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   jj.tile0 = 0;
   JTile<K>* d_tiles = big.at<JTile<K>>(o_tiles);
   uint64_t* d_jlb = big.at<uint64_t>(o_jlb);
-  TJ_CUDA(cudaMemcpyAsync(d_jj, &jj, sizeof(jj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_jj, &jj, sizeof(jj), st));
   TJ_CUDA(launch_tile_ranges<K>(d_jj, 1, jtiles, d_tiles, st));
   TJ_CUDA(cudaMemsetAsync(d_jlb, 0, jtiles * sizeof(uint64_t), st));
   tr.begin("join", 2.0 * w * (nr + ns));
@@ -608,9 +692,9 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   tr.end();
   int64_t h_misc[2] = {0, 0};
   int h_err = 0;
-  TJ_CUDA(cudaMemcpyAsync(&h_misc[0], d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&h_misc[0], d_total, sizeof(int64_t), st));
+  TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
+  TJ_CUDA(sync_stream(st));
   if (h_misc[0] <= cap) tr.add_bytes("join", 2.0 * w * (double)h_misc[0]);
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
@@ -709,8 +793,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       for (int i = 0; i < 32; ++i) th[33 + i] = uni(1.0f);          // b1
       for (int i = 0; i < 1024; ++i) th[65 + i] = uni(0.433f);      // W2
       for (int i = 0; i < 32; ++i) th[1121 + i] = uni(0.433f);      // w3
-      TJ_CUDA(cudaMemcpyAsync(sb.at<float>(o_th), th.data(), th.size() * 4,
-                              cudaMemcpyHostToDevice, st));
+      TJ_CUDA(put_small(sb.at<float>(o_th), th.data(), th.size() * 4, st));
       tr.begin("mlp_train", 0.0);
       TJ_CUDA(launch_mlp_train<K>(sb.at<K>(o_k), m, sb.at<float>(o_th), o.mlp_steps, o.mlp_lr,
                                   o.seed, st));
@@ -720,8 +803,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
                                        sb.at<K>(o_k), m, sb.at<K>(o_b), st));
       tr.end();
     }
-    TJ_CUDA(cudaMemcpyAsync(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K),
-                            cudaMemcpyDeviceToHost, st));
+    TJ_CUDA(get_small(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K), st));
     // radix judge on the (sorted) sample: balance of equal-width ranges of the
     // same count, from bucket edges found by binary search on the device
     {
@@ -733,9 +815,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       TJ_CUDA(launch_sorted_bucket_edges<K>(sb.at<K>(o_k), m, lo_bits<K>(lo), sh, nb,
                                             sb.at<int64_t>(o_edges), st));
       std::vector<int64_t> edges((size_t)nb + 1);
-      TJ_CUDA(cudaMemcpyAsync(edges.data(), sb.at<int64_t>(o_edges), edges.size() * 8,
-                              cudaMemcpyDeviceToHost, st));
-      TJ_CUDA(cudaStreamSynchronize(st));
+      TJ_CUDA(get_small(edges.data(), sb.at<int64_t>(o_edges), edges.size() * 8, st));
+      TJ_CUDA(sync_stream(st));
       int64_t mx = 0;
       for (int d = 0; d < nb; ++d)
         mx = std::max(mx, (d + 1 < nb ? edges[(size_t)d + 1] : m) - edges[(size_t)d]);
@@ -747,15 +828,14 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     if (!o.exact_route && cuts.size() <= 255) {
       std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
       std::copy(cuts.begin(), cuts.end(), hc.begin());
-      TJ_CUDA(cudaMemcpyAsync(sb.at<K>(o_scuts), hc.data(), kMaxCuts * sizeof(K),
-                              cudaMemcpyHostToDevice, st));
+      TJ_CUDA(put_small(sb.at<K>(o_scuts), hc.data(), kMaxCuts * sizeof(K), st));
       TJ_CUDA(cudaMemsetAsync(sb.at<uint32_t>(o_scnt), 0, 2 * kMaxBins * sizeof(uint32_t), st));
       TJ_CUDA(launch_sample_route_counts<K>(sb.at<K>(o_k), sb.at<K>(o_v), m, m_r, sb.at<K>(o_scuts),
                                             (int)cuts.size(), sb.at<uint32_t>(o_scnt), st));
       sample_cnt.assign(2 * (size_t)kMaxBins, 0u);
-      TJ_CUDA(cudaMemcpyAsync(sample_cnt.data(), sb.at<uint32_t>(o_scnt),
-                              sample_cnt.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-      TJ_CUDA(cudaStreamSynchronize(st));
+      TJ_CUDA(get_small(sample_cnt.data(), sb.at<uint32_t>(o_scnt),
+                              sample_cnt.size() * sizeof(uint32_t), st));
+      TJ_CUDA(sync_stream(st));
       sample_m[0] = m_r;
       sample_m[1] = m_s;
     }
@@ -914,10 +994,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   uint32_t* d_counters = stg.at<uint32_t>(o_misc + 16);
   std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
   std::copy(cuts.begin(), cuts.end(), hc.begin());
-  TJ_CUDA(cudaMemcpyAsync(stg.at<K>(o_cuts), hc.data(), kMaxCuts * sizeof(K),
-                          cudaMemcpyHostToDevice, st));
-  TJ_CUDA(cudaMemcpyAsync(stg.at<uint16_t>(o_tab), tab.data(), tab.size() * sizeof(uint16_t),
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(stg.at<K>(o_cuts), hc.data(), kMaxCuts * sizeof(K), st));
+  TJ_CUDA(put_small(stg.at<uint16_t>(o_tab), tab.data(), tab.size() * sizeof(uint16_t), st));
   // histogram jobs (global tile numbering) then per-launch route jobs (tile0
   // rebased to their launch); the route jobs' hist slots receive the bases
   std::vector<RadixJob<K>> hj((size_t)nch * 2);
@@ -964,8 +1042,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
   RadixJob<K>* d_rj = stg.at<RadixJob<K>>(o_jobs);
   TJ_CUDA(cudaMemsetAsync(stg.p + o_misc, 0, 32 * sizeof(int64_t), st));
-  TJ_CUDA(cudaMemcpyAsync(d_rj, hj.data(), hj.size() * sizeof(RadixJob<K>),
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_rj, hj.data(), hj.size() * sizeof(RadixJob<K>), st));
   std::vector<int64_t> pcount(2 * (size_t)nparts, 0);
   std::vector<uint32_t> hcount((size_t)nch * kMaxBins, 0u);
   std::vector<uint32_t> rend(2 * (size_t)kMaxBins, 0u), rfin(2 * (size_t)kMaxBins, 0u);
@@ -974,9 +1051,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     tr.begin("histogram", w * (nr + ns));
     TJ_CUDA(launch_histogram<K>(d_rj, nch, tiles_all, st));
     tr.end();
-    TJ_CUDA(cudaMemcpyAsync(hcount.data(), stg.at<uint32_t>(o_hist), hcount.size() * 4,
-                            cudaMemcpyDeviceToHost, st));
-    TJ_CUDA(cudaStreamSynchronize(st));
+    TJ_CUDA(get_small(hcount.data(), stg.at<uint32_t>(o_hist), hcount.size() * 4, st));
+    TJ_CUDA(sync_stream(st));
     // partition sizes and every chunk's base per partition (partition-major,
     // chunks in row order: the route is stable)
     for (int c = 0; c < nch; ++c)
@@ -1013,13 +1089,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         for (int p2 = 0; p2 < nparts; ++p2)
           hcount[(size_t)c * kMaxBins + p2] =
               (uint32_t)rstart[(size_t)chunks[(size_t)c].side * nparts + p2];
-    TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_rend), rend.data(), rend.size() * 4,
-                            cudaMemcpyHostToDevice, st));
-    TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_fin), rfin.data(), rfin.size() * 4,
-                            cudaMemcpyHostToDevice, st));
+    TJ_CUDA(put_small(stg.at<uint32_t>(o_rend), rend.data(), rend.size() * 4, st));
+    TJ_CUDA(put_small(stg.at<uint32_t>(o_fin), rfin.data(), rfin.size() * 4, st));
   }
-  TJ_CUDA(cudaMemcpyAsync(stg.at<uint32_t>(o_hist), hcount.data(), hcount.size() * 4,
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(stg.at<uint32_t>(o_hist), hcount.data(), hcount.size() * 4, st));
 
   // ---- 3. the route pass (look-back words in a block of their own) ----
   // Memory: the routed copies (staging, reported apart) | route control (cuts,
@@ -1035,8 +1108,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   TJ_CUDA(rlb.alloc((size_t)std::max<int64_t>(lb_max, 256), st));
   for (int c = 0; c < nch; ++c)
     hj[(size_t)nch + c].lookback = rlb.at<uint32_t>(0) + route_lbw[(size_t)c];
-  TJ_CUDA(cudaMemcpyAsync(d_rj + nch, hj.data() + nch, (size_t)nch * sizeof(RadixJob<K>),
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_rj + nch, hj.data() + nch, (size_t)nch * sizeof(RadixJob<K>), st));
   for (auto& g : cgroups) {
     int64_t t = 0;
     for (int c = g.first; c < g.second; ++c) t += ceil_div(chunks[(size_t)c].n, rtile);
@@ -1059,10 +1131,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
   if (est) {  // exact batch sizes
     int h_err = 0;
-    TJ_CUDA(cudaMemcpyAsync(rfin.data(), stg.at<uint32_t>(o_fin), rfin.size() * 4,
-                            cudaMemcpyDeviceToHost, st));
-    TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TJ_CUDA(cudaStreamSynchronize(st));
+    TJ_CUDA(get_small(rfin.data(), stg.at<uint32_t>(o_fin), rfin.size() * 4, st));
+    TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
+    TJ_CUDA(sync_stream(st));
     if (h_err == TJ_ERR_CAPACITY) return kRouteAgain;
     if (h_err) return set_err((tj_status)h_err, "device reported %d during the route pass", h_err);
     for (int side = 0; side < 2; ++side)
@@ -1311,7 +1382,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     memcpy(h + t_rj, all_rj.data(), rj_used);
     memcpy(h + t_rjh, all_rjh.data(), rj_used);
     memcpy(h + t_jj, all_jj.data(), all_jj.size() * sizeof(JoinJob<K>));
-    TJ_CUDA(cudaMemcpyAsync(tbl.p, h, t_hist, cudaMemcpyHostToDevice, st));
+    TJ_CUDA(put_small(tbl.p, h, t_hist, st));
     TJ_CUDA(cudaEventRecord(pinned_event(), st));  // the staging buffer is busy until here
     TJ_CUDA(cudaMemsetAsync(tbl.p + t_hist, 0, tbl_bytes - t_hist, st));
   }
@@ -1385,10 +1456,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   stats.radix_passes = maxp;
   int64_t h_total = 0;
   int h_err = 0;
-  TJ_CUDA(cudaMemcpyAsync(&h_total, d_gbase + plans.size(), sizeof(int64_t),
-                          cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&h_total, d_gbase + plans.size(), sizeof(int64_t), st));
+  TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
+  TJ_CUDA(sync_stream(st));
   if (h_total <= cap) tr.add_bytes(lanes > 1 ? "group/lanes" : "join", 2.0 * w * (double)h_total);
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
@@ -1429,15 +1499,15 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   hj.n = n;
   TJ_CUDA(cudaMemsetAsync(ctl.p + o_misc, 0, 32 * sizeof(int64_t), st));
   TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, sizeof(KeyStats), st));
-  TJ_CUDA(cudaMemcpyAsync(d_jobs, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_jobs, &hj, sizeof(hj), st));
   Tracer tr(st);
   const double w = (double)sizeof(K);
   tr.begin("stats", w * n);
   TJ_CUDA(launch_stats<K>(d_jobs, 1, tiles, d_stats, st));
   tr.end();
   KeyStats hs;
-  TJ_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&hs, d_stats, sizeof(hs), st));
+  TJ_CUDA(sync_stream(st));
   tr.flush();
   Tracer tr2(st);
   const K lo = key_of<K>(hs.min_u), hi = key_of<K>(~hs.max_u);
@@ -1469,7 +1539,7 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   const K* rv;
   // even number of passes: B, keys, B, keys, ... ends in the caller's arrays
   set_job_buffers(hj, keys, ids, big.at<K>(o_bk), big.at<K>(o_bv), keys, ids, &rk, &rv);
-  TJ_CUDA(cudaMemcpyAsync(d_jobs, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_jobs, &hj, sizeof(hj), st));
   TJ_CUDA(cudaMemsetAsync(hj.hist, 0, kMaxPasses * kMaxBins * sizeof(uint32_t), st));
   tr2.begin("histogram", w * n);
   TJ_CUDA(launch_histogram<K>(d_jobs, 1, tiles, st));
@@ -1483,8 +1553,8 @@ tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
     tr2.end();
   }
   int h_err = 0;
-  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
+  TJ_CUDA(sync_stream(st));
   tr2.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
   if (rk != keys) return set_err(TJ_ERR_INTERNAL, "odd pass count in place");
@@ -1535,17 +1605,15 @@ tj_status sort_multi_impl(K* const* cols, int ncols, K* ids, int64_t n, int path
     hj[(size_t)col].n = n;
     hj[(size_t)col].tile0 = col * tiles;
   }
-  TJ_CUDA(cudaMemcpyAsync(blk.at<RadixJob<K>>(o_jobs), hj.data(), hj.size() * sizeof(RadixJob<K>),
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(blk.at<RadixJob<K>>(o_jobs), hj.data(), hj.size() * sizeof(RadixJob<K>), st));
   TJ_CUDA(cudaMemsetAsync(blk.at<KeyStats>(o_stats), 0xFF, (size_t)ncols * sizeof(KeyStats), st));
   tr.begin("stats", w * n * ncols);
   TJ_CUDA(launch_stats<K>(blk.at<RadixJob<K>>(o_jobs), ncols, tiles * ncols,
                           blk.at<KeyStats>(o_stats), st));
   tr.end();
   std::vector<KeyStats> hs((size_t)ncols);
-  TJ_CUDA(cudaMemcpyAsync(hs.data(), blk.at<KeyStats>(o_stats), hs.size() * sizeof(KeyStats),
-                          cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(hs.data(), blk.at<KeyStats>(o_stats), hs.size() * sizeof(KeyStats), st));
+  TJ_CUDA(sync_stream(st));
   tr.flush();
   PackArgs<K> pa;
   memset(&pa, 0, sizeof(pa));
@@ -1603,7 +1671,7 @@ tj_status sort_multi_impl(K* const* cols, int ncols, K* ids, int64_t n, int path
     }
     stats.groups = ncols;
   }
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(sync_stream(st));
   tr.flush();
   g_stats = stats;
   return TJ_OK;
@@ -1657,13 +1725,11 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   JoinJob<K>* d_jj = ctl.at<JoinJob<K>>(o_jj);
   TJ_CUDA(cudaMemsetAsync(ctl.p + o_misc, 0, 32 * sizeof(int64_t), st));
   TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, (size_t)(2 * nj) * sizeof(KeyStats), st));
-  TJ_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>),
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>), st));
   TJ_CUDA(launch_stats<K>(d_jobs, (int)(2 * nj), tiles, d_stats, st, tile));
   std::vector<KeyStats> hs((size_t)(2 * nj));
-  TJ_CUDA(cudaMemcpyAsync(hs.data(), d_stats, hs.size() * sizeof(KeyStats),
-                          cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(hs.data(), d_stats, hs.size() * sizeof(KeyStats), st));
+  TJ_CUDA(sync_stream(st));
 
   // per-pair ranges; pairs that cannot match are dropped from the batch
   std::vector<uint64_t> plo((size_t)nj, 0), prange((size_t)nj, 0);
@@ -1760,10 +1826,8 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
     y.tile0 = jt;
     jt += ceil_div(y.ns, kJTile);
   }
-  TJ_CUDA(cudaMemcpyAsync(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>),
-                          cudaMemcpyHostToDevice, st));
-  TJ_CUDA(cudaMemcpyAsync(d_jj, hjj.data(), hjj.size() * sizeof(JoinJob<K>),
-                          cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_jobs, hj.data(), hj.size() * sizeof(RadixJob<K>), st));
+  TJ_CUDA(put_small(d_jj, hjj.data(), hjj.size() * sizeof(JoinJob<K>), st));
 
   // the batch's device work, captured once as a graph (plain launches on the
   // legacy stream, which cannot be captured)
@@ -1804,9 +1868,9 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
   int64_t h_total = 0;
   int h_err = 0;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&h_total, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    e = get_small(&h_total, d_total, sizeof(int64_t), st);
+  if (e == cudaSuccess) e = get_small(&h_err, d_err, sizeof(int), st);
+  if (e == cudaSuccess) e = sync_stream(st);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess)
@@ -1976,11 +2040,11 @@ tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   hj.n = n;
   TJ_CUDA(cudaMemsetAsync(tail + 2048, 0, 2048, st));  // error word and tile counters
   TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, sizeof(KeyStats), st));
-  TJ_CUDA(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_job, &hj, sizeof(hj), st));
   TJ_CUDA(launch_stats<K>(d_job, 1, tiles, d_stats, st));
   KeyStats hs;
-  TJ_CUDA(cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&hs, d_stats, sizeof(hs), st));
+  TJ_CUDA(sync_stream(st));
   const K lo = key_of<K>(hs.min_u), hi = key_of<K>(~hs.max_u);
   const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), /*even=*/true,
                               max_digit_bits<K>());
@@ -1993,7 +2057,7 @@ tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   const K* rk;
   const K* rv;
   set_job_buffers(hj, keys, ids, bk, bv, keys, ids, &rk, &rv);
-  TJ_CUDA(cudaMemcpyAsync(d_job, &hj, sizeof(hj), cudaMemcpyHostToDevice, st));
+  TJ_CUDA(put_small(d_job, &hj, sizeof(hj), st));
   // the array keeps the last call's contents: clear what must start at zero
   TJ_CUDA(cudaMemsetAsync(hist, 0, (size_t)kMaxPasses * kMaxBins * sizeof(uint32_t), st));
   TJ_CUDA(launch_histogram<K>(d_job, 1, tiles, st));
@@ -2004,8 +2068,8 @@ tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
                                st));
   }
   int h_err = 0;
-  TJ_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
+  TJ_CUDA(sync_stream(st));
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
   if (rk != keys) return set_err(TJ_ERR_INTERNAL, "odd pass count in place");
   return TJ_OK;
@@ -2032,6 +2096,7 @@ tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, i
                            size_t mem_budget_bytes, const tj_join_opts* opts, void* out_pairs,
                            int64_t out_capacity, int64_t* out_count, void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (!out_count) return set_err(TJ_ERR_INVALID, "out_count is NULL");
   *out_count = 0;
   if (n_r < 0 || n_s < 0 || out_capacity < 0)
@@ -2061,6 +2126,7 @@ tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, i
 
 tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (n < 0) return set_err(TJ_ERR_INVALID, "negative size");
   if (n > kNoAllocMaxRows)
     return set_err(TJ_ERR_INVALID,
@@ -2077,6 +2143,7 @@ tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* s
 tj_status tj_sort_multi(tj_dtype dt, void* const* cols, int32_t n_cols, void* ids, int64_t n,
                         int32_t path, void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (n < 0 || n_cols < 0) return set_err(TJ_ERR_INVALID, "negative size");
   if (path < 0 || path > 2) return set_err(TJ_ERR_INVALID, "path %d (0, 1 or 2)", path);
   if (n >= kMaxRows) return set_err(TJ_ERR_INVALID, "n >= 2^30 rows is not supported");
@@ -2095,6 +2162,7 @@ tj_status tj_sort_multi(tj_dtype dt, void* const* cols, int32_t n_cols, void* id
 
 tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (n < 0) return set_err(TJ_ERR_INVALID, "negative size");
   if (n >= kMaxRows) return set_err(TJ_ERR_INVALID, "n >= 2^30 rows is not supported");
   if (bad_ptr(keys, n) || bad_ptr(ids, n))
@@ -2108,6 +2176,7 @@ tj_status tj_sort(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
 tj_status tj_gather_pairs(tj_dtype id_dt, const void* pairs, int64_t n, int64_t n_r,
                           int64_t n_s, const tj_column* cols, int32_t n_cols, void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (n < 0 || n_r < 0 || n_s < 0 || n_cols < 0) return set_err(TJ_ERR_INVALID, "negative size");
   if (id_dt != TJ_I32 && id_dt != TJ_I64) return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)id_dt);
   if (n_cols > 0 && !cols) return set_err(TJ_ERR_INVALID, "cols is NULL");
@@ -2156,8 +2225,8 @@ tj_status tj_gather_pairs(tj_dtype id_dt, const void* pairs, int64_t n, int64_t 
     tr.end();
   }
   int h_err = 0;
-  TJ_CUDA(cudaMemcpyAsync(&h_err, eb.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(get_small(&h_err, eb.p, sizeof(int), st));
+  TJ_CUDA(sync_stream(st));
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "an id of `pairs` is out of range");
   return TJ_OK;
@@ -2169,6 +2238,7 @@ static tj_status batch_entry(tj_dtype dt, int64_t n_jobs, const int64_t* r_off,
                              int64_t out_capacity, int64_t* out_off, int64_t* out_count,
                              void* stream, bool tune) {
   g_err[0] = 0;
+  arena_reset();
   if (!out_count) return set_err(TJ_ERR_INVALID, "out_count is NULL");
   *out_count = 0;
   if (n_jobs < 0 || out_capacity < 0) return set_err(TJ_ERR_INVALID, "negative size");
@@ -2221,26 +2291,28 @@ tj_status tj_autotune_batch(tj_dtype dt, int64_t n_jobs, const int64_t* r_off,
 tj_status tj_mlp_grad(const float* theta, const float* x, const float* y, int n, float* grad,
                       void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (n < 1 || n > 256) return set_err(TJ_ERR_INVALID, "batch must have 1..256 rows");
   if (!theta || !x || !y || !grad) return set_err(TJ_ERR_INVALID, "null pointer");
   tj_status s = ensure_device();
   if (s != TJ_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   TJ_CUDA(launch_mlp_grad(theta, x, y, n, grad, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(sync_stream(st));
   return TJ_OK;
 }
 
 tj_status tj_mlp_adam(float* theta, float* m, float* v, const float* grad, int n, int t,
                       float lr, void* stream) {
   g_err[0] = 0;
+  arena_reset();
   if (n < 0 || t < 1) return set_err(TJ_ERR_INVALID, "bad size or step");
   if (n > 0 && (!theta || !m || !v || !grad)) return set_err(TJ_ERR_INVALID, "null pointer");
   tj_status s = ensure_device();
   if (s != TJ_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   if (n > 0) TJ_CUDA(launch_adam(theta, m, v, grad, n, t, lr, st));
-  TJ_CUDA(cudaStreamSynchronize(st));
+  TJ_CUDA(sync_stream(st));
   return TJ_OK;
 }
 

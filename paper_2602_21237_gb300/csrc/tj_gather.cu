@@ -208,6 +208,33 @@ template cudaError_t launch_pack<int32_t>(const PackArgs<int32_t>&, int32_t*, in
                                           cudaStream_t);
 template cudaError_t launch_pack<int64_t>(const PackArgs<int64_t>&, int64_t*, int64_t, bool, int,
                                           cudaStream_t);
+// Small control transfers between device memory and pinned host memory that
+// the device maps (tables going in, counts and statistics coming out), done by
+// a kernel instead of a copy engine: a transfer queued on an engine behind a
+// caller's bulk copy in the same direction would wait for all of it.
+__global__ void k_copy_bytes(unsigned char* __restrict__ dst, const unsigned char* __restrict__ src,
+                             size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15u) == 0) {
+    const size_t n16 = n / 16;
+    for (size_t i = t; i < n16; i += stride)
+      reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+    for (size_t i = n16 * 16 + t; i < n; i += stride) dst[i] = src[i];
+  } else {
+    for (size_t i = t; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_copy_bytes(void* dst, const void* src, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const size_t per = (size_t)kGatherThreads * 16;
+  const unsigned grid = (unsigned)std::min<size_t>((n + per - 1) / per, 1024);
+  k_copy_bytes<<<grid, kGatherThreads, 0, st>>>(static_cast<unsigned char*>(dst),
+                                                static_cast<const unsigned char*>(src), n);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_gather_pairs<int32_t>(const int32_t*, int64_t, int64_t, int64_t,
                                                   const GatherArgs&, int*, int, cudaStream_t);
 template cudaError_t launch_gather_pairs<int64_t>(const int64_t*, int64_t, int64_t, int64_t,

@@ -177,6 +177,8 @@ cudaError_t launch_gather_idx(const K* src, const K* idx, K* dst, int64_t n, int
                               cudaStream_t st);
 template <typename K>
 cudaError_t launch_iota(K* out, int64_t n, int sms, cudaStream_t st);
+// dst[0, n) = src[0, n) by a kernel (one side may be pinned, mapped host memory)
+cudaError_t launch_copy_bytes(void* dst, const void* src, size_t n, cudaStream_t st);
 // key columns folded into one key (pack) and back (unpack)
 template <typename K>
 struct PackArgs {
