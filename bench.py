@@ -387,7 +387,10 @@ def run_tj(args, ws, rank, local):
         ms = sum(d["ms"] for d in solo)
         n_l = sum(d["launches"] for d in solo)
         ach = by / (ms / 1e3) / 1e9
-        ratio = roofline_traffic("onesweep")
+        # DRAM bytes per algorithmic byte of each kind of launch (ncu)
+        ratios = {k: roofline_traffic(k) for k in ("route", "onesweep") if k in trace}
+        traffic = (sum(trace[k]["bytes"] * r for k, r in ratios.items()) / n_l
+                   if all(r is not None for r in ratios.values()) else None)
         per_launch_alg = by / n_l
         step_bytes = sum(v["bytes"] for v in trace.values()) / len(step_ms)
         step_ach = step_bytes / (ms_step / 1e3) / 1e9
@@ -396,7 +399,7 @@ def run_tj(args, ws, rank, local):
                           "router's sample sorts)",
                 "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_kind": f"{peak_kind} hbm_gbs (copy, burst)",
-                "traffic": (per_launch_alg * ratio) if ratio else None,
+                "traffic": traffic,
                 "alg_bytes_per_launch": per_launch_alg, "launches": n_l,
                 "share_of_traced_ms": ms / sum(v["ms"] for v in trace.values()),
                 "step": {"alg_bytes": step_bytes, "achieved": step_ach,

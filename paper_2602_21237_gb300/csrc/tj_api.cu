@@ -918,7 +918,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       route_shift = us;
     }
   }
-  const int64_t rtile = kTile;  // route pass tiles
+  const int64_t rtile = kTileRoute;  // route pass tiles
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
                                   : INT64_MAX;
@@ -1118,7 +1118,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
     tr.begin("route", 4.0 * w * rows);
     TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
-                               d_counters + kMaxPasses, d_err, st, nullptr, kItems, est));
+                               d_counters + kMaxPasses, d_err, st, nullptr, kItemsRoute, est));
     tr.end();
     if (est) {  // where this chunk ended: the next chunk's bases, or the side's end
       const int c = g.first, side = chunks[(size_t)c].side;

@@ -34,6 +34,13 @@ constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (3072)
 constexpr int kItemsWide = 10;
 constexpr int kWideBits = 7;
 constexpr int kTileWide = kSortThreads * kItemsWide;
+// rows per thread of the route pass (its batch-index tables and per-slot
+// digits take shared memory of their own)
+#ifndef TJ_ROUTE_ITEMS
+#define TJ_ROUTE_ITEMS 9
+#endif
+constexpr int kItemsRoute = TJ_ROUTE_ITEMS;
+constexpr int kTileRoute = kSortThreads * kItemsRoute;
 constexpr int kMaxDigitBits = 10;           // widest radix digit
 constexpr int kMaxBins = 1 << kMaxDigitBits;
 constexpr int kMaxPasses = 8;               // 64-bit keys at 8 bits per pass

@@ -462,7 +462,7 @@ template <int NB, int ITEMS>
 __device__ __forceinline__ void rank_items(uint32_t (&dr)[ITEMS], int nv, uint32_t* wh) {
   const int lane = threadIdx.x & 31;
   const uint32_t ltm = lanemask_lt();
-  constexpr int kHalf = ITEMS % 4 == 0 ? 4 : (ITEMS % 2 == 0 ? 2 : 1);
+  constexpr int kHalf = ITEMS % 4 == 0 ? 4 : (ITEMS % 3 == 0 ? 3 : (ITEMS % 2 == 0 ? 2 : 1));
 #pragma unroll
   for (int i0 = 0; i0 < ITEMS; i0 += kHalf) {
     uint32_t peers[kHalf];
@@ -687,16 +687,17 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     // batch regions sized in advance: a row past its region's end is dropped
     // and reported (the caller then routes again with exact sizes)
     bool over = false;
+#pragma unroll 4
     for (int q = tid; q < nvalid; q += kSortThreads) {
       const int r = s_src[q];
       const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
       const long long g = s_gbase[d] + q;
-      if (g >= (long long)s_rend[d]) {
-        over = true;
-        continue;
+      const bool in = g < (long long)s_rend[d];
+      over |= !in;
+      if (in) {
+        dst_k[g] = s_keys[r];
+        dst_v[g] = s_vals[r];
       }
-      dst_k[g] = s_keys[r];
-      dst_v[g] = s_vals[r];
     }
     if (over) atomicCAS(err, 0, (int)TJ_ERR_CAPACITY);
     return;
@@ -788,6 +789,10 @@ cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t tot
     const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4, guard);
     k_onesweep<K, 4><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  } else if (items == kItemsRoute && kItemsRoute != kItems && kItemsRoute != kItemsWide) {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTileRoute, guard);
+    k_onesweep<K, kItemsRoute><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   } else if (items == kItemsWide) {
     const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTileWide, guard);
     k_onesweep<K, kItemsWide><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
@@ -809,6 +814,16 @@ cudaError_t radix_init_attributes() {
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTile, true));
   if (e != cudaSuccess) return e;
+  if (kItemsRoute != kItems && kItemsRoute != kItemsWide) {
+    e = cudaFuncSetAttribute(k_onesweep<int32_t, kItemsRoute>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTileRoute, true));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_onesweep<int64_t, kItemsRoute>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTileRoute, true));
+    if (e != cudaSuccess) return e;
+  }
   e = cudaFuncSetAttribute(k_onesweep<int32_t, kItemsWide>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTileWide, true));
