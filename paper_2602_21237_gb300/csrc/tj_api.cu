@@ -525,8 +525,8 @@ Opts make_opts(const tj_join_opts* o) {
 
 template <typename K>
 tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is,
-                         int64_t ns, K lo, K hi, size_t budget, const Opts& o, K* out,
-                         int64_t cap, int64_t* out_count, tj_stats& stats, Tracer& tr,
+                         int64_t ns, K lo, K hi, bool range_known, size_t budget, const Opts& o,
+                         K* out, int64_t cap, int64_t* out_count, tj_stats& stats, Tracer& tr,
                          cudaStream_t st);
 template <typename K>
 tj_status sort_impl(K* keys, K* ids, int64_t n, cudaStream_t st);
@@ -573,6 +573,35 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   TJ_CUDA(put_small(d_jobs, hj, sizeof(hj), st));
   Tracer tr(st);
   const double w = (double)sizeof(K);
+
+  // the partitioned path (again with exact batch sizes if a sampled region overflowed)
+  auto partitioned = [&](int router, K lo, K hi, bool range_known) -> tj_status {
+    stats.learned = router;
+    Opts po = opts;
+    po.router = router;
+    tj_status ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, range_known, budget, po,
+                                     out, cap, out_count, stats, tr, st);
+    if (ps == kRouteAgain) {
+      po.exact_route = true;
+      ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, range_known, budget, po, out, cap,
+                             out_count, stats, tr, st);
+      stats.route_regions = 3;
+    }
+    if (ps == TJ_OK || ps == TJ_ERR_CAPACITY) {
+      stats.out_count = *out_count;
+      g_stats = stats;
+    }
+    return ps;
+  };
+  // One sorted copy of both relations already exceeds the budget: the join is
+  // partitioned whatever the key range, and a learned router needs no key
+  // statistics first (its sample gives the range for routing, the route pass
+  // the exact one for the batches).
+  if ((opts.router == TJ_ROUTE_AUTO || opts.router == TJ_ROUTE_PLA ||
+       opts.router == TJ_ROUTE_MLP) &&
+      budget != 0 && (double)(nr + ns) * 2.0 * w > (double)budget)
+    return partitioned(opts.router == TJ_ROUTE_AUTO ? (int)TJ_ROUTE_PLA : opts.router, K(0),
+                       K(0), false);
   tr.begin("stats", w * (nr + ns));
   TJ_CUDA(launch_stats<K>(d_jobs, 2, tiles_r + tiles_s, d_stats, st));
   tr.end();
@@ -612,24 +641,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   int router = opts.router;
   if (router == TJ_ROUTE_AUTO)
     router = (budget == 0 || need <= budget) ? TJ_ROUTE_SINGLE : TJ_ROUTE_PLA;
-  if (router != TJ_ROUTE_SINGLE) {
-    stats.learned = router;
-    Opts po = opts;
-    po.router = router;
-    tj_status ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, budget, po, out, cap,
-                                     out_count, stats, tr, st);
-    if (ps == kRouteAgain) {
-      po.exact_route = true;
-      ps = part_join_impl<K>(kr, ir, nr, ks, is, ns, lo, hi, budget, po, out, cap, out_count,
-                             stats, tr, st);
-      stats.route_regions = 3;
-    }
-    if (ps == TJ_OK || ps == TJ_ERR_CAPACITY) {
-      stats.out_count = *out_count;
-      g_stats = stats;
-    }
-    return ps;
-  }
+  if (router != TJ_ROUTE_SINGLE) return partitioned(router, lo, hi, true);
   if (budget != 0 && need > budget)
     return set_err(TJ_ERR_BUDGET,
                    "join needs %zu bytes of scratch in one pass, budget is %zu", need, budget);
@@ -736,8 +748,8 @@ std::vector<K> make_cuts(const std::vector<K>& b) {
 
 template <typename K>
 tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is,
-                         int64_t ns, K lo, K hi, size_t budget, const Opts& o, K* out,
-                         int64_t cap, int64_t* out_count, tj_stats& stats, Tracer& tr,
+                         int64_t ns, K lo, K hi, bool range_known, size_t budget, const Opts& o,
+                         K* out, int64_t cap, int64_t* out_count, tj_stats& stats, Tracer& tr,
                          cudaStream_t st) {
   const double w = (double)sizeof(K);
   const int maxd = max_digit_bits<K>();
@@ -768,6 +780,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     tj_status ss = sort_impl<K>(sb.at<K>(o_k), sb.at<K>(o_v), m, st);
     g_stats = keep;
     if (ss != TJ_OK) return ss;
+    if (!range_known) {  // the sorted sample's ends stand for the range until the route
+      TJ_CUDA(get_small(&lo, sb.at<K>(o_k), sizeof(K), st));
+      TJ_CUDA(get_small(&hi, sb.at<K>(o_k) + (m - 1), sizeof(K), st));
+      TJ_CUDA(sync_stream(st));
+    }
     std::vector<K> bnd((size_t)(parts - 1));
     if (router == TJ_ROUTE_PLA) {
       // boundaries of the piecewise-linear CDF: knots t_{(G / parts) p}
@@ -840,6 +857,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       sample_m[1] = m_s;
     }
   } else {  // TJ_ROUTE_RADIX
+    if (!range_known) return set_err(TJ_ERR_INTERNAL, "equal-width batches need the key range");
     router = TJ_ROUTE_RADIX;
     const int b = bitlen(range_of<K>(lo, hi));
     int plog = 0;
@@ -987,6 +1005,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   const size_t o_fin = cc.add<uint32_t>(2 * (size_t)kMaxBins);   // where the route ended (est)
   const size_t o_jobs = cc.add<RadixJob<K>>((size_t)nch * 2);
   const size_t o_misc = cc.add<int64_t>(32);
+  // the key range from the first and the last batch (range not known): jobs, min / max
+  const size_t o_rjobs = cc.add<RadixJob<K>>(4), o_range = cc.add<KeyStats>(4);
   Block stg;
   TJ_CUDA(stg.alloc(cc.off, st));
   stats.staging_bytes = (int64_t)staging;
@@ -1042,6 +1062,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
   RadixJob<K>* d_rj = stg.at<RadixJob<K>>(o_jobs);
   TJ_CUDA(cudaMemsetAsync(stg.p + o_misc, 0, 32 * sizeof(int64_t), st));
+
   TJ_CUDA(put_small(d_rj, hj.data(), hj.size() * sizeof(RadixJob<K>), st));
   std::vector<int64_t> pcount(2 * (size_t)nparts, 0);
   std::vector<uint32_t> hcount((size_t)nch * kMaxBins, 0u);
@@ -1141,6 +1162,39 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         const size_t i = (size_t)side * nparts + p2;
         pcount[i] = (int64_t)rfin[(size_t)side * kMaxBins + p2] - rstart[i];
       }
+  }
+  if (!range_known) {
+    // the smallest key is in the first batch, the largest in the last: their
+    // rows on both sides (about 2 / nparts of the data) give the exact range
+    std::vector<RadixJob<K>> rj;
+    int64_t rtiles = 0;
+    for (int side = 0; side < 2; ++side)
+      for (int p2 : {0, nparts - 1}) {
+        const size_t i = (size_t)side * nparts + p2;
+        RadixJob<K> x;
+        memset(&x, 0, sizeof(x));
+        x.keys = (side ? stg.at<K>(o_sk) : stg.at<K>(o_rk)) + rstart[i];
+        x.n = pcount[i];
+        x.tile0 = rtiles;
+        rtiles += ceil_div(x.n, kTile);
+        rj.push_back(x);
+      }
+    TJ_CUDA(put_small(stg.at<RadixJob<K>>(o_rjobs), rj.data(), rj.size() * sizeof(RadixJob<K>), st));
+    TJ_CUDA(cudaMemsetAsync(stg.at<KeyStats>(o_range), 0xFF, 4 * sizeof(KeyStats), st));
+    tr.begin("stats", w * (double)rtiles * kTile);
+    TJ_CUDA(launch_stats<K>(stg.at<RadixJob<K>>(o_rjobs), 4, rtiles, stg.at<KeyStats>(o_range), st));
+    tr.end();
+    KeyStats hr[4];
+    TJ_CUDA(get_small(hr, stg.at<KeyStats>(o_range), sizeof(hr), st));
+    TJ_CUDA(sync_stream(st));
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (int i = 0; i < 4; ++i) {  // empty jobs keep 0xFF..: no effect on either
+      mn = std::min(mn, hr[i].min_u);
+      mx = std::max(mx, ~hr[i].max_u);
+    }
+    lo = key_of<K>(mn);
+    hi = key_of<K>(mx);
+    stats.key_bits = bitlen(range_of<K>(lo, hi));
   }
   {
     int64_t tot[2] = {0, 0}, maxrows = 0;
@@ -1367,6 +1421,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, its lane has %zu", gc.off,
                      lane_bytes);
     maxp = std::max(maxp, gp.P);
+    stats.digit_bits = std::max(stats.digit_bits, gp.maxbits);
     plans.push_back(gp);
   }
   // (tables were sized for every planned batch; batches found empty after a

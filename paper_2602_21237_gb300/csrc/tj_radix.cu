@@ -73,7 +73,8 @@ __device__ __forceinline__ uint32_t route_idx(K key, typename UnsignedOf<K>::typ
                                               const K* s_cuts, const uint16_t* s_tab, int steps,
                                               int ushift) {
   using U = typename UnsignedOf<K>::type;
-  const unsigned long long x = (unsigned long long)(U)((U)key - lo);
+  // keys below lo (a range estimated from a sample) take bucket 0
+  const unsigned long long x = key < (K)lo ? 0ull : (unsigned long long)(U)((U)key - lo);
   uint32_t b;
   if (ushift >= 0) {
     // uniform index; keys of the range give b < kRouteBuckets - 1, the clamp

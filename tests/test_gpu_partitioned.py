@@ -149,3 +149,30 @@ def test_two_lanes_many_to_many_on_a_side_stream():
     s.synchronize()
     assert st["groups"] > 1 and st["lanes"] == 2
     assert_pairs_equal(got, exp)
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
+def test_keys_outside_the_sample_range_without_key_statistics(dtype):
+    # one sorted copy exceeds the budget, so the join routes by the sample's
+    # range (no statistics pass); the extreme keys are never sampled and must
+    # still reach the first and the last batch, whose ranges come from the
+    # route pass itself
+    n, stride, seed = 200_000, 10, 5
+    off_r = (((seed * 0x9E3779B97F4A7C15) % (1 << 64)) >> 33) % stride
+    off_s = (((seed * 0xBF58476D1CE4E5B9) % (1 << 64)) >> 33) % stride
+    info = torch.iinfo(dtype)
+    g = torch.Generator().manual_seed(8)
+    kr = torch.randint(0, 1 << 20, (n,), generator=g, dtype=dtype)
+    ks = torch.randint(0, 1 << 20, (n,), generator=g, dtype=dtype)
+    far = (1 << 50) if dtype == torch.int64 else (1 << 29)
+    for side_k, off in ((kr, off_r), (ks, off_s)):
+        side_k[off + 1] = info.min
+        side_k[off + 2] = info.max
+        side_k[off + 3] = -far
+        side_k[off + 4] = far
+    ir = torch.arange(n, dtype=dtype)
+    is_ = torch.arange(n, dtype=dtype)
+    st = check(kr, ir, ks, is_, mem_budget_bytes=4 << 20, router="pla", partitions=64,
+               sample_stride=stride, seed=seed)
+    assert st["groups"] > 1 and st["scratch_peak"] <= 4 << 20
+    assert st["key_bits"] == (64 if dtype == torch.int64 else 32)
