@@ -936,7 +936,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       route_shift = us;
     }
   }
-  const int64_t rtile = kTileRoute;  // route pass tiles
+  // route pass tiles: kItemsRoute rows per thread for narrow batch indices
+  // (shared memory still fits three CTAs per SM), kItems otherwise (with 1024
+  // batches the 9-row tile measured 1.4x slower)
+  const int ritems = rbits <= kWideBits ? kItemsRoute : kItems;
+  const int64_t rtile = (int64_t)kSortThreads * ritems;
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
                                   : INT64_MAX;
@@ -1139,7 +1143,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
     tr.begin("route", 4.0 * w * rows);
     TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
-                               d_counters + kMaxPasses, d_err, st, nullptr, kItemsRoute, est));
+                               d_counters + kMaxPasses, d_err, st, nullptr, ritems, est));
     tr.end();
     if (est) {  // where this chunk ended: the next chunk's bases, or the side's end
       const int c = g.first, side = chunks[(size_t)c].side;

@@ -34,8 +34,8 @@ constexpr int kTile = kSortThreads * kItems;   // rows per onesweep tile (3072)
 constexpr int kItemsWide = 10;
 constexpr int kWideBits = 7;
 constexpr int kTileWide = kSortThreads * kItemsWide;
-// rows per thread of the route pass (its batch-index tables and per-slot
-// digits take shared memory of their own)
+// rows per thread of a route pass with at most kWideBits of batch index (its
+// batch-index tables and per-slot digits take shared memory of their own)
 #ifndef TJ_ROUTE_ITEMS
 #define TJ_ROUTE_ITEMS 9
 #endif
