@@ -6,10 +6,11 @@
 //   k_histogram  : the counts of every digit of every pass, in one read of the
 //                  keys (per-CTA shared-memory histograms merged into global).
 //   k_digit_scan : exclusive scan of each pass's digit counts (digit bases).
-//   k_onesweep   : one digit pass: a tile of 4096 rows is copied to shared
-//                  memory, publishes its digit counts to a decoupled
-//                  look-back chain, is ranked stably inside the CTA
-//                  (ballot-matched digit groups + per-warp counters), and is
+//   k_onesweep   : one digit pass: a tile of 1536 to 3840 rows is copied to
+//                  shared memory, publishes its digit counts to a decoupled
+//                  look-back chain, is ranked stably inside the CTA (digit
+//                  groups of a warp matched by a shared lane-mask table or by
+//                  ballots, + per-warp counters), and is
 //                  written out in tile-sorted order so that each digit's run
 //                  lands contiguously.
 //
@@ -498,13 +499,45 @@ __device__ __forceinline__ void rank_items(uint32_t (&dr)[ITEMS], int nv, uint32
   }
 }
 
+// Stable ranks as rank_items, with the lanes of each digit found through a
+// per-warp table of lane masks in shared memory (wm[bins], zero on entry and
+// on exit): every lane ORs its bit into its digit's word, the warp reads the
+// words back, and each digit group's highest lane clears its word.  One
+// shared atomic per row instead of one ballot per digit bit (3% faster passes
+// with 7-bit digits); the tables of all warps must fit the slot-index array.
+template <int ITEMS>
+__device__ __forceinline__ void rank_items_or(uint32_t (&dr)[ITEMS], int nv, uint32_t* wh,
+                                              uint32_t* wm) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t ltm = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const bool ok = i * 32 + lane < nv;
+    const uint32_t d = dr[i] & 0xFFFFu;
+    if (ok) atomicOr(&wm[d], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = ok ? wm[d] : (1u << lane);
+    __syncwarp();
+    const int leader = 31 - __clz(peers);
+    const uint32_t sh = (d & 1u) * 16u;
+    uint32_t base = 0u;
+    if (ok && leader == lane) {
+      wm[d] = 0u;
+      base = (atomicAdd(&wh[d >> 1], (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
+    }
+    __syncwarp();
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    dr[i] |= (base + __popc(peers & ltm)) << 16;
+  }
+}
+
 // One LSD pass over a tile of kSortThreads * ITEMS rows:
 //   1. copy the tile's keys and ids into shared memory (cp.async, 16-byte
 //      chunks) where they stay in input order;
 //   2. take every row's digit, count the tile's digits (shared atomics) and
 //      publish the counts to the look-back chain at once, so that successors
 //      rarely wait on this tile;
-//   3. rank stably inside each warp (rank_items; warp w owns rows
+//   3. rank stably inside each warp (rank_items_or / rank_items; warp w owns rows
 //      [w*32*ITEMS, (w+1)*32*ITEMS), item i covers 32 consecutive rows);
 //   4. record, for every tile-sorted slot, its input row (a 16-bit index)
 //      while the first look-back window is in flight, then finish the
@@ -571,6 +604,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
       for (int i = tid; i < bins; i += kSortThreads) s_rend[i] = J->route_end[i];
   }
   for (int i = tid; i < kSortWarps * hb + bins; i += kSortThreads) s_whist[i] = 0u;
+  // lane-mask tables of the ranking (digits of up to 7 bits), in the
+  // slot-index array, which is not live before step 4
+  const bool rank_or = nbits <= 7 && kSortWarps * bins * 4 <= TILE * 2;
+  if (rank_or)
+    for (int i = tid; i < kSortWarps * bins; i += kSortThreads)
+      reinterpret_cast<uint32_t*>(s_src)[i] = 0u;
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 
@@ -590,23 +629,27 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   for (int d = tid; d < bins; d += kSortThreads)
     st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | s_count[d]);
 
-  // 3. stable rank inside the warp (digit width fixed at compile time so that
-  //    the ballots of several items interleave)
+  // 3. stable rank inside the warp: lane-mask tables for digits of up to 7
+  //    bits, else ballots (digit width fixed at compile time so that the
+  //    ballots of several items interleave)
   {
     uint32_t* wh = s_whist + warp * hb;
     const int nv = nvalid - wbase;  // valid rows of this warp (may be <= 0)
-    switch (nbits) {
-      case 1: rank_items<1, ITEMS>(dr, nv, wh); break;
-      case 2: rank_items<2, ITEMS>(dr, nv, wh); break;
-      case 3: rank_items<3, ITEMS>(dr, nv, wh); break;
-      case 4: rank_items<4, ITEMS>(dr, nv, wh); break;
-      case 5: rank_items<5, ITEMS>(dr, nv, wh); break;
-      case 6: rank_items<6, ITEMS>(dr, nv, wh); break;
-      case 7: rank_items<7, ITEMS>(dr, nv, wh); break;
-      case 8: rank_items<8, ITEMS>(dr, nv, wh); break;
-      case 9: rank_items<9, ITEMS>(dr, nv, wh); break;
-      default: rank_items<10, ITEMS>(dr, nv, wh); break;
-    }
+    if (rank_or)
+      rank_items_or<ITEMS>(dr, nv, wh, reinterpret_cast<uint32_t*>(s_src) + warp * bins);
+    else
+      switch (nbits) {
+        case 1: rank_items<1, ITEMS>(dr, nv, wh); break;
+        case 2: rank_items<2, ITEMS>(dr, nv, wh); break;
+        case 3: rank_items<3, ITEMS>(dr, nv, wh); break;
+        case 4: rank_items<4, ITEMS>(dr, nv, wh); break;
+        case 5: rank_items<5, ITEMS>(dr, nv, wh); break;
+        case 6: rank_items<6, ITEMS>(dr, nv, wh); break;
+        case 7: rank_items<7, ITEMS>(dr, nv, wh); break;
+        case 8: rank_items<8, ITEMS>(dr, nv, wh); break;
+        case 9: rank_items<9, ITEMS>(dr, nv, wh); break;
+        default: rank_items<10, ITEMS>(dr, nv, wh); break;
+      }
   }
   __syncthreads();
 
