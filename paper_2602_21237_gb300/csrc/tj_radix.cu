@@ -500,12 +500,13 @@ __device__ __forceinline__ void rank_items(uint32_t (&dr)[ITEMS], int nv, uint32
 }
 
 // Stable ranks as rank_items, with the lanes of each digit found through a
-// per-warp table of lane masks in shared memory (wm[bins], zero on entry and
-// on exit): every lane ORs its bit into its digit's word, the warp reads the
-// words back, and each digit group's highest lane clears its word.  One
-// shared atomic per row instead of one ballot per digit bit (3% faster passes
-// with 7-bit digits); the tables of all warps must fit the slot-index array.
-template <int ITEMS>
+// per-warp table of lane masks in shared memory (wm[min(bins, 128)], zero on
+// entry and on exit): every lane ORs its bit into the word of its digit's low
+// 7 bits, the warp reads the words back, one ballot per higher digit bit (NH
+// of them) drops the lanes that differ above, and each group's highest lane
+// clears the word.  One shared atomic and NH ballots per row instead of one
+// ballot per digit bit; the tables of all warps must fit the slot-index array.
+template <int NH, int ITEMS>
 __device__ __forceinline__ void rank_items_or(uint32_t (&dr)[ITEMS], int nv, uint32_t* wh,
                                               uint32_t* wm) {
   const int lane = threadIdx.x & 31;
@@ -514,15 +515,22 @@ __device__ __forceinline__ void rank_items_or(uint32_t (&dr)[ITEMS], int nv, uin
   for (int i = 0; i < ITEMS; ++i) {
     const bool ok = i * 32 + lane < nv;
     const uint32_t d = dr[i] & 0xFFFFu;
-    if (ok) atomicOr(&wm[d], 1u << lane);
+    const uint32_t w = d & 127u;
+    if (ok) atomicOr(&wm[w], 1u << lane);
     __syncwarp();
-    const uint32_t peers = ok ? wm[d] : (1u << lane);
+    uint32_t peers = ok ? wm[w] : (1u << lane);
+#pragma unroll
+    for (int b = 7; b < 7 + NH; ++b) {
+      const int32_t m = (int32_t)(d << (31 - b)) >> 31;  // bit b: -1, else 0
+      const uint32_t x = __ballot_sync(0xFFFFFFFFu, m != 0);
+      peers &= ~(x ^ (uint32_t)m);
+    }
     __syncwarp();
     const int leader = 31 - __clz(peers);
     const uint32_t sh = (d & 1u) * 16u;
     uint32_t base = 0u;
     if (ok && leader == lane) {
-      wm[d] = 0u;
+      wm[w] = 0u;
       base = (atomicAdd(&wh[d >> 1], (uint32_t)__popc(peers) << sh) >> sh) & 0xFFFFu;
     }
     __syncwarp();
@@ -604,11 +612,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
       for (int i = tid; i < bins; i += kSortThreads) s_rend[i] = J->route_end[i];
   }
   for (int i = tid; i < kSortWarps * hb + bins; i += kSortThreads) s_whist[i] = 0u;
-  // lane-mask tables of the ranking (digits of up to 7 bits), in the
-  // slot-index array, which is not live before step 4
-  const bool rank_or = nbits <= 7 && kSortWarps * bins * 4 <= TILE * 2;
+  // lane-mask tables of the ranking (one word per value of the digit's low
+  // 7 bits), in the slot-index array, which is not live before step 4
+  const int mwords = bins < 128 ? bins : 128;
+  const bool rank_or = kSortWarps * mwords * 4 <= TILE * 2;
   if (rank_or)
-    for (int i = tid; i < kSortWarps * bins; i += kSortThreads)
+    for (int i = tid; i < kSortWarps * mwords; i += kSortThreads)
       reinterpret_cast<uint32_t*>(s_src)[i] = 0u;
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
@@ -629,14 +638,20 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   for (int d = tid; d < bins; d += kSortThreads)
     st_volatile_u32(lb_mine + d, (lt == 0 ? kFlagInc : kFlagAgg) | s_count[d]);
 
-  // 3. stable rank inside the warp: lane-mask tables for digits of up to 7
-  //    bits, else ballots (digit width fixed at compile time so that the
-  //    ballots of several items interleave)
+  // 3. stable rank inside the warp: lane-mask tables when they fit (tiles of
+  //    at least 3072 rows), else one ballot per digit bit (digit width fixed
+  //    at compile time so that the ballots of several items interleave)
   {
     uint32_t* wh = s_whist + warp * hb;
     const int nv = nvalid - wbase;  // valid rows of this warp (may be <= 0)
+    uint32_t* wm = reinterpret_cast<uint32_t*>(s_src) + warp * mwords;
     if (rank_or)
-      rank_items_or<ITEMS>(dr, nv, wh, reinterpret_cast<uint32_t*>(s_src) + warp * bins);
+      switch (nbits) {
+        case 8: rank_items_or<1, ITEMS>(dr, nv, wh, wm); break;
+        case 9: rank_items_or<2, ITEMS>(dr, nv, wh, wm); break;
+        case 10: rank_items_or<3, ITEMS>(dr, nv, wh, wm); break;
+        default: rank_items_or<0, ITEMS>(dr, nv, wh, wm); break;
+      }
     else
       switch (nbits) {
         case 1: rank_items<1, ITEMS>(dr, nv, wh); break;
