@@ -59,3 +59,23 @@ def test_sort_even_pass_count_lands_in_place():
     check(keys, ids)
     st = api.stats()
     assert st["radix_passes"] % 2 == 0 and st["key_bits"] == 27
+
+
+@pytest.mark.parametrize("dtype,bits,digit", [(torch.int32, 20, 10), (torch.int32, 18, 9),
+                                              (torch.int32, 16, 8), (torch.int64, 18, 9),
+                                              (torch.int64, 16, 8), (torch.int64, 14, 7)])
+def test_sort_digit_widths_with_colliding_digits(dtype, bits, digit):
+    """Every digit width of the warp ranking (7 bits through its lane-mask table,
+    wider ones with a ballot per higher bit), on keys from 40 values so that
+    many lanes of a warp share a digit, ids in reverse order so that a wrong
+    tie order shows."""
+    n = 50_000
+    g = torch.Generator().manual_seed(bits * 10 + digit)
+    vals = torch.randint(0, 1 << bits, (40,), generator=g, dtype=torch.int64)
+    vals[0] = (1 << bits) - 1
+    vals[1] = 0
+    keys = vals[torch.randint(0, 40, (n,), generator=g)].to(dtype)
+    ids = torch.arange(n, dtype=dtype).flip(0)
+    check(keys, ids)
+    st = api.stats()
+    assert st["key_bits"] == bits and st["digit_bits"] == digit
