@@ -419,11 +419,26 @@ constexpr int max_digit_bits() {
   return sizeof(K) == 4 ? 10 : 9;
 }
 
-Plan make_plan(uint64_t lo, uint64_t range, bool even, int max_digit, int force_passes = -1) {
+// Time of one pass per row by digit width, relative to a pass of at most 7
+// bits (measured on GB300 with 16-byte rows: 8 bits 1.17x, 9 bits 1.43x; a
+// wider digit splits each tile into more and shorter output runs).
+double pass_cost(int w) { return w <= 7 ? 1.0 : w == 8 ? 1.17 : w == 9 ? 1.43 : 1.7; }
+
+// A plan that need not be even, over at least kCostRows rows, takes one pass
+// more when the narrower digits make it cheaper (27 bits: 4 passes of 7 bits
+// instead of 3 of 9); below that size a pass's fixed cost decides.
+constexpr int64_t kCostRows = int64_t(1) << 22;
+
+Plan make_plan(uint64_t lo, uint64_t range, bool even, int max_digit, int force_passes = -1,
+               int64_t rows = 0) {
   Plan p;
   p.lo = lo;
   p.key_bits = bitlen(range);
   int P = force_passes >= 0 ? force_passes : (p.key_bits + max_digit - 1) / max_digit;
+  if (force_passes < 0 && !even && rows >= kCostRows && P > 0 && P < kMaxPasses) {
+    const int w0 = (p.key_bits + P - 1) / P, w1 = (p.key_bits + P) / (P + 1);
+    if ((P + 1) * pass_cost(w1) < P * pass_cost(w0)) ++P;
+  }
   if (even && (P & 1)) ++P;
   if (P > kMaxPasses) P = kMaxPasses;
   p.passes = P;
@@ -547,7 +562,7 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
 
   const int64_t tiles_r = ceil_div(nr, kTile), tiles_s = ceil_div(ns, kTile);
   Carve cc;
-  const size_t o_jobs = cc.add<RadixJob<K>>(2);
+  const size_t o_jobs = cc.add<RadixJob<K>>(4);  // R, S; again for the onesweep tile
   const size_t o_stats = cc.add<KeyStats>(2);
   const size_t o_misc = cc.add<int64_t>(32);  // err, counters, total
   const size_t o_jj = cc.add<JoinJob<K>>(1);
@@ -616,7 +631,8 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
     return TJ_OK;
   }
   const K lo = std::min(min_r, min_s), hi = std::max(max_r, max_s);
-  const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), false, max_digit_bits<K>());
+  const Plan plan =
+      make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), false, max_digit_bits<K>(), -1, nr + ns);
   stats.key_bits = plan.key_bits;
   stats.radix_passes = plan.passes;
   stats.digit_bits = plan.max_bits;
@@ -669,7 +685,16 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
                     &res_rv);
     set_job_buffers(hj[1], ks, is, big.at<K>(o_s[0]), big.at<K>(o_s[1]), sb_k, sb_v, &res_sk,
                     &res_sv);
-    TJ_CUDA(put_small(d_jobs, hj, sizeof(hj), st));
+    // the onesweep passes take the wider tile when every digit is narrow: a
+    // second pair of jobs numbers their tiles (no more tiles than the
+    // histogram's, so the look-back region holds them)
+    const int items = plan.max_bits <= kWideBits ? kItemsWide : kItems;
+    const int64_t otile = (int64_t)kSortThreads * items;
+    const int64_t otiles_r = ceil_div(nr, otile), otiles_s = ceil_div(ns, otile);
+    RadixJob<K> hw[4] = {hj[0], hj[1], hj[0], hj[1]};
+    hw[3].tile0 = otiles_r;
+    hw[3].lookback = hw[2].lookback + otiles_r * bins_max;
+    TJ_CUDA(put_small(d_jobs, hw, sizeof(hw), st));
     TJ_CUDA(cudaMemsetAsync(hj[0].hist, 0, 2 * kMaxPasses * kMaxBins * sizeof(uint32_t), st));
     tr.begin("histogram", w * (nr + ns));
     TJ_CUDA(launch_histogram<K>(d_jobs, 2, tiles_r + tiles_s, st));
@@ -677,10 +702,10 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
     TJ_CUDA(launch_digit_scan<K>(d_jobs, 2, P, st));
     for (int p = 0; p < P; ++p) {
       TJ_CUDA(cudaMemsetAsync(hj[0].lookback, 0,
-                              (size_t)(tiles_r + tiles_s) * bins_max * sizeof(uint32_t), st));
+                              (size_t)(otiles_r + otiles_s) * bins_max * sizeof(uint32_t), st));
       tr.begin("onesweep", 4.0 * w * (nr + ns));
-      TJ_CUDA(launch_onesweep<K>(d_jobs, 2, tiles_r + tiles_s, p, plan.max_bits, false, d_counters + p,
-                                 d_err, st));
+      TJ_CUDA(launch_onesweep<K>(d_jobs + 2, 2, otiles_r + otiles_s, p, plan.max_bits, false,
+                                 d_counters + p, d_err, st, nullptr, items));
       tr.end();
     }
   }
@@ -1232,7 +1257,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     if (q.nr == 0 || q.ns == 0) continue;
     q.lo = j == 0 ? lo : std::max(lo, cuts[(size_t)j - 1]);
     q.hi = j == ncuts ? hi : std::min(hi, (K)(cuts[(size_t)j] - 1));
-    q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd);
+    q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd, -1, q.nr + q.ns);
     // one sort buffer (the passes alternate between it and the batch's routed
     // copy), one look-back region per pass (a group keeps as many as its
     // deepest batch), join tile state (tile descriptors, chained words, tile map), the
