@@ -319,7 +319,7 @@ void tj_server_destroy(tj_server* s);
 /*
  * tj_join_batch after tuning (no counterpart in the paper): runs the batch
  * once per candidate (widest radix digit 6..10 bits, which sets the passes and
- * each pass's fan-out, and onesweep tiles of 2048 or 4096 rows), keeps the
+ * each pass's fan-out, and onesweep tiles of 1536 or 3072 rows), keeps the
  * fastest, caches it for batches of the same dtype, job count and mean size
  * (bucketed by powers of two; the file named by the environment variable
  * TJ_TUNE_CACHE, if set, keeps the cache across processes) and returns the

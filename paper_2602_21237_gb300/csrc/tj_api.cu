@@ -1972,7 +1972,7 @@ tj_status batch_impl(int64_t nj, const int64_t* r_off, const int64_t* s_off, con
 
 // ---- autotuner of the batched join --------------------------------------------------
 // Choices: the widest radix digit (and so the number of passes and the fan-out
-// of each pass) and the onesweep tile (2048 or 4096 rows: small jobs waste
+// of each pass) and the onesweep tile (1536 or 3072 rows: small jobs waste
 // less of a smaller last tile).  A choice is cached per (dtype, log2 jobs,
 // log2 mean rows per array); TJ_TUNE_CACHE names a file that persists it.
 struct TuneChoice {
