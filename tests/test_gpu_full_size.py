@@ -118,3 +118,39 @@ def test_lognormal_2e28_pla_under_1gb():
     pick = torch.randint(0, got.shape[0], (8,), generator=g).to(DEV)
     starts = k[pick].tolist()
     check_slices(kr, ir, ks, is_, got, k, starts, 1 << 10)
+
+
+def batch_as_one_join(r_off, s_off, kr, ks, got, out_off):
+    """A batch of joins seen as one join: each row's key becomes (job, key)
+    and each id a global row position, so check_properties applies."""
+    nj = len(r_off) - 1
+    dev = kr.device
+    jobs = torch.arange(nj, device=dev, dtype=torch.int64)
+    nr = torch.tensor(r_off, device=dev).diff()
+    ns = torch.tensor(s_off, device=dev).diff()
+    kr64 = (jobs.repeat_interleave(nr) << 32) | kr.to(torch.int64)
+    ks64 = (jobs.repeat_interleave(ns) << 32) | ks.to(torch.int64)
+    pj = jobs.repeat_interleave(out_off.diff())  # job of each pair
+    r0 = torch.tensor(r_off[:-1], device=dev)[pj]
+    s0 = torch.tensor(s_off[:-1], device=dev)[pj]
+    glob = torch.stack([r0 + got[:, 0].to(torch.int64), s0 + got[:, 1].to(torch.int64)], 1)
+    return kr64, ks64, glob
+
+
+def test_batched_4096_joins_full_size():
+    """The batched workload: 4096 int32 joins, |R| and |S| log-uniform in
+    [10^3, 10^6], keys uniform over [0, 2|R|), one batched call.  The whole
+    batch is checked by the join properties (keys made (job, key)), eight
+    sampled jobs byte for byte against the oracle."""
+    r_off, s_off, kr, ir, ks, is_ = datagen.batch_jobs(4096, 1e3, 1e6, 20260224, device=DEV)
+    out = torch.empty((s_off[-1] * 2, 2), dtype=torch.int32, device=DEV)
+    got, out_off = api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out)
+    assert int(out_off[-1]) == got.shape[0]
+    kr64, ks64, glob = batch_as_one_join(r_off, s_off, kr, ks, got, out_off)
+    check_properties(kr64, ks64, glob)
+    oo = out_off.tolist()
+    g = torch.Generator().manual_seed(17)
+    for j in torch.randint(0, 4096, (8,), generator=g).tolist():
+        a, b, c, d = r_off[j], r_off[j + 1], s_off[j], s_off[j + 1]
+        exp = oracle.join_inner(np_of(kr[a:b]), np_of(ir[a:b]), np_of(ks[c:d]), np_of(is_[c:d]))
+        assert_pairs_equal(got[oo[j]:oo[j + 1]], exp)
