@@ -406,6 +406,13 @@ def run_tj(args, ws, rank, local):
                          "frac": step_ach / peak,
                          "what": "algorithmic bytes of every traced kernel of one step / "
                                  "the step's time (overlapped lanes included)"}}
+        # the bytes no implementation can avoid: every input row read once and
+        # every result written once (keys and ids of 8 bytes, pairs of 16)
+        comp = len(rels) * ((n_r + n_s) * 16 + n_s * 16) + n_sort * 32
+        comp_ach = comp / (ms_step / 1e3) / 1e9
+        roof["compulsory"] = {"bytes": comp, "achieved": comp_ach, "frac": comp_ach / peak,
+                              "what": "inputs read once and results written once per step "
+                                      "(keys, ids, pairs) / the step's time"}
     kernels = {k: {"launches": v["launches"], "ms": v["ms"],
                    "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None}
                for k, v in trace.items()}
