@@ -176,9 +176,12 @@ tj_status tj_sort_multi(tj_dtype dt, void* const* cols, int32_t n_cols, void* id
  * allocator when they sort: code that runs while an outer framework owns the
  * device's memory pool, allocation-free real-time paths, or processes that
  * must not grow device memory after start-up.  This entry point runs the same
- * kernels as tj_sort and allocates nothing: its scratch is one file-scope
- * device array of about 18 MB that every GPU loading this library holds until
- * the process exits.  Limits and rules:
+ * kernels as tj_sort and allocates nothing, on the device or on the host (no
+ * cudaMalloc*, no pool allocation, no pinned host memory): its scratch is one
+ * file-scope device array of about 18 MB that every GPU loading this library
+ * holds until the process exits; its job table travels as a kernel argument
+ * and its two small reads (key statistics, error word) land in variables on
+ * the calling thread's stack.  Limits and rules:
  *   - n <= 2^20 rows per call; larger n returns TJ_ERR_INVALID (use tj_sort).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
@@ -187,7 +190,9 @@ tj_status tj_sort_multi(tj_dtype dt, void* const* cols, int32_t n_cols, void* id
  *     different streams, or from different threads) race and must not be made;
  *     the array keeps the last call's contents, and each call clears what it
  *     needs zeroed.
- * Arguments, ordering of the result and synchronisation are those of tj_sort.
+ * Arguments and ordering of the result are those of tj_sort; the call
+ * synchronises `stream` twice (after the key statistics and at the end).
+ * tj_get_stats() reports it with scratch_peak = 0.
  */
 tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream);
 

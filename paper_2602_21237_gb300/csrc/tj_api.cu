@@ -2097,9 +2097,29 @@ tj_status noalloc_scratch(unsigned char** out) {
   return TJ_OK;
 }
 
+// The job table enters the device as a kernel parameter (no host staging
+// buffer, no copy engine).
+template <typename K>
+__global__ void k_put_job(RadixJob<K> job, RadixJob<K>* dst) {
+  *dst = job;
+}
+
+// Device -> host read of a few bytes into the caller's (pageable) variable;
+// returns once the bytes have arrived.
+cudaError_t read_now(void* dst, const void* src, size_t n, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
 template <typename K>
 tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
-  if (n <= 1) return TJ_OK;
+  tj_stats stats = {};
+  stats.groups = 1;
+  if (n <= 1) {
+    g_stats = stats;
+    return TJ_OK;
+  }
   tj_status s = ensure_device();
   if (s != TJ_OK) return s;
   unsigned char* base = nullptr;
@@ -2124,15 +2144,21 @@ tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   hj.n = n;
   TJ_CUDA(cudaMemsetAsync(tail + 2048, 0, 2048, st));  // error word and tile counters
   TJ_CUDA(cudaMemsetAsync(d_stats, 0xFF, sizeof(KeyStats), st));
-  TJ_CUDA(put_small(d_job, &hj, sizeof(hj), st));
+  k_put_job<K><<<1, 1, 0, st>>>(hj, d_job);
+  TJ_CUDA(cudaGetLastError());
   TJ_CUDA(launch_stats<K>(d_job, 1, tiles, d_stats, st));
   KeyStats hs;
-  TJ_CUDA(get_small(&hs, d_stats, sizeof(hs), st));
-  TJ_CUDA(sync_stream(st));
+  TJ_CUDA(read_now(&hs, d_stats, sizeof(hs), st));
   const K lo = key_of<K>(hs.min_u), hi = key_of<K>(~hs.max_u);
   const Plan plan = make_plan(lo_bits<K>(lo), range_of<K>(lo, hi), /*even=*/true,
                               max_digit_bits<K>());
-  if (plan.passes == 0) return TJ_OK;  // all keys equal
+  stats.key_bits = plan.key_bits;
+  stats.radix_passes = plan.passes;
+  stats.digit_bits = plan.max_bits;
+  if (plan.passes == 0) {  // all keys equal
+    g_stats = stats;
+    return TJ_OK;
+  }
   const int64_t bins_max = (int64_t)1 << plan.max_bits;
   set_job_plan(hj, plan);
   hj.hist_stride = kMaxBins;
@@ -2141,7 +2167,8 @@ tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
   const K* rk;
   const K* rv;
   set_job_buffers(hj, keys, ids, bk, bv, keys, ids, &rk, &rv);
-  TJ_CUDA(put_small(d_job, &hj, sizeof(hj), st));
+  k_put_job<K><<<1, 1, 0, st>>>(hj, d_job);
+  TJ_CUDA(cudaGetLastError());
   // the array keeps the last call's contents: clear what must start at zero
   TJ_CUDA(cudaMemsetAsync(hist, 0, (size_t)kMaxPasses * kMaxBins * sizeof(uint32_t), st));
   TJ_CUDA(launch_histogram<K>(d_job, 1, tiles, st));
@@ -2152,10 +2179,12 @@ tj_status sort_noalloc_impl(K* keys, K* ids, int64_t n, cudaStream_t st) {
                                st));
   }
   int h_err = 0;
-  TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
-  TJ_CUDA(sync_stream(st));
+  TJ_CUDA(read_now(&h_err, d_err, sizeof(int), st));
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
   if (rk != keys) return set_err(TJ_ERR_INTERNAL, "odd pass count in place");
+  // the library's scratch for this call is the fixed array, none of it allocated
+  stats.scratch_peak = 0;
+  g_stats = stats;
   return TJ_OK;
 }
 
@@ -2209,8 +2238,7 @@ tj_status tj_join_inner_ex(tj_dtype dt, const void* keys_r, const void* ids_r, i
 }
 
 tj_status tj_sort_noalloc(tj_dtype dt, void* keys, void* ids, int64_t n, void* stream) {
-  g_err[0] = 0;
-  arena_reset();
+  g_err[0] = 0;  // (no arena_reset: this entry point never touches the pinned arena)
   if (n < 0) return set_err(TJ_ERR_INVALID, "negative size");
   if (n > kNoAllocMaxRows)
     return set_err(TJ_ERR_INVALID,
