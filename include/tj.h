@@ -256,6 +256,24 @@ tj_status tj_mlp_adam(float* theta, float* m, float* v, const float* grad, int n
                       float lr, void* stream);
 
 /*
+ * The step that turns a trained network into batch boundaries (no counterpart
+ * in the paper; a check of the learned partitioner's inference kernels).
+ * The sample s (sorted, m >= 1 keys of type dt) fixes the normalised axis
+ * x = log2(1 + k - s_0) / log2(1 + s_{m-1} - s_0).  The network theta (1153
+ * fp32, layout as in tj_mlp_grad) is evaluated on the grid x = u / T,
+ * u = 0..T, clipped to [0, 1] and made monotone by a running maximum:
+ *   table[u] = max_{u' <= u} clip(f(u' / T), 0, 1)            (T + 1 fp32)
+ * and boundary p (p = 1..parts-1) is the key of the first grid point whose
+ * table value reaches p / parts (both in fp32), mapped back through the
+ * inverse of the normalisation and rounded up, at most s_{m-1}:
+ *   bounds[p - 1] = min(ceil(s_0 + 2^(x L) - 1), s_{m-1}), x = u_p / T.
+ * theta, table, sorted and bounds are DEVICE arrays; 1 <= T <= 65536,
+ * 2 <= parts <= 1024.  Synchronises `stream`.
+ */
+tj_status tj_mlp_table(const float* theta, int T, float* table, int parts, tj_dtype dt,
+                       const void* sorted, int64_t m, void* bounds, void* stream);
+
+/*
  * Serving loop (no counterpart in the paper; it measures the P50/P99 latency
  * the paper reports, Sec. 5.2 and Sec. 6, for a stream of requests).
  *

@@ -172,14 +172,20 @@ def mlp_table(theta, T: int = 4096):
     return np.maximum.accumulate(y)
 
 
-def boundaries_table(table, parts: int, s0: int, s1: int, dtype=np.int64):
+def boundaries_table(table, parts: int, s0: int, s1: int, dtype=np.int64,
+                     target_dtype=np.float64):
     """B_p from a monotone tabulated CDF on the normalised axis: the first grid
-    point u with table[u] >= p / parts, mapped back to a key (ceil)."""
+    point u with table[u] >= p / parts, mapped back to a key (ceil).  The
+    comparison is made in `target_dtype` (the library tabulates in fp32 and
+    compares there; a check of its kernels takes the decision in the same
+    precision)."""
     T = len(table) - 1
     L = np.log2(1.0 + float(s1) - float(s0))
+    tab = np.asarray(table).astype(target_dtype)
     out = []
     for p in range(1, parts):
-        u = int(np.searchsorted(table, p / parts, side="left"))
+        target = target_dtype(p) / target_dtype(parts)
+        u = int(np.searchsorted(tab, target, side="left"))
         u = min(u, T)
         x = u / T
         out.append(int(np.ceil(s0 + (2.0 ** (x * L) - 1.0))))

@@ -103,6 +103,8 @@ def _load():
         lib.tj_mlp_grad.restype = ci
         lib.tj_mlp_adam.argtypes = [vp, vp, vp, vp, ci, ci, ctypes.c_float, vp]
         lib.tj_mlp_adam.restype = ci
+        lib.tj_mlp_table.argtypes = [vp, ci, vp, ci, ci, vp, i64, vp, vp]
+        lib.tj_mlp_table.restype = ci
         lib.tj_trace_enable.argtypes = [ci]
         lib.tj_trace_enable.restype = None
         lib.tj_trace_reset.argtypes = []
@@ -196,6 +198,23 @@ def mlp_adam(theta, m, v, g, t: int, lr: float, stream=None):
         _check(lib, lib.tj_mlp_adam(theta.data_ptr(), m.data_ptr(), v.data_ptr(), g.data_ptr(),
                                     theta.numel(), int(t), float(lr), _stream(stream)))
     return theta, m, v
+
+
+def mlp_table(theta, T: int, parts: int, sorted_sample, stream=None):
+    """Monotone tabulation of the network on T + 1 grid points and the
+    parts - 1 batch boundaries it gives over a sorted sample (tj_mlp_table).
+    Returns (table fp32 of T + 1, boundaries of the sample's dtype)."""
+    lib = _load()
+    if not theta.is_cuda or theta.dtype != torch.float32 or not theta.is_contiguous():
+        raise TypeError("theta must be a contiguous CUDA float32 tensor")
+    _need(sorted_sample, sorted_sample.dtype, theta.device, "sorted_sample")
+    table = torch.empty(T + 1, dtype=torch.float32, device=theta.device)
+    bounds = torch.empty(parts - 1, dtype=sorted_sample.dtype, device=theta.device)
+    with torch.cuda.device(theta.device):
+        _check(lib, lib.tj_mlp_table(theta.data_ptr(), int(T), table.data_ptr(), int(parts),
+                                     _dt(sorted_sample), sorted_sample.data_ptr(),
+                                     sorted_sample.numel(), bounds.data_ptr(), _stream(stream)))
+    return table, bounds
 
 
 def version() -> str:

@@ -2428,6 +2428,29 @@ tj_status tj_mlp_adam(float* theta, float* m, float* v, const float* grad, int n
   return TJ_OK;
 }
 
+tj_status tj_mlp_table(const float* theta, int T, float* table, int parts, tj_dtype dt,
+                       const void* sorted, int64_t m, void* bounds, void* stream) {
+  g_err[0] = 0;
+  arena_reset();
+  if (T < 1 || T > 65536) return set_err(TJ_ERR_INVALID, "T must be 1..65536");
+  if (parts < 2 || parts > kMaxCuts) return set_err(TJ_ERR_INVALID, "parts must be 2..%d", kMaxCuts);
+  if (m < 1) return set_err(TJ_ERR_INVALID, "the sample needs at least one key");
+  if (!theta || !table || !sorted || !bounds) return set_err(TJ_ERR_INVALID, "null pointer");
+  tj_status s = ensure_device();
+  if (s != TJ_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dt == TJ_I32)
+    TJ_CUDA(launch_mlp_boundaries<int32_t>(theta, T, table, parts, (const int32_t*)sorted, m,
+                                           (int32_t*)bounds, st));
+  else if (dt == TJ_I64)
+    TJ_CUDA(launch_mlp_boundaries<int64_t>(theta, T, table, parts, (const int64_t*)sorted, m,
+                                           (int64_t*)bounds, st));
+  else
+    return set_err(TJ_ERR_INVALID, "unknown dtype %d", (int)dt);
+  TJ_CUDA(sync_stream(st));
+  return TJ_OK;
+}
+
 const char* tj_status_str(tj_status s) {
   switch (s) {
     case TJ_OK: return "TJ_OK";

@@ -101,3 +101,72 @@ def test_pla_boundaries_are_sample_quantiles():
                         minlength=len(cuts) + 1)
     assert st["partitions"] == len(cuts) + 1
     assert st["max_partition"] == parts.max()
+
+
+def _fp32_forward_bound(th, x):
+    """Forward error bound of the device's fp32 evaluation of the network at
+    x (exact fp32 grid points): one rounding per fma (u = 2^-24), summed over
+    each chain's terms, propagated through the 1-Lipschitz ReLUs; 1.1 covers
+    the second-order terms."""
+    u = 2.0 ** -24
+    b3, w1, b1, W2, b2, w3 = L.unpack(np.asarray(th, np.float64))
+    x = np.asarray(x, np.float64)
+    z1 = x[:, None] * w1 + b1
+    h1 = np.maximum(z1, 0)
+    e1 = u * np.abs(z1)
+    a = h1 @ W2 + b2
+    ea = 33 * u * (np.abs(b2) + np.abs(h1) @ np.abs(W2)) + e1 @ np.abs(W2)
+    h2 = np.maximum(a, 0)
+    eo = 33 * u * (abs(b3) + np.abs(h2) @ np.abs(w3)) + ea @ np.abs(w3)
+    return 1.1 * eo
+
+
+@pytest.mark.parametrize("seed,T,parts,span", [(11, 4096, 128, (1 << 40) - 1),
+                                               (12, 4096, 1024, 987_654_321_987),
+                                               (13, 1024, 37, (1 << 20) - 1)])
+def test_mlp_table_and_boundaries_match_oracle(seed, T, parts, span):
+    rng = np.random.default_rng(seed)
+    # a ramp with hinges at i / 32 whose slope changes at random: it dips
+    # below 0, rises and falls (not monotone) and may pass 1, so the clip, the
+    # running maximum and its plateaus are all exercised
+    th = np.zeros(L.N_PARAMS, np.float32)
+    th[1:33] = 1.0 + rng.normal(0, 0.05, 32)                                # w1
+    th[33:65] = -np.arange(32) / 32.0                                       # b1
+    th[65:1089] = (np.eye(32) + rng.normal(0, 0.03, (32, 32))).reshape(-1)  # W2
+    th[1089:1121] = rng.normal(0, 0.01, 32)                                 # b2
+    c = rng.normal(0, 1.2, 32)
+    c[0] = 1.0
+    th[1121:1153] = c                                                       # w3
+    th[0] = -0.05
+    s0 = int(rng.integers(-(1 << 40), 1 << 40))
+    sample = np.sort(np.concatenate([[s0, s0 + span],
+                                     s0 + rng.integers(0, span, 5000)])).astype(np.int64)
+    table, bounds = api.mlp_table(torch.from_numpy(th).to(DEV), T, parts,
+                                  torch.from_numpy(sample).to(DEV))
+    table = table.cpu().numpy()
+    bounds = bounds.cpu().numpy()
+    # the table: within the fp32 bound of the fp64 oracle (the running maximum
+    # and the clip are 1-Lipschitz, so the bound is the running max of the
+    # pointwise one)
+    ref = L.mlp_table(th.astype(np.float64), T)
+    grid = np.arange(T + 1, dtype=np.float64) / T
+    tol = np.maximum.accumulate(_fp32_forward_bound(th, grid))
+    assert np.all(np.abs(table - ref) <= tol + 1e-30), float(np.max(np.abs(table - ref) - tol))
+    assert np.all(np.diff(table) >= 0) and table.min() >= 0 and table.max() <= 1
+    fwd = L.mlp_forward(th.astype(np.float64), grid)
+    assert fwd.min() < 0 and np.any(np.diff(fwd) < 0) and ref[-1] > 0.9  # not degenerate
+    # the boundaries: decided on the device's own table in fp32, mapped back in
+    # fp64; the fp64 key equals the oracle's unless it lies within rounding of
+    # an integer (exp2 and log2 may differ in the last bit)
+    exp = L.boundaries_table(table, parts, int(sample[0]), int(sample[-1]), np.int64,
+                             target_dtype=np.float32)
+    Lg = np.log2(1.0 + float(sample[-1]) - float(sample[0]))
+    for p in range(1, parts):
+        if bounds[p - 1] == exp[p - 1]:
+            continue
+        tgt = np.float32(p) / np.float32(parts)
+        uu = min(int(np.searchsorted(table.astype(np.float32), tgt, side="left")), T)
+        k = float(sample[0]) + 2.0 ** (uu / T * Lg) - 1.0
+        assert abs(k - round(k)) <= 1e-9 * max(1.0, abs(k)) and abs(int(bounds[p - 1]) - int(exp[p - 1])) == 1, \
+            (p, bounds[p - 1], exp[p - 1], k)
+    assert np.all(np.diff(bounds) >= 0)

@@ -129,3 +129,65 @@ def test_normalize_is_monotone_and_bounded():
     k = np.sort(np.random.default_rng(7).integers(0, 1 << 40, 1000))
     x = L.normalize_keys(k, k[0], k[-1])
     assert x[0] == 0.0 and abs(x[-1] - 1.0) < 1e-12 and np.all(np.diff(x) >= 0)
+
+
+def test_normalize_keys_exact_values():
+    # s1 - s0 + 1 = 2^20, so the denominator is log2(2^20) = 20 exactly and a
+    # key s0 + 2^j - 1 maps to j / 20: exact in fp64.  A dropped "1 +" (log2 of
+    # k - s0) or a wrong endpoint moves these values.
+    for s0 in (0, -(1 << 30), 12345):
+        s1 = s0 + (1 << 20) - 1
+        ks = np.array([s0 + (1 << j) - 1 for j in range(0, 21)], dtype=np.int64)
+        x = L.normalize_keys(ks, s0, s1)
+        assert np.array_equal(x, np.arange(21) / 20.0)
+        assert L.normalize_keys(np.array([s0 + (1 << 10) - 1]), s0, s1)[0] == 0.5
+        # outside [s0, s1]: clipped to the ends
+        assert list(L.normalize_keys(np.array([s0 - 7, s1 + 99]), s0, s1)) == [0.0, 1.0]
+    # a single-key range has no width: everything maps to 0
+    assert np.all(L.normalize_keys(np.array([3, 4, 5]), 4, 4) == 0.0)
+
+
+def _two_unit_theta(a0, c0, a1, c1, v0, v1, b3=0.0):
+    """Network whose output is v0 relu(a0 x + c0) + v1 relu(a1 x + c1) + b3 on
+    x >= 0: hidden-1 units 0 and 1 feed hidden-2 units 0 and 1 through a unit
+    weight (relu of a non-negative value is itself)."""
+    th = np.zeros(L.N_PARAMS)
+    b3_, w1, b1, W2, b2, w3 = L.unpack(th)
+    w1[0], b1[0], w1[1], b1[1] = a0, c0, a1, c1
+    W2[0, 0] = 1.0
+    W2[1, 1] = 1.0
+    w3[0], w3[1] = v0, v1
+    th[0] = b3
+    return th
+
+
+def test_mlp_table_running_max_of_a_rise_and_fall():
+    # f(x) = relu(x) - 2 relu(x - 1/2): rises to 1/2 at x = 1/2, then falls
+    # back to 0 at x = 1.  The monotone table keeps the peak: min(u / T, 1/2).
+    T = 64
+    th = _two_unit_theta(1.0, 0.0, 1.0, -0.5, 1.0, -2.0)
+    u = np.arange(T + 1)
+    assert np.allclose(L.mlp_forward(th, u / T), np.where(u <= T // 2, u / T, 1 - u / T))
+    assert np.allclose(L.mlp_table(th, T), np.minimum(u / T, 0.5), rtol=0, atol=1e-15)
+
+
+def test_mlp_table_clips_to_unit_interval():
+    # f(x) = 3 x - 1 - 3 relu(x - 0.9) ... below 0 until x = 1/3, above 1 from
+    # x = 2/3 (up to 1.7 at x = 0.9, then down to 1.4): the table is
+    # clip(3x - 1, 0, 1), flat at 1 after 2/3 whatever f does there.
+    T = 90
+    th = _two_unit_theta(3.0, 0.0, 1.0, -0.9, 1.0, -3.0, b3=-1.0)
+    u = np.arange(T + 1)
+    assert np.allclose(L.mlp_table(th, T), np.clip(3 * u / T - 1, 0.0, 1.0), rtol=0, atol=1e-12)
+
+
+def test_boundaries_table_reads_the_first_grid_point():
+    # table = min(u / T, 1/2) with T = 64: F reaches p / 8 at u = 8p for p <= 4
+    # and never beyond 1/2, so the later boundaries take the last grid point,
+    # which maps to s1.
+    T = 64
+    table = np.minimum(np.arange(T + 1) / T, 0.5)
+    s0, s1 = 0, (1 << 20) - 1
+    B = L.boundaries_table(table, 8, s0, s1)
+    exp = [int(np.ceil(2.0 ** (8 * p / 64 * 20) - 1)) for p in range(1, 5)] + [s1] * 3
+    assert list(B) == exp
