@@ -1,13 +1,14 @@
-"""GPU tests of the serving loop (tj_server_*): every request's result is the
-same alone and in a concurrent mix, admission never exceeds the budget, an
-oversized request is rejected with TJ_ERR_BUDGET, and latency percentiles are
-reported."""
+"""GPU tests of the serving loop (tj_server_*): every request's result equals
+the CPU oracle's and is the same alone and in a concurrent mix, admission
+never exceeds the budget, an oversized request is rejected with
+TJ_ERR_BUDGET, and latency percentiles are reported."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2602_21237_gb300 import api, datagen
-from gpu_util import DEV
+from gpu_util import DEV, assert_pairs_equal, np_of
 
 pytestmark = pytest.mark.gpu
 
@@ -47,10 +48,15 @@ def test_results_same_alone_and_in_the_mix():
     srv.close()
     for r in res:
         assert r["status"] == 0
-    for j in range(len(reqs)):
+    for j, (kr, ir, ks, is_) in enumerate(reqs):
         n = res[j]["out_count"]
+        exp = oracle.join_inner(np_of(kr), np_of(ir), np_of(ks), np_of(is_))
+        assert n == exp.shape[0]
+        assert_pairs_equal(outs[j][:n], exp)
         assert torch.equal(outs[j][:n], alone[j])
-    for (k, i), (ka, ia) in zip(sorted_mix, sorts_alone):
+    for (k, i), (ka, ia), (kr, ir, _, _) in zip(sorted_mix, sorts_alone, reqs[:6]):
+        ek, ei = oracle.sort(np_of(kr), np_of(ir))
+        assert np.array_equal(np_of(k), ek) and np.array_equal(np_of(i), ei)
         assert torch.equal(k, ka) and torch.equal(i, ia)
     assert rep["completed"] == len(tickets)
     assert rep["peak_reserved"] <= 256 << 20
@@ -78,3 +84,7 @@ def test_replay_poisson_stream():
     srv.close()
     assert all(r["status"] == 0 for r in res)
     assert rep["completed"] == 16 and rep["makespan_s"] > 0
+    for (kr, ir, ks, is_), o, r in zip(reqs, outs, res):
+        exp = oracle.join_inner(np_of(kr), np_of(ir), np_of(ks), np_of(is_))
+        assert r["out_count"] == exp.shape[0]
+        assert_pairs_equal(o[: r["out_count"]], exp)
