@@ -8,12 +8,13 @@ load the library; the first call does, and fails loudly if it is missing.
 """
 from __future__ import annotations
 
-__all__ = ["join_inner", "sort", "join_batch", "TjError", "lib_path", "build"]
+__all__ = ["join_inner", "sort", "sort_multi", "join_batch", "gather_pairs", "stats", "Server",
+           "TjError", "lib_path", "build"]
 
 
 def __getattr__(name):
-    if name in ("join_inner", "sort", "join_batch", "TjError", "lib_path", "stats",
-                "learned_fit", "learned_route", "Server"):
+    if name in ("join_inner", "sort", "sort_multi", "join_batch", "gather_pairs", "TjError",
+                "lib_path", "stats", "Server"):
         from . import api
 
         return getattr(api, name)
