@@ -241,6 +241,99 @@ def time_oracle(sample, reps=1):
     return tuples / dt, dt, tuples, n
 
 
+def host_cores():
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "processor name")):
+                    model = ln.split(":", 1)[1].strip()
+                    if ln.lower().startswith("model name"):
+                        break
+    except OSError:
+        pass
+    return n, model
+
+
+def time_oracle_threads(sample, threads):
+    """The same oracle on `threads` host threads: both relations and the sort
+    input are split into `threads` key ranges (splitters from R's keys), each
+    thread runs the unchanged oracle on its ranges (the C calls release the
+    GIL), and the parts are concatenated in key order, which is the
+    single-threaded result exactly.  Partitioning and concatenation are timed."""
+    import concurrent.futures as cf
+
+    import numpy as np
+
+    import oracle
+
+    r_k, r_i, sk, si, so_k, so_i, s, frac = sample
+    oracle.build()
+    oracle._load()
+    t0 = time.perf_counter()
+    q = np.quantile(r_k[:: max(1, len(r_k) // 65536)], np.arange(1, threads) / threads)
+    split = np.unique(q.astype(r_k.dtype))
+    qs = np.quantile(so_k[:: max(1, len(so_k) // 65536)], np.arange(1, threads) / threads)
+    split_s = np.unique(qs.astype(so_k.dtype))
+
+    def rng(keys, sp, t):
+        lo = sp[t - 1] if t > 0 else None
+        hi = sp[t] if t < len(sp) else None
+        m = np.ones(len(keys), dtype=bool)
+        if lo is not None:
+            m &= keys >= lo
+        if hi is not None:
+            m &= keys < hi
+        return m
+
+    def join_part(t):
+        mr, ms = rng(r_k, split, t), rng(sk, split, t)
+        return oracle.join_inner(r_k[mr], r_i[mr], sk[ms], si[ms])
+
+    def sort_part(t):
+        m = rng(so_k, split_s, t)
+        return oracle.sort(so_k[m], so_i[m])
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        jp = list(ex.map(join_part, range(len(split) + 1)))
+        sp = list(ex.map(sort_part, range(len(split_s) + 1)))
+    pairs = np.concatenate(jp)
+    sorted_k = np.concatenate([a for a, _ in sp])
+    sorted_i = np.concatenate([b for _, b in sp])
+    dt = time.perf_counter() - t0
+    tuples = len(r_k) + len(sk) + len(so_k)
+    return tuples / dt, dt, pairs, (sorted_k, sorted_i)
+
+
+def cpu_baseline_line(sample, reps=3):
+    """The oracle on this host's cores (T threads) and on one core, median of
+    `reps` runs each; the T-thread result is checked against one core's."""
+    import numpy as np
+
+    import oracle
+
+    cores, model = host_cores()
+    one = sorted(time_oracle(sample)[1] for _ in range(reps))[reps // 2]
+    runs = [time_oracle_threads(sample, cores) for _ in range(reps)]
+    dt = sorted(r[1] for r in runs)[reps // 2]
+    r_k, r_i, sk, si, so_k, so_i, s, frac = sample
+    ok = np.array_equal(runs[0][2], oracle.join_inner(r_k, r_i, sk, si))
+    ek, ei = oracle.sort(so_k, so_i)
+    ok = ok and np.array_equal(runs[0][3][0], ek) and np.array_equal(runs[0][3][1], ei)
+    tuples = sample_tuples(sample)
+    desc = (f"key range [0, {frac:g} n_r) of the workload: {len(r_k)} R rows, {len(sk)} S rows "
+            f"(Zipf s={s}), sort of {len(so_k)} rows; {cores} threads (key-range parts, "
+            f"result equal to one thread's: {bool(ok)}) {dt:.3f} s, one thread {one:.2f} s, "
+            f"median of {reps}; host CPU: {model or 'unknown'}")
+    return {"value": tuples / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": desc, "single_thread": {"value": tuples / one, "cores": 1},
+            "cpu_model": model, "threads_match_single": bool(ok)}
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args, ws, rank):
     """The CPU oracle, as it stands, on a bounded sample per step."""
@@ -253,22 +346,23 @@ def run_reference(args, ws, rank):
     sample = cpu_sample(kr, ir, rels, sk, si)
     del kr, ir, rels, sk, si
     torch.cuda.empty_cache()
+    cores, model = host_cores()
     for _ in range(args.warmup):
-        time_oracle(sample)
+        time_oracle_threads(sample, cores)
     times = []
     for _ in range(args.steps):
-        v, dt, tuples, n = time_oracle(sample)
-        times.append(dt)
+        times.append(time_oracle_threads(sample, cores)[1])
     dt = statistics.mean(times)
     value = sample_tuples(sample) / dt
     desc = (f"key range [0, {sample[7]:g} n_r) of the workload: {len(sample[0])} R rows, "
-            f"{len(sample[2])} S rows (Zipf s={sample[6]}), sort of {len(sample[4])} rows")
+            f"{len(sample[2])} S rows (Zipf s={sample[6]}), sort of {len(sample[4])} rows; "
+            f"the oracle on {cores} threads over key-range parts; host CPU: {model or 'unknown'}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": workload_config(args, zipfs),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -334,6 +428,11 @@ def run_tj(args, ws, rank, local):
                                                   "scratch_peak", "staging_bytes",
                                                   "route_regions", "balance")}
            for s in join_st}
+    for s in join_st:
+        d = st0[f"s{s}"]
+        # scratch (bounded by the budget) + the routed batches (held apart)
+        d["device_footprint_bytes"] = d["scratch_peak"] + d["staging_bytes"]
+        d["mem_budget_bytes"] = budget
 
     api.trace_reset()
     api.trace_enable(True)
@@ -413,6 +512,22 @@ def run_tj(args, ws, rank, local):
         roof["compulsory"] = {"bytes": comp, "achieved": comp_ach, "frac": comp_ach / peak,
                               "what": "inputs read once and results written once per step "
                                       "(keys, ids, pairs) / the step's time"}
+        # the partitioned join's algorithmic bytes by the hash-partition model:
+        # one partition pass (read + write of key and id), build read of R,
+        # probe read of S, table writes at load 0.5, one 32-byte sector per
+        # probe, the pairs written once (w = 16 bytes of key + id per row)
+        wrow = 16
+        jb = (2 * (n_r + n_s) * wrow + n_r * wrow + n_s * wrow + 2 * n_r * wrow + 32 * n_s
+              + n_s * wrow)
+        roof["join"] = {
+            "alg_bytes_per_join": jb,
+            "what": "2 (n_r + n_s) w + n_r w + n_s w + 2 n_r w + 32 n_s + |J| 2 w_id "
+                    "(w = 16 B, |J| = n_s) / the join call's time",
+            "per_zipf": {}}
+        for s, _, _ in rels:
+            ms_j = statistics.mean(per_op[f"join_s{s}"])
+            a = jb / (ms_j / 1e3) / 1e9
+            roof["join"]["per_zipf"][f"s{s}"] = {"ms": ms_j, "achieved": a, "frac": a / peak}
     kernels = {k: {"launches": v["launches"], "ms": v["ms"],
                    "gbs": v["bytes"] / (v["ms"] / 1e3) / 1e9 if v["ms"] > 0 else None}
                for k, v in trace.items()}
@@ -424,11 +539,7 @@ def run_tj(args, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         sample = cpu_sample(kr, ir, rels, sort_src_k, sort_src_i)
-        v, dt, tuples, _ = time_oracle(sample)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"key range [0, n_r/64) of the workload: {len(sample[0])} R rows, "
-                          f"{len(sample[2])} S rows (s={sample[6]}), sort of {len(sample[4])} "
-                          f"rows; {dt:.2f} s single-threaded")}
+        cpu = cpu_baseline_line(sample)
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras:
         del kr, ir, rels, sort_src_k, sort_src_i, out, sk, si

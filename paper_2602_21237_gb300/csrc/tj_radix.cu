@@ -350,7 +350,9 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 // K4: one onesweep digit pass
 // ---------------------------------------------------------------------------
 // Shared memory (bins = 2^bits of this pass, set at launch; hb = ceil(bins/2)):
-//   keys[tile] K | ids[tile] K          rows in input order (never moved)
+//   keys[tile + 16 B] K | ids[tile + 16 B] K   rows in input order (never moved),
+//                                       each starting where its source's address
+//                                       modulo 16 puts it
 //   src[tile] u16                       input row of each tile-sorted slot
 //   warp counters[kSortWarps][hb] u32   two 16-bit digit counters per word
 //   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
@@ -361,7 +363,7 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 template <typename K>
 __host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile,
                                                          bool guard = false) {
-  return 2 * sizeof(K) * (size_t)tile + sizeof(uint16_t) * (size_t)tile +
+  return 2 * sizeof(K) * (size_t)tile + 2 * 16 + sizeof(uint16_t) * (size_t)tile +
          sizeof(uint32_t) * (size_t)kSortWarps * (size_t)((bins + 1) / 2) +
          sizeof(uint32_t) * 2 * (size_t)bins + sizeof(long long) * (size_t)bins +
          (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
@@ -428,30 +430,42 @@ __device__ __forceinline__ int lookback_consume(const uint32_t (&v)[W], uint32_t
   return used;
 }
 
-// Asynchronous global -> shared copy of n elements of K (no registers held):
-// 16-byte chunks when both ends allow it, else one element per copy.
-template <typename K>
-__device__ __forceinline__ void copy_rows_async(K* dst, const K* __restrict__ src, int n) {
-  const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
-  if ((((uintptr_t)src) & 15u) == 0) {
-    constexpr int kPer = 16 / (int)sizeof(K);
-    const int chunks = n / kPer;
-    for (int c = threadIdx.x; c < chunks; c += kSortThreads)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sdst + 16u * c),
-                   "l"(src + c * kPer)
-                   : "memory");
-    for (int i = chunks * kPer + threadIdx.x; i < n; i += kSortThreads)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
-                       sdst + (uint32_t)(i * sizeof(K))),
-                   "l"(src + i), "n"(sizeof(K))
-                   : "memory");
-  } else {
-    for (int i = threadIdx.x; i < n; i += kSortThreads)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
-                       sdst + (uint32_t)(i * sizeof(K))),
-                   "l"(src + i), "n"(sizeof(K))
+// Asynchronous global -> shared copy of n <= TILE elements of K (no registers
+// held) into `area` (TILE + 16 / sizeof(K) elements, 16-byte aligned).  The
+// copy starts at area + (src mod 16) / sizeof(K), so both ends agree modulo
+// 16 and all but a head and a tail element move in 16-byte chunks whatever
+// the source's alignment; returns where it starts.  Every loop has a fixed
+// trip count (predicated), so the compiler unrolls it.
+template <typename K, int TILE>
+__device__ __forceinline__ K* copy_rows_async(K* area, const K* __restrict__ src, int n) {
+  constexpr int kPer = 16 / (int)sizeof(K);
+  const uint32_t mis = (uint32_t)((uintptr_t)src & 15u);  // a multiple of sizeof(K)
+  K* d = area + mis / sizeof(K);
+  const uint32_t sd = (uint32_t)__cvta_generic_to_shared(d);
+  const int head = min(n, mis ? (int)((16u - mis) / sizeof(K)) : 0);
+  const int chunks = (n - head) / kPer;
+  const int tail0 = head + chunks * kPer;
+  const int tid = threadIdx.x;
+  if (tid < head)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(sd + (uint32_t)(tid * sizeof(K))),
+                 "l"(src + tid), "n"(sizeof(K))
+                 : "memory");
+  constexpr int kIters = (TILE / kPer + kSortThreads - 1) / kSortThreads;
+#pragma unroll
+  for (int it = 0; it < kIters; ++it) {
+    const int c = tid + it * kSortThreads;
+    if (c < chunks)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       sd + (uint32_t)(head * sizeof(K)) + 16u * c),
+                   "l"(src + head + c * kPer)
                    : "memory");
   }
+  if (tid < n - tail0)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                     sd + (uint32_t)((tail0 + tid) * sizeof(K))),
+                 "l"(src + tail0 + tid), "n"(sizeof(K))
+                 : "memory");
+  return d;
 }
 
 // Stable ranks of a warp's rows by digit.  Row i*32 + lane of the warp holds
@@ -552,7 +566,9 @@ __device__ __forceinline__ void rank_items_or(uint32_t (&dr)[ITEMS], int nv, uin
 //      look-back (bounded wait; on timeout report TJ_ERR_TIMEOUT and go on);
 //   5. walk the slots in order and write each row to its global position:
 //      consecutive slots of one digit go to consecutive addresses.
-template <typename K, int ITEMS>
+// ROUTE: a route pass (digit = batch index from the cut table, pass 0);
+// otherwise a sort pass (digit = bits of key - lo).
+template <typename K, int ITEMS, bool ROUTE>
 __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     k_onesweep(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles, int pass,
                uint32_t* __restrict__ tile_counter, int* __restrict__ err,
@@ -584,9 +600,10 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   uint32_t* lb_base = J->lookback + pass * J->lb_stride;
   uint32_t* lb_mine = lb_base + lt * bins;
 
-  K* s_keys = reinterpret_cast<K*>(smem);
-  K* s_vals = s_keys + TILE;
-  uint16_t* s_src = reinterpret_cast<uint16_t*>(s_vals + TILE);
+  constexpr int kPad = 16 / (int)sizeof(K);
+  K* const a_keys = reinterpret_cast<K*>(smem);  // staging areas (16-byte aligned)
+  K* const a_vals = a_keys + TILE + kPad;
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(a_vals + TILE + kPad);
   uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_src + TILE);
   uint32_t* s_count = s_whist + kSortWarps * hb;  // contiguous with s_whist
   uint32_t* s_excl = s_count + bins;
@@ -598,11 +615,14 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   uint32_t* s_rend =  // end of each batch's region (route passes with sized regions)
       reinterpret_cast<uint32_t*>(s_dig8 + (bins <= 256 ? 1 : 2) * TILE);
   const bool dig8 = bins <= 256;
-  const bool route = J->cuts != nullptr;
+  constexpr bool route = ROUTE;
+  // sort digits within the low 32 bits of key - lo: 32-bit arithmetic
+  const bool narrow = shift + nbits <= 32;
+  const uint32_t lo32 = (uint32_t)lo;
 
   // 1. tile -> shared memory (asynchronous), counters zeroed meanwhile
-  copy_rows_async<K>(s_keys, J->src_k[pass] + row0, nvalid);
-  copy_rows_async<K>(s_vals, J->src_v[pass] + row0, nvalid);
+  const K* s_keys = copy_rows_async<K, TILE>(a_keys, J->src_k[pass] + row0, nvalid);
+  const K* s_vals = copy_rows_async<K, TILE>(a_vals, J->src_v[pass] + row0, nvalid);
   asm volatile("cp.async.commit_group;" ::: "memory");
   const bool guard = route && J->route_end != nullptr;
   if (route) {
@@ -625,11 +645,20 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   // 2. digits (low 16 bits of dr; the rank goes to the high 16 bits later)
   const int wbase = warp * 32 * ITEMS;
   uint32_t dr[ITEMS];
+  if (route) {
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const K k = s_keys[wbase + i * 32 + lane];  // padding rows: unused values
-    dr[i] = route ? route_idx<K>(k, lo, s_cuts, s_tab, J->route_steps, J->route_shift)
-                  : digit_of<K>(k, lo, shift, mask);
+    for (int i = 0; i < ITEMS; ++i) {
+      const K k = s_keys[wbase + i * 32 + lane];  // padding rows: unused values
+      dr[i] = route_idx<K>(k, lo, s_cuts, s_tab, J->route_steps, J->route_shift);
+    }
+  } else if (narrow) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      dr[i] = (((uint32_t)s_keys[wbase + i * 32 + lane] - lo32) >> shift) & mask;
+  } else {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i)
+      dr[i] = digit_of<K>(s_keys[wbase + i * 32 + lane], lo, shift, mask);
   }
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i)
@@ -742,34 +771,68 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   // 5. slots in order -> global
   K* __restrict__ dst_k = J->dst_k[pass];
   K* __restrict__ dst_v = J->dst_v[pass];
-  if (guard) {
-    // batch regions sized in advance: a row past its region's end is dropped
-    // and reported (the caller then routes again with exact sizes)
-    bool over = false;
-#pragma unroll 4
-    for (int q = tid; q < nvalid; q += kSortThreads) {
-      const int r = s_src[q];
-      const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
-      const long long g = s_gbase[d] + q;
-      const bool in = g < (long long)s_rend[d];
-      over |= !in;
-      if (in) {
+  if (route) {
+    if (guard) {
+      // batch regions sized in advance: a row past its region's end is
+      // dropped and reported (the caller then routes again with exact sizes)
+      bool over = false;
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int q = tid + it * kSortThreads;
+        if (q < nvalid) {
+          const int r = s_src[q];
+          const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
+          const long long g = s_gbase[d] + q;
+          const bool in = g < (long long)s_rend[d];
+          over |= !in;
+          if (in) {
+            dst_k[g] = s_keys[r];
+            dst_v[g] = s_vals[r];
+          }
+        }
+      }
+      if (over) atomicCAS(err, 0, (int)TJ_ERR_CAPACITY);
+      return;
+    }
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int q = tid + it * kSortThreads;
+      if (q < nvalid) {
+        const int r = s_src[q];
+        const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
+        const long long g = s_gbase[d] + q;
         dst_k[g] = s_keys[r];
         dst_v[g] = s_vals[r];
       }
     }
-    if (over) atomicCAS(err, 0, (int)TJ_ERR_CAPACITY);
     return;
   }
-#pragma unroll 4
-  for (int q = tid; q < nvalid; q += kSortThreads) {
-    const int r = s_src[q];
-    const K k = s_keys[r];
-    const uint32_t d = route ? (dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q])
-                             : digit_of<K>(k, lo, shift, mask);
-    const long long g = s_gbase[d] + q;
-    dst_k[g] = k;
-    dst_v[g] = s_vals[r];
+  if (narrow) {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int q = tid + it * kSortThreads;
+      if (q < nvalid) {
+        const int r = s_src[q];
+        const K k = s_keys[r];
+        const uint32_t d = (((uint32_t)k - lo32) >> shift) & mask;
+        const long long g = s_gbase[d] + q;
+        dst_k[g] = k;
+        dst_v[g] = s_vals[r];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int q = tid + it * kSortThreads;
+      if (q < nvalid) {
+        const int r = s_src[q];
+        const K k = s_keys[r];
+        const uint32_t d = digit_of<K>(k, lo, shift, mask);
+        const long long g = s_gbase[d] + q;
+        dst_k[g] = k;
+        dst_v[g] = s_vals[r];
+      }
+    }
   }
 }
 
@@ -838,64 +901,75 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
   return cudaGetLastError();
 }
 
+template <typename K, bool ROUTE>
+cudaError_t launch_onesweep_t(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
+                              int pass, int max_bits, uint32_t* d_tile_counter, int* d_err,
+                              cudaStream_t st, const int32_t* d_tile_job, int items, bool guard) {
+  if (items == 4) {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kSortThreads * 4, guard);
+    k_onesweep<K, 4, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  } else if (items == kItemsRoute && kItemsRoute != kItems && kItemsRoute != kItemsWide) {
+    if constexpr (ROUTE) {  // route passes only
+      const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kTileRoute, guard);
+      k_onesweep<K, kItemsRoute, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+          d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  } else if (items == kItemsWide) {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kTileWide, guard);
+    k_onesweep<K, kItemsWide, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  } else {
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kTile, guard);
+    k_onesweep<K, kItems, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
+  }
+  return cudaGetLastError();
+}
+
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                             int pass, int max_bits, bool route, uint32_t* d_tile_counter,
                             int* d_err, cudaStream_t st, const int32_t* d_tile_job, int items,
                             bool guard) {
   if (total_tiles <= 0) return cudaSuccess;
-  if (items == 4) {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kSortThreads * 4, guard);
-    k_onesweep<K, 4><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
-        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
-  } else if (items == kItemsRoute && kItemsRoute != kItems && kItemsRoute != kItemsWide) {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTileRoute, guard);
-    k_onesweep<K, kItemsRoute><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
-        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
-  } else if (items == kItemsWide) {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTileWide, guard);
-    k_onesweep<K, kItemsWide><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
-        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
-  } else {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, route, kTile, guard);
-    k_onesweep<K, kItems><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
-        d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
-  }
-  return cudaGetLastError();
+  if (route)
+    return launch_onesweep_t<K, true>(d_jobs, num_jobs, total_tiles, pass, max_bits,
+                                      d_tile_counter, d_err, st, d_tile_job, items, guard);
+  return launch_onesweep_t<K, false>(d_jobs, num_jobs, total_tiles, pass, max_bits,
+                                     d_tile_counter, d_err, st, d_tile_job, items, false);
+}
+
+// Largest dynamic shared memory of every onesweep instantiation (route passes
+// with sized regions need the most).
+template <typename K, int ITEMS, bool ROUTE>
+cudaError_t onesweep_attr() {
+  return cudaFuncSetAttribute(k_onesweep<K, ITEMS, ROUTE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)onesweep_smem_bytes<K>(kMaxBins, ROUTE, kSortThreads * ITEMS,
+                                                          ROUTE));
+}
+
+template <typename K>
+cudaError_t onesweep_attrs() {
+  cudaError_t e;
+  if ((e = onesweep_attr<K, kItems, false>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItems, true>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItemsWide, false>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItemsWide, true>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, 4, false>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, 4, true>()) != cudaSuccess) return e;
+  if (kItemsRoute != kItems && kItemsRoute != kItemsWide)
+    if ((e = onesweep_attr<K, kItemsRoute, true>()) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 cudaError_t radix_init_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_onesweep<int32_t, kItems>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTile, true));
+  cudaError_t e = onesweep_attrs<int32_t>();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_onesweep<int64_t, kItems>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTile, true));
-  if (e != cudaSuccess) return e;
-  if (kItemsRoute != kItems && kItemsRoute != kItemsWide) {
-    e = cudaFuncSetAttribute(k_onesweep<int32_t, kItemsRoute>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTileRoute, true));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_onesweep<int64_t, kItemsRoute>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTileRoute, true));
-    if (e != cudaSuccess) return e;
-  }
-  e = cudaFuncSetAttribute(k_onesweep<int32_t, kItemsWide>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kTileWide, true));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_onesweep<int64_t, kItemsWide>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kTileWide, true));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_onesweep<int32_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)onesweep_smem_bytes<int32_t>(kMaxBins, true, kSortThreads * 4, true));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_onesweep<int64_t, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)onesweep_smem_bytes<int64_t>(kMaxBins, true, kSortThreads * 4, true));
+  return onesweep_attrs<int64_t>();
 }
 
 #define TJ_INSTANTIATE_RADIX(K)                                                                 \
