@@ -758,6 +758,7 @@ def extra_learned(scale):
         st = api.stats()
         res[label] = {"ms": ms, "tuples_per_s": 2 * n / (ms / 1e3),
                       "path": "single_pass" if st["partitions"] == 0 else
+                      ("radix (judge) for " if st["learned"] >= 100 else "") +
                       {2: "radix", 3: "pla", 4: "mlp"}.get(st["learned"] % 100, "?"),
                       "groups": st["groups"]}
     res["under_1GB_budget"] = under

@@ -62,12 +62,16 @@ typedef struct {
   int32_t route_regions;   /* batch regions of the route pass: 0 none (single pass),
                               1 sized by a route histogram, 2 sized from the sample,
                               3 sized from the sample, then routed again exactly */
-  int32_t learned;         /* router used: tj_router value; +100 if it fell back to radix */
+  int32_t learned;         /* router used: tj_router value; +100 when the radix judge
+                              replaced the requested learned model by equal-width
+                              ranges (their sampled balance within 1.25x of the
+                              model's) */
   int32_t partitions;      /* key-range batches of the route pass (0 = single pass) */
   int32_t heavy_keys;      /* keys that got a batch of their own */
   int64_t max_partition;   /* rows (R + S) of the largest batch */
   double balance;          /* largest batch / mean batch (1 = perfect) */
-  double radix_balance;    /* the same for equal-width key ranges, from the sample */
+  double radix_balance;    /* the same for equal-width key ranges on the sample, over the
+                              non-empty ones (learned routers only) */
   int32_t tile_rows;       /* batched join: rows per onesweep tile used */
   int32_t digit_cap;       /* batched join: widest radix digit allowed */
   int32_t lanes;           /* streams the groups alternate between (2 when the budget
@@ -75,6 +79,8 @@ typedef struct {
                               the single pass) */
   int32_t packed_keys;     /* tj_sort_multi: 1 if the key columns were folded into one
                               key (their significant bits fit it), 0 if sorted per column */
+  double learned_balance;  /* the learned model's batches on the sample: largest / mean,
+                              batches of a single key left out (0 if no model) */
 } tj_stats;
 
 /*
@@ -88,6 +94,11 @@ typedef enum {
   TJ_ROUTE_PLA = 3,    /* batches from a piecewise-linear CDF on a sample's quantiles */
   TJ_ROUTE_MLP = 4     /* batches from a 1-32-32-1 MLP CDF trained on the device */
 } tj_router;
+/* Radix judges the learned routers: on the sample, when equal-width ranges are
+ * balanced within 1.25x of the model's batches (single-key batches of heavy
+ * keys left out) and, under a budget, their largest batch fits half of the
+ * working set, the join routes by equal-width ranges instead (their route pass
+ * needs no cut-table search) and tj_stats.learned reports router + 100. */
 
 typedef struct {
   int32_t router;        /* tj_router */
@@ -98,6 +109,10 @@ typedef struct {
   int32_t mlp_batch;     /* sample rows per step (0 = 512) */
   float mlp_lr;          /* Adam learning rate (0 = 3e-3) */
   uint64_t seed;         /* sample offsets, MLP initialisation and batches (0 = 20260221) */
+  float radix_judge;     /* equal-width ranges replace a learned model whose sampled
+                            balance is not better than theirs by more than this
+                            factor (0 = 1.25; negative = never) */
+  int32_t reserved;      /* 0 */
 } tj_join_opts;
 
 /*

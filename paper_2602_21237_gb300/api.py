@@ -40,14 +40,16 @@ class _Stats(ctypes.Structure):
                 ("heavy_keys", ctypes.c_int32), ("max_partition", ctypes.c_int64),
                 ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double),
                 ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32),
-                ("lanes", ctypes.c_int32), ("packed_keys", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("packed_keys", ctypes.c_int32),
+                ("learned_balance", ctypes.c_double)]
 
 
 class _Opts(ctypes.Structure):
     _fields_ = [("router", ctypes.c_int32), ("partitions", ctypes.c_int32),
                 ("sample_stride", ctypes.c_int32), ("pla_segments", ctypes.c_int32),
                 ("mlp_steps", ctypes.c_int32), ("mlp_batch", ctypes.c_int32),
-                ("mlp_lr", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("mlp_lr", ctypes.c_float), ("seed", ctypes.c_uint64),
+                ("radix_judge", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class _Column(ctypes.Structure):
@@ -224,7 +226,8 @@ def version() -> str:
 def join_inner(keys_r, ids_r, keys_s, ids_s, mem_budget_bytes: int = 0, out=None,
                stream=None, router: str | None = None, partitions: int = 0,
                sample_stride: int = 0, pla_segments: int = 0, mlp_steps: int = 0,
-               mlp_batch: int = 0, mlp_lr: float = 0.0, seed: int = 0):
+               mlp_batch: int = 0, mlp_lr: float = 0.0, seed: int = 0,
+               radix_judge: float = 0.0):
     """Inner equi-join (paper Sec. 4.1) -> (count, 2) tensor of (r_id, s_id)
     ordered by key, then S position, then R position.
 
@@ -232,12 +235,14 @@ def join_inner(keys_r, ids_r, keys_s, ids_s, mem_budget_bytes: int = 0, out=None
     pairs; otherwise one of n_s rows is tried first and, if the result is
     larger, the join is run again into a buffer of the exact size.  `router`
     ('auto', 'single', 'radix', 'pla', 'mlp') and the other keywords fill
-    tj_join_opts (0 = library default)."""
+    tj_join_opts (0 = library default; radix_judge < 0 keeps a learned model
+    whatever the radix judge finds)."""
     opts = None
     if router is not None or partitions or sample_stride or pla_segments or mlp_steps or \
-            mlp_batch or mlp_lr or seed:
+            mlp_batch or mlp_lr or seed or radix_judge:
         opts = _Opts(ROUTERS[router or "auto"], int(partitions), int(sample_stride),
-                     int(pla_segments), int(mlp_steps), int(mlp_batch), float(mlp_lr), int(seed))
+                     int(pla_segments), int(mlp_steps), int(mlp_batch), float(mlp_lr), int(seed),
+                     float(radix_judge), 0)
     lib = _load()
     dev = keys_r.device
     dt = _dt(keys_r)

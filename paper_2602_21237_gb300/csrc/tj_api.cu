@@ -517,6 +517,7 @@ struct Opts {
   int mlp_batch = 512;
   float mlp_lr = 3e-3f;
   uint64_t seed = 20260221ull;
+  double radix_judge = 1.25;  // < 0: the learned model is always kept
   bool exact_route = false;  // size the batch regions by a histogram, not the sample
 };
 
@@ -535,6 +536,7 @@ Opts make_opts(const tj_join_opts* o) {
   if (o->mlp_batch > 0) x.mlp_batch = o->mlp_batch;
   if (o->mlp_lr > 0.f) x.mlp_lr = o->mlp_lr;
   if (o->seed) x.seed = o->seed;
+  if (o->radix_judge != 0.f) x.radix_judge = o->radix_judge;
   return x;
 }
 
@@ -752,6 +754,49 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
 //    buffers, histograms, look-back, join state) fits the budget, and every
 //    group is sorted and aligned by one batched launch sequence, its output
 //    written after the previous group's (device-side running offset).
+// Cuts of 2^plog equal-width batches over [lo, hi]: lo + p 2^(b - plog), b =
+// significant bits of hi - lo (every key of the range its own batch when
+// b <= plog).  The batch of a key is then (key - lo) >> (b - plog).
+template <typename K>
+std::vector<K> radix_cuts(K lo, K hi, int plog) {
+  std::vector<K> cuts;
+  const int b = bitlen(range_of<K>(lo, hi));
+  if (b <= plog) {
+    for (uint64_t x = 1; x <= range_of<K>(lo, hi); ++x) cuts.push_back((K)(lo_bits<K>(lo) + x));
+  } else {
+    for (int64_t p = 1; p < ((int64_t)1 << plog); ++p)
+      cuts.push_back((K)(lo_bits<K>(lo) + ((uint64_t)p << (b - plog))));
+  }
+  return cuts;
+}
+
+// Smallest and largest key of both relations (one read of the keys).
+template <typename K>
+tj_status key_range(const K* kr, int64_t nr, const K* ks, int64_t ns, K* lo, K* hi,
+                    cudaStream_t st) {
+  Carve c;
+  const size_t o_jobs = c.add<RadixJob<K>>(2), o_stats = c.add<KeyStats>(2);
+  Block b;
+  TJ_CUDA(b.alloc(c.off, st));
+  RadixJob<K> hj[2];
+  memset(hj, 0, sizeof(hj));
+  hj[0].keys = kr;
+  hj[0].n = nr;
+  hj[1].keys = ks;
+  hj[1].n = ns;
+  hj[1].tile0 = ceil_div(nr, kTile);
+  TJ_CUDA(put_small(b.at<RadixJob<K>>(o_jobs), hj, sizeof(hj), st));
+  TJ_CUDA(cudaMemsetAsync(b.at<KeyStats>(o_stats), 0xFF, 2 * sizeof(KeyStats), st));
+  TJ_CUDA(launch_stats<K>(b.at<RadixJob<K>>(o_jobs), 2, hj[1].tile0 + ceil_div(ns, kTile),
+                          b.at<KeyStats>(o_stats), st));
+  KeyStats hs[2];
+  TJ_CUDA(get_small(hs, b.at<KeyStats>(o_stats), sizeof(hs), st));
+  TJ_CUDA(sync_stream(st));
+  *lo = key_of<K>(std::min(hs[0].min_u, hs[1].min_u));
+  *hi = key_of<K>(std::max(~hs[0].max_u, ~hs[1].max_u));
+  return TJ_OK;
+}
+
 template <typename K>
 std::vector<K> make_cuts(const std::vector<K>& b) {
   std::vector<K> v(b);
@@ -783,6 +828,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   int router = o.router;
   std::vector<uint32_t> sample_cnt;  // per side and batch, when regions are sized by the sample
   int64_t sample_m[2] = {0, 0};
+  bool radix_route = false;  // equal-width batches, routed by their digit (no cut table)
+  bool fell_back = false;    // the radix judge replaced the learned model
   // ---- 1. cut keys ----
   if (router == TJ_ROUTE_PLA || router == TJ_ROUTE_MLP) {
     const int stride = o.stride;
@@ -846,54 +893,111 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       tr.end();
     }
     TJ_CUDA(get_small(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K), st));
-    // radix judge on the (sorted) sample: balance of equal-width ranges of the
-    // same count, from bucket edges found by binary search on the device
+    // per-side sample counts of the batches a set of cuts makes
+    auto sample_counts = [&](const std::vector<K>& cv, std::vector<uint32_t>& cnt) -> tj_status {
+      std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
+      std::copy(cv.begin(), cv.end(), hc.begin());
+      TJ_CUDA(put_small(sb.at<K>(o_scuts), hc.data(), kMaxCuts * sizeof(K), st));
+      TJ_CUDA(cudaMemsetAsync(sb.at<uint32_t>(o_scnt), 0, 2 * kMaxBins * sizeof(uint32_t), st));
+      TJ_CUDA(launch_sample_route_counts<K>(sb.at<K>(o_k), sb.at<K>(o_v), m, m_r,
+                                            sb.at<K>(o_scuts), (int)cv.size(),
+                                            sb.at<uint32_t>(o_scnt), st));
+      cnt.assign(2 * (size_t)kMaxBins, 0u);
+      TJ_CUDA(get_small(cnt.data(), sb.at<uint32_t>(o_scnt), cnt.size() * sizeof(uint32_t), st));
+      TJ_CUDA(sync_stream(st));
+      return TJ_OK;
+    };
+    // Radix judges the model on the (sorted) sample: the balance of
+    // equal-width ranges of the same count (bucket edges by binary search on
+    // the device) against the balance of the model's batches, leaving out the
+    // batches of a single key (a heavy key isolated by its cuts needs no
+    // sort).  Radix replaces the model whenever it is within o.radix_judge
+    // (1.25 by default) of it, allowing for the sample's noise (the model is
+    // judged on the sample it was fitted to), and its largest batch fits the
+    // budget
+    // -- its route pass is a plain digit pass, no cut-table search -- so a
+    // model that fits the keys no better than equal-width ranges (uniform
+    // keys, or a network that failed to fit) falls back to radix.
+    const int b_all = bitlen(range_of<K>(lo, hi));
+    int plog = 0;
+    while ((2 << plog) <= parts) ++plog;
+    int64_t radix_max = 0;  // sample rows of the largest equal-width range
+    double radix_noise = 0;  // sampling noise of the largest range's balance
     {
-      const int b = bitlen(range_of<K>(lo, hi));
-      int plog = 0;
-      while ((2 << plog) <= parts) ++plog;
-      const int sh = std::max(0, b - plog);
+      const int sh = std::max(0, b_all - plog);
       const int nb = 1 << plog;
       TJ_CUDA(launch_sorted_bucket_edges<K>(sb.at<K>(o_k), m, lo_bits<K>(lo), sh, nb,
                                             sb.at<int64_t>(o_edges), st));
       std::vector<int64_t> edges((size_t)nb + 1);
       TJ_CUDA(get_small(edges.data(), sb.at<int64_t>(o_edges), edges.size() * 8, st));
       TJ_CUDA(sync_stream(st));
+      // over the non-empty ranges: a key range that is not a power of two
+      // leaves the top ranges empty, which costs nothing
       int64_t mx = 0;
-      for (int d = 0; d < nb; ++d)
-        mx = std::max(mx, (d + 1 < nb ? edges[(size_t)d + 1] : m) - edges[(size_t)d]);
-      stats.radix_balance = (double)mx * (double)nb / (double)std::max<int64_t>(1, m);
+      int used = 0;
+      for (int d = 0; d < nb; ++d) {
+        const int64_t c = (d + 1 < nb ? edges[(size_t)d + 1] : m) - edges[(size_t)d];
+        mx = std::max(mx, c);
+        used += c > 0;
+      }
+      stats.radix_balance = (double)mx * (double)std::max(used, 1) / (double)std::max<int64_t>(1, m);
+      radix_max = mx;
+      // the largest of the ranges' sample counts lies about 3 standard
+      // deviations (Poisson: the square root of the mean) above their mean
+      radix_noise = 3.0 / std::sqrt(std::max(1.0, (double)m / std::max(used, 1)));
     }
     cuts = make_cuts<K>(bnd);
+    std::vector<uint32_t> cnt;
+    tj_status js = sample_counts(cuts, cnt);
+    if (js != TJ_OK) return js;
+    {
+      const int np = (int)cuts.size() + 1;
+      int64_t mx = 0;
+      for (int p2 = 0; p2 < np; ++p2) {
+        const bool single = p2 > 0 && p2 < np - 1 &&
+                            (uint64_t)cuts[(size_t)p2] - (uint64_t)cuts[(size_t)p2 - 1] == 1;
+        if (!single)
+          mx = std::max<int64_t>(mx, (int64_t)cnt[(size_t)p2] + cnt[(size_t)kMaxBins + p2]);
+      }
+      stats.learned_balance = (double)mx * (double)np / (double)std::max<int64_t>(1, m);
+    }
+    // Under a budget, the largest equal-width batch (its sample share of all
+    // rows plus 10%) must also fit one lane's half of the working set: about
+    // 2w + 2 bytes per row (one sort buffer, look-back words).
+    const double radix_rows =
+        1.1 * (double)radix_max / (double)std::max<int64_t>(1, m) * (double)(nr + ns) + 4096.0;
+    const bool radix_fits =
+        budget == 0 || radix_rows * (2.0 * sizeof(K) + 2.0) <= 0.45 * (double)budget;
+    if (o.radix_judge >= 0 && radix_fits &&
+        stats.radix_balance <= o.radix_judge * stats.learned_balance + radix_noise) {
+      radix_route = true;
+      fell_back = true;
+      cuts = radix_cuts<K>(lo, hi, plog);
+      js = sample_counts(cuts, cnt);
+      if (js != TJ_OK) return js;
+    }
     // batch sizes per side estimated from the sample (regions sized ahead of
     // the route pass, so it needs no histogram of its own)
     if (!o.exact_route && cuts.size() <= 255) {
-      std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
-      std::copy(cuts.begin(), cuts.end(), hc.begin());
-      TJ_CUDA(put_small(sb.at<K>(o_scuts), hc.data(), kMaxCuts * sizeof(K), st));
-      TJ_CUDA(cudaMemsetAsync(sb.at<uint32_t>(o_scnt), 0, 2 * kMaxBins * sizeof(uint32_t), st));
-      TJ_CUDA(launch_sample_route_counts<K>(sb.at<K>(o_k), sb.at<K>(o_v), m, m_r, sb.at<K>(o_scuts),
-                                            (int)cuts.size(), sb.at<uint32_t>(o_scnt), st));
-      sample_cnt.assign(2 * (size_t)kMaxBins, 0u);
-      TJ_CUDA(get_small(sample_cnt.data(), sb.at<uint32_t>(o_scnt),
-                              sample_cnt.size() * sizeof(uint32_t), st));
-      TJ_CUDA(sync_stream(st));
+      sample_cnt = cnt;
       sample_m[0] = m_r;
       sample_m[1] = m_s;
+    }
+    // a retry with exact sizes routes equal-width ranges by their digit over
+    // the whole key range: take it from the key statistics
+    if (radix_route && o.exact_route && !range_known) {
+      tj_status rs = key_range<K>(kr, nr, ks, ns, &lo, &hi, st);
+      if (rs != TJ_OK) return rs;
+      range_known = true;
+      cuts = radix_cuts<K>(lo, hi, plog);
     }
   } else {  // TJ_ROUTE_RADIX
     if (!range_known) return set_err(TJ_ERR_INTERNAL, "equal-width batches need the key range");
     router = TJ_ROUTE_RADIX;
-    const int b = bitlen(range_of<K>(lo, hi));
+    radix_route = true;
     int plog = 0;
     while ((2 << plog) <= parts) ++plog;
-    if (b <= plog) {
-      for (uint64_t x = 1; x <= range_of<K>(lo, hi); ++x)
-        cuts.push_back((K)(lo_bits<K>(lo) + x));
-    } else {
-      for (int64_t p = 1; p < ((int64_t)1 << plog); ++p)
-        cuts.push_back((K)(lo_bits<K>(lo) + ((uint64_t)p << (b - plog))));
-    }
+    cuts = radix_cuts<K>(lo, hi, plog);
   }
   while ((int)cuts.size() > kMaxCuts - 1) cuts.pop_back();  // cannot happen for parts <= 1024
   const int ncuts = (int)cuts.size();
@@ -901,7 +1005,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   int rbits = bitlen((uint64_t)ncuts);
   if (rbits == 0) rbits = 1;
   stats.partitions = nparts;
-  {
+  if (!radix_route) {
     int heavy = 0;
     for (int i = 0; i + 1 < ncuts; ++i)
       if ((uint64_t)cuts[(size_t)i + 1] - (uint64_t)cuts[(size_t)i] == 1) ++heavy;
@@ -964,7 +1068,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   // route pass tiles: kItemsRoute rows per thread for narrow batch indices
   // (shared memory still fits three CTAs per SM), kItems otherwise (with 1024
   // batches the 9-row tile measured 1.4x slower)
-  const int ritems = rbits <= kWideBits ? kItemsRoute : kItems;
+  // equal-width batches: batch = (clamp(key) - lo) >> rshift, rbits wide
+  const int rshift = radix_route ? std::max(0, bitlen(krange) - rbits) : 0;
+  const int ritems = radix_route ? (rbits <= kWideBits ? kItemsWide : kItems)
+                                 : (rbits <= kWideBits ? kItemsRoute : kItems);
   const int64_t rtile = (int64_t)kSortThreads * ritems;
   const int64_t lb_per_tile = ((int64_t)1 << rbits) * 4;
   const int64_t route_lb = budget ? std::max<int64_t>((int64_t)budget / 4, 16 * lb_per_tile)
@@ -1062,13 +1169,15 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     x.lo = lo_bits<K>(lo);
     x.passes = 1;
     x.bits[0] = rbits;
+    x.shift[0] = radix_route ? rshift : 0;
+    x.route_hi = lo_bits<K>(hi);
     x.hist_stride = kMaxBins;
     x.hist = stg.at<uint32_t>(o_hist) + (size_t)c * kMaxBins;
     x.src_k[0] = kb + ch.r0;
     x.src_v[0] = vb + ch.r0;
     x.dst_k[0] = ch.side ? stg.at<K>(o_sk) : stg.at<K>(o_rk);
     x.dst_v[0] = ch.side ? stg.at<K>(o_sv) : stg.at<K>(o_rv);
-    x.cuts = stg.at<K>(o_cuts);
+    x.cuts = radix_route ? nullptr : stg.at<K>(o_cuts);  // radix: the digit path
     x.ncuts = ncuts;
     x.route_tab = stg.at<uint16_t>(o_tab);
     x.route_steps = route_steps;
@@ -1167,8 +1276,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     double rows = 0;
     for (int c = g.first; c < g.second; ++c) rows += (double)chunks[(size_t)c].n;
     tr.begin("route", 4.0 * w * rows);
-    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits, true,
-                               d_counters + kMaxPasses, d_err, st, nullptr, ritems, est));
+    TJ_CUDA(launch_onesweep<K>(d_rj + nch + g.first, g.second - g.first, t, 0, rbits,
+                               radix_route ? kModeRadix : kModeCuts, d_counters + kMaxPasses,
+                               d_err, st, nullptr, ritems, est));
     tr.end();
     if (est) {  // where this chunk ended: the next chunk's bases, or the side's end
       const int c = g.first, side = chunks[(size_t)c].side;
@@ -1193,12 +1303,19 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       }
   }
   if (!range_known) {
-    // the smallest key is in the first batch, the largest in the last: their
-    // rows on both sides (about 2 / nparts of the data) give the exact range
+    // the smallest key is in the first non-empty batch, the largest in the
+    // last one (equal-width ranges over a sample's range may leave the top
+    // ranges empty): their rows on both sides (about 2 / nparts of the data)
+    // give the exact range
+    int p_first = 0, p_last = nparts - 1;
+    while (p_first < nparts - 1 && pcount[(size_t)p_first] + pcount[(size_t)nparts + p_first] == 0)
+      ++p_first;
+    while (p_last > p_first && pcount[(size_t)p_last] + pcount[(size_t)nparts + p_last] == 0)
+      --p_last;
     std::vector<RadixJob<K>> rj;
     int64_t rtiles = 0;
     for (int side = 0; side < 2; ++side)
-      for (int p2 : {0, nparts - 1}) {
+      for (int p2 : {p_first, p_last}) {
         const size_t i = (size_t)side * nparts + p2;
         RadixJob<K> x;
         memset(&x, 0, sizeof(x));
@@ -1547,7 +1664,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
   *out_count = h_total;
-  stats.learned = router;
+  stats.learned = router + (fell_back ? 100 : 0);
   if (h_total > cap)
     return set_err(TJ_ERR_CAPACITY, "result has %lld pairs, capacity %lld", (long long)h_total,
                    (long long)cap);

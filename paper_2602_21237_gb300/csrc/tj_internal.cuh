@@ -126,7 +126,17 @@ struct RadixJob {
   // route_end[d]; a row that would not is dropped and the pass reports
   // TJ_ERR_CAPACITY, after which the caller routes again with exact sizes.
   const uint32_t* route_end;
+  // Equal-width batches (route passes in kModeRadix): the batch of a key is
+  // (clamp(key, lo, route_hi) - lo) >> shift[0]; keys outside the range (a
+  // range read off a sample) take the first or the last batch.
+  uint64_t route_hi;
 };
+
+// Kinds of onesweep pass: a sort digit of key - lo, a route by the cut table
+// (batch = number of cuts <= key), a route by equal-width ranges.
+constexpr int kModeSort = 0;
+constexpr int kModeCuts = 1;
+constexpr int kModeRadix = 2;
 
 // Per-array min/max, stored as order-preserving unsigned (key ^ sign bit).
 struct KeyStats {
@@ -222,7 +232,7 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
                               cudaStream_t st);
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                            int pass, int max_bits, bool route, uint32_t* d_tile_counter,
+                            int pass, int max_bits, int mode, uint32_t* d_tile_counter,
                             int* d_err, cudaStream_t st, const int32_t* d_tile_job = nullptr,
                             int items = kItems, bool guard = false);
 

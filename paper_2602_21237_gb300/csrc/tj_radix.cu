@@ -356,20 +356,20 @@ __global__ void k_digit_scan(const RadixJob<K>* __restrict__ jobs, int num_jobs,
 //   src[tile] u16                       input row of each tile-sorted slot
 //   warp counters[kSortWarps][hb] u32   two 16-bit digit counters per word
 //   tile count[bins] u32 | tile exclusive[bins] u32 | global base[bins] i64
-//   [route passes only: cut keys[bins] K | radix index[kRouteBuckets + 8] u16 |
-//    digit of each tile-sorted slot[tile] u8 (<= 256 bins) or u16 |
-//    [end of each batch's region[bins] u32, when the regions are sized ahead]]
+//   [route passes by the cut table: cut keys[bins] K | radix index[kRouteBuckets + 8]
+//    u16 | digit of each tile-sorted slot[tile] u8 (<= 256 bins) or u16]
 //   (a route pass has fewer than bins cuts)
+//   [route passes whose regions are sized ahead: end of each batch's region[bins] u32]
 template <typename K>
-__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, bool route, int tile = kTile,
+__host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, int mode, int tile = kTile,
                                                          bool guard = false) {
   return 2 * sizeof(K) * (size_t)tile + 2 * 16 + sizeof(uint16_t) * (size_t)tile +
          sizeof(uint32_t) * (size_t)kSortWarps * (size_t)((bins + 1) / 2) +
          sizeof(uint32_t) * 2 * (size_t)bins + sizeof(long long) * (size_t)bins +
-         (route ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
-                      (bins <= 256 ? 1 : 2) * (size_t)tile +
-                      (guard ? sizeof(uint32_t) * (size_t)bins : 0)
-                : 0);
+         (mode == kModeCuts ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
+                                  (bins <= 256 ? 1 : 2) * (size_t)tile
+                            : 0) +
+         (mode != kModeSort && guard ? sizeof(uint32_t) * (size_t)bins : 0);
 }
 
 // Exclusive scan of in[0, bins) by a CTA of kSortThreads (bins <= kMaxBins):
@@ -566,9 +566,10 @@ __device__ __forceinline__ void rank_items_or(uint32_t (&dr)[ITEMS], int nv, uin
 //      look-back (bounded wait; on timeout report TJ_ERR_TIMEOUT and go on);
 //   5. walk the slots in order and write each row to its global position:
 //      consecutive slots of one digit go to consecutive addresses.
-// ROUTE: a route pass (digit = batch index from the cut table, pass 0);
-// otherwise a sort pass (digit = bits of key - lo).
-template <typename K, int ITEMS, bool ROUTE>
+// MODE: kModeSort (digit = bits of key - lo), kModeCuts (route pass, pass 0:
+// digit = batch index from the cut table) or kModeRadix (route pass, pass 0:
+// digit = bits of clamp(key, lo, hi) - lo, equal-width batches).
+template <typename K, int ITEMS, int MODE>
 __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     k_onesweep(const RadixJob<K>* __restrict__ jobs, int num_jobs, int64_t total_tiles, int pass,
                uint32_t* __restrict__ tile_counter, int* __restrict__ err,
@@ -613,9 +614,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   uint16_t* s_dig = s_tab + (kRouteBuckets + 8);  // u16 slots; u8 when bins <= 256
   uint8_t* s_dig8 = reinterpret_cast<uint8_t*>(s_dig);
   uint32_t* s_rend =  // end of each batch's region (route passes with sized regions)
-      reinterpret_cast<uint32_t*>(s_dig8 + (bins <= 256 ? 1 : 2) * TILE);
+      MODE == kModeCuts ? reinterpret_cast<uint32_t*>(s_dig8 + (bins <= 256 ? 1 : 2) * TILE)
+                        : reinterpret_cast<uint32_t*>(s_gbase + bins);
   const bool dig8 = bins <= 256;
-  constexpr bool route = ROUTE;
+  constexpr bool route = MODE == kModeCuts;  // digits from the cut table, kept per slot
+  constexpr bool radix = MODE == kModeRadix;
+  const K c_lo = (K)lo, c_hi = (K)J->route_hi;  // clamp of a radix route
   // sort digits within the low 32 bits of key - lo: 32-bit arithmetic
   const bool narrow = shift + nbits <= 32;
   const uint32_t lo32 = (uint32_t)lo;
@@ -624,13 +628,13 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   const K* s_keys = copy_rows_async<K, TILE>(a_keys, J->src_k[pass] + row0, nvalid);
   const K* s_vals = copy_rows_async<K, TILE>(a_vals, J->src_v[pass] + row0, nvalid);
   asm volatile("cp.async.commit_group;" ::: "memory");
-  const bool guard = route && J->route_end != nullptr;
+  const bool guard = MODE != kModeSort && J->route_end != nullptr;
   if (route) {
     for (int i = tid; i < bins; i += kSortThreads) s_cuts[i] = J->cuts[i];
     for (int i = tid; i <= kRouteBuckets; i += kSortThreads) s_tab[i] = J->route_tab[i];
-    if (guard)
-      for (int i = tid; i < bins; i += kSortThreads) s_rend[i] = J->route_end[i];
   }
+  if (guard)
+    for (int i = tid; i < bins; i += kSortThreads) s_rend[i] = J->route_end[i];
   for (int i = tid; i < kSortWarps * hb + bins; i += kSortThreads) s_whist[i] = 0u;
   // lane-mask tables of the ranking (one word per value of the digit's low
   // 7 bits), in the slot-index array, which is not live before step 4
@@ -650,6 +654,13 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     for (int i = 0; i < ITEMS; ++i) {
       const K k = s_keys[wbase + i * 32 + lane];  // padding rows: unused values
       dr[i] = route_idx<K>(k, lo, s_cuts, s_tab, J->route_steps, J->route_shift);
+    }
+  } else if (radix) {
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const K k = s_keys[wbase + i * 32 + lane];
+      const K c = k < c_lo ? c_lo : (c_hi < k ? c_hi : k);
+      dr[i] = narrow ? (((uint32_t)c - lo32) >> shift) & mask : digit_of<K>(c, lo, shift, mask);
     }
   } else if (narrow) {
 #pragma unroll
@@ -807,6 +818,30 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
     }
     return;
   }
+  if (radix) {
+    // digit recomputed from the key (cheaper than keeping it per slot)
+    bool over = false;
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int q = tid + it * kSortThreads;
+      if (q < nvalid) {
+        const int r = s_src[q];
+        const K k = s_keys[r];
+        const K c = k < c_lo ? c_lo : (c_hi < k ? c_hi : k);
+        const uint32_t d =
+            narrow ? (((uint32_t)c - lo32) >> shift) & mask : digit_of<K>(c, lo, shift, mask);
+        const long long g = s_gbase[d] + q;
+        const bool in = !guard || g < (long long)s_rend[d];
+        over |= !in;
+        if (in) {
+          dst_k[g] = k;
+          dst_v[g] = s_vals[r];
+        }
+      }
+    }
+    if (over) atomicCAS(err, 0, (int)TJ_ERR_CAPACITY);
+    return;
+  }
   if (narrow) {
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -901,29 +936,29 @@ cudaError_t launch_digit_scan(const RadixJob<K>* d_jobs, int num_jobs, int passe
   return cudaGetLastError();
 }
 
-template <typename K, bool ROUTE>
+template <typename K, int MODE>
 cudaError_t launch_onesweep_t(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
                               int pass, int max_bits, uint32_t* d_tile_counter, int* d_err,
                               cudaStream_t st, const int32_t* d_tile_job, int items, bool guard) {
   if (items == 4) {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kSortThreads * 4, guard);
-    k_onesweep<K, 4, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, MODE, kSortThreads * 4, guard);
+    k_onesweep<K, 4, MODE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   } else if (items == kItemsRoute && kItemsRoute != kItems && kItemsRoute != kItemsWide) {
-    if constexpr (ROUTE) {  // route passes only
-      const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kTileRoute, guard);
-      k_onesweep<K, kItemsRoute, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+    if constexpr (MODE == kModeCuts) {  // route passes by the cut table only
+      const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, MODE, kTileRoute, guard);
+      k_onesweep<K, kItemsRoute, MODE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
           d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
     } else {
       return cudaErrorInvalidValue;
     }
   } else if (items == kItemsWide) {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kTileWide, guard);
-    k_onesweep<K, kItemsWide, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, MODE, kTileWide, guard);
+    k_onesweep<K, kItemsWide, MODE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   } else {
-    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, ROUTE, kTile, guard);
-    k_onesweep<K, kItems, ROUTE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
+    const size_t smem = onesweep_smem_bytes<K>(1 << max_bits, MODE, kTile, guard);
+    k_onesweep<K, kItems, MODE><<<(unsigned)total_tiles, kSortThreads, smem, st>>>(
         d_jobs, num_jobs, total_tiles, pass, d_tile_counter, d_err, d_tile_job);
   }
   return cudaGetLastError();
@@ -931,38 +966,44 @@ cudaError_t launch_onesweep_t(const RadixJob<K>* d_jobs, int num_jobs, int64_t t
 
 template <typename K>
 cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t total_tiles,
-                            int pass, int max_bits, bool route, uint32_t* d_tile_counter,
+                            int pass, int max_bits, int mode, uint32_t* d_tile_counter,
                             int* d_err, cudaStream_t st, const int32_t* d_tile_job, int items,
                             bool guard) {
   if (total_tiles <= 0) return cudaSuccess;
-  if (route)
-    return launch_onesweep_t<K, true>(d_jobs, num_jobs, total_tiles, pass, max_bits,
-                                      d_tile_counter, d_err, st, d_tile_job, items, guard);
-  return launch_onesweep_t<K, false>(d_jobs, num_jobs, total_tiles, pass, max_bits,
-                                     d_tile_counter, d_err, st, d_tile_job, items, false);
+  if (mode == kModeCuts)
+    return launch_onesweep_t<K, kModeCuts>(d_jobs, num_jobs, total_tiles, pass, max_bits,
+                                           d_tile_counter, d_err, st, d_tile_job, items, guard);
+  if (mode == kModeRadix)
+    return launch_onesweep_t<K, kModeRadix>(d_jobs, num_jobs, total_tiles, pass, max_bits,
+                                            d_tile_counter, d_err, st, d_tile_job, items, guard);
+  return launch_onesweep_t<K, kModeSort>(d_jobs, num_jobs, total_tiles, pass, max_bits,
+                                         d_tile_counter, d_err, st, d_tile_job, items, false);
 }
 
 // Largest dynamic shared memory of every onesweep instantiation (route passes
 // with sized regions need the most).
-template <typename K, int ITEMS, bool ROUTE>
+template <typename K, int ITEMS, int MODE>
 cudaError_t onesweep_attr() {
-  return cudaFuncSetAttribute(k_onesweep<K, ITEMS, ROUTE>,
+  return cudaFuncSetAttribute(k_onesweep<K, ITEMS, MODE>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)onesweep_smem_bytes<K>(kMaxBins, ROUTE, kSortThreads * ITEMS,
-                                                          ROUTE));
+                              (int)onesweep_smem_bytes<K>(kMaxBins, MODE, kSortThreads * ITEMS,
+                                                          MODE != kModeSort));
 }
 
 template <typename K>
 cudaError_t onesweep_attrs() {
   cudaError_t e;
-  if ((e = onesweep_attr<K, kItems, false>()) != cudaSuccess) return e;
-  if ((e = onesweep_attr<K, kItems, true>()) != cudaSuccess) return e;
-  if ((e = onesweep_attr<K, kItemsWide, false>()) != cudaSuccess) return e;
-  if ((e = onesweep_attr<K, kItemsWide, true>()) != cudaSuccess) return e;
-  if ((e = onesweep_attr<K, 4, false>()) != cudaSuccess) return e;
-  if ((e = onesweep_attr<K, 4, true>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItems, kModeSort>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItems, kModeCuts>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItems, kModeRadix>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItemsWide, kModeSort>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItemsWide, kModeCuts>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, kItemsWide, kModeRadix>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, 4, kModeSort>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, 4, kModeCuts>()) != cudaSuccess) return e;
+  if ((e = onesweep_attr<K, 4, kModeRadix>()) != cudaSuccess) return e;
   if (kItemsRoute != kItems && kItemsRoute != kItemsWide)
-    if ((e = onesweep_attr<K, kItemsRoute, true>()) != cudaSuccess) return e;
+    if ((e = onesweep_attr<K, kItemsRoute, kModeCuts>()) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -980,7 +1021,7 @@ cudaError_t radix_init_attributes() {
   template cudaError_t launch_fill_tile_job<K>(const RadixJob<K>*, int, int32_t*, cudaStream_t, \
                                                int);                                            \
   template cudaError_t launch_digit_scan<K>(const RadixJob<K>*, int, int, cudaStream_t);        \
-  template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, bool,    \
+  template cudaError_t launch_onesweep<K>(const RadixJob<K>*, int, int64_t, int, int, int,     \
                                           uint32_t*, int*, cudaStream_t, const int32_t*, int,   \
                                           bool);
 TJ_INSTANTIATE_RADIX(int32_t)

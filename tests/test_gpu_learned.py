@@ -75,10 +75,12 @@ def test_trained_network_gains_over_radix_and_untrained():
     d = [x.to(DEV) for x in (kr, ir, ks, is_)]
     api.join_inner(*d, router="radix", partitions=256)
     radix = api.stats()["balance"]
-    api.join_inner(*d, router="mlp", partitions=256, mlp_steps=1)
+    # the networks themselves (radix_judge < 0: no fallback to equal ranges)
+    api.join_inner(*d, router="mlp", partitions=256, mlp_steps=1, radix_judge=-1)
     untrained = api.stats()["balance"]
-    api.join_inner(*d, router="mlp", partitions=256)
+    api.join_inner(*d, router="mlp", partitions=256, radix_judge=-1)
     trained = api.stats()["balance"]
+    assert api.stats()["learned"] == api.ROUTERS["mlp"]
     assert trained < radix / 3, (trained, radix)
     assert trained < untrained, (trained, untrained)
 

@@ -26,7 +26,36 @@ def test_router_unbounded(router, dtype):
     kr, ir, ks, is_ = datagen.uniform_pair(200_000, 300_003, -50_000, 150_000, 31, dtype)
     st = check(kr, ir, ks, is_, router=router)
     assert st["partitions"] > 1 and st["groups"] == 1
+    # uniform keys: the radix judge replaces the piecewise-linear model
+    assert st["learned"] == (api.ROUTERS["pla"] + 100 if router == "pla" else api.ROUTERS["radix"])
+    st = check(kr, ir, ks, is_, router=router, radix_judge=-1)  # the cut table routes
     assert st["learned"] == api.ROUTERS[router]
+
+
+def test_radix_judge_replaces_a_model_no_better_than_equal_ranges():
+    # uniform keys: equal-width ranges balance as well as the PLA; an MLP
+    # trained for one step fits nothing.  Both fall back to radix (+100), and
+    # the result is the same.
+    kr, ir, ks, is_ = datagen.uniform_pair(150_000, 250_007, -(1 << 40), 1 << 40, 37, torch.int64)
+    for router in ("pla", "mlp"):
+        st = check(kr, ir, ks, is_, router=router, partitions=128, mlp_steps=1)
+        assert st["learned"] == api.ROUTERS[router] + 100
+        m = (150_000 + 250_007) // 100  # the 1% sample; 128 ranges, 3-sigma allowance
+        assert st["radix_balance"] <= 1.25 * st["learned_balance"] + 3 / np.sqrt(m / 128)
+        assert st["heavy_keys"] == 0 and st["partitions"] == 128
+
+
+def test_radix_judge_keeps_a_model_that_balances_better():
+    # log-normal clusters: equal-width ranges put most rows in a few batches
+    kr, ir = datagen.lognormal_mix(1 << 17, 53)
+    ks, is_ = datagen.lognormal_mix(1 << 17, 54)
+    st = check(kr, ir, ks, is_, router="pla", partitions=128)
+    assert st["learned"] == api.ROUTERS["pla"]
+    assert st["radix_balance"] > 1.25 * st["learned_balance"]
+    # heavy keys isolated by the model's cuts do not count against it
+    kr, ir, ks, is_ = datagen.fk_zipf(100_000, 400_000, 1.2, 55)
+    st = check(kr, ir, ks, is_, router="pla", partitions=128)
+    assert st["learned"] == api.ROUTERS["pla"] and st["heavy_keys"] >= 1
 
 
 @pytest.mark.parametrize("router", ["radix", "pla"])
@@ -72,7 +101,7 @@ def test_pla_budgeted_fk_zipf(s):
 def test_auto_switches_to_partitioned_under_budget():
     kr, ir, ks, is_ = datagen.fk_zipf(300_000, 900_000, 0.8, 43)
     st = check(kr, ir, ks, is_, mem_budget_bytes=8 << 20)
-    assert st["learned"] == api.ROUTERS["pla"] and st["groups"] > 1
+    assert st["learned"] % 100 == api.ROUTERS["pla"] and st["groups"] > 1
     assert st["scratch_peak"] <= 8 << 20
     st = check(kr, ir, ks, is_)  # unbounded: single pass
     assert st["partitions"] == 0
@@ -176,3 +205,17 @@ def test_keys_outside_the_sample_range_without_key_statistics(dtype):
                sample_stride=stride, seed=seed)
     assert st["groups"] > 1 and st["scratch_peak"] <= 4 << 20
     assert st["key_bits"] == (64 if dtype == torch.int64 else 32)
+
+
+def test_radix_judge_on_a_sample_range_plans_batches_by_their_width():
+    # AUTO under a budget routes by the sample's range (no statistics pass);
+    # the judge takes equal-width ranges for these uniform keys, and a key
+    # range that is not a power of two leaves the top ranges empty: the exact
+    # range must come from the last non-empty batch, so every batch is sorted
+    # over its own 13 bits (two passes), not over 64
+    kr, ir, ks, is_ = datagen.fk_zipf(600_000, 2_400_000, 0.0, 57)
+    st = check(kr, ir, ks, is_, mem_budget_bytes=16 << 20)
+    assert st["learned"] == api.ROUTERS["pla"] + 100
+    assert st["partitions"] == 128 and st["groups"] > 1
+    assert st["radix_passes"] == 2 and st["digit_bits"] <= 7
+    assert st["key_bits"] == 20  # keys 0 .. 599_999
