@@ -81,6 +81,8 @@ typedef struct {
                               key (their significant bits fit it), 0 if sorted per column */
   double learned_balance;  /* the learned model's batches on the sample: largest / mean,
                               batches of a single key left out (0 if no model) */
+  int32_t fused_batches;   /* batches joined by the partition-resident phase */
+  int32_t reserved;
 } tj_stats;
 
 /*
@@ -102,7 +104,8 @@ typedef enum {
 
 typedef struct {
   int32_t router;        /* tj_router */
-  int32_t partitions;    /* key-range batches requested, 2..1024 (0 = 128) */
+  int32_t partitions;    /* key-range batches requested, 2..1024 (0 = from the key range:
+                            256 for ranges of 27..30 bits, else 128) */
   int32_t sample_stride; /* sample one row in this many (0 = 100, a 1% sample) */
   int32_t pla_segments;  /* segments of the piecewise-linear CDF (0 = 4096) */
   int32_t mlp_steps;     /* Adam steps of the MLP (0 = 600) */
@@ -112,8 +115,15 @@ typedef struct {
   float radix_judge;     /* equal-width ranges replace a learned model whose sampled
                             balance is not better than theirs by more than this
                             factor (0 = 1.25; negative = never) */
-  int32_t reserved;      /* 0 */
+  int32_t flags;         /* TJ_JOIN_* bits (0 = defaults) */
 } tj_join_opts;
+
+/* tj_join_opts.flags: sort every batch of the partitioned join by LSD passes
+ * and align it with the sorted-merge join, instead of the partition-resident
+ * phase (the default for batches whose key range spans 10 to 20 bits: one
+ * MSD pass into sub-batches of 1024 key values, each sorted and aligned on
+ * chip).  The result is the same. */
+#define TJ_JOIN_NO_FUSED 1
 
 /*
  * Inner equi-join (Sec. 4.1): J = { (r.id, s.id) : r.key == s.key }.

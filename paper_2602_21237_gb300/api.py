@@ -21,6 +21,7 @@ _lib = None
 TJ_OK, TJ_ERR_INVALID, TJ_ERR_BUDGET, TJ_ERR_CAPACITY, TJ_ERR_CUDA, TJ_ERR_TIMEOUT, \
     TJ_ERR_INTERNAL = range(7)
 TJ_I32, TJ_I64 = 0, 1
+TJ_JOIN_NO_FUSED = 1
 
 
 class TjError(RuntimeError):
@@ -41,7 +42,8 @@ class _Stats(ctypes.Structure):
                 ("balance", ctypes.c_double), ("radix_balance", ctypes.c_double),
                 ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("packed_keys", ctypes.c_int32),
-                ("learned_balance", ctypes.c_double)]
+                ("learned_balance", ctypes.c_double), ("fused_batches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):
@@ -49,7 +51,7 @@ class _Opts(ctypes.Structure):
                 ("sample_stride", ctypes.c_int32), ("pla_segments", ctypes.c_int32),
                 ("mlp_steps", ctypes.c_int32), ("mlp_batch", ctypes.c_int32),
                 ("mlp_lr", ctypes.c_float), ("seed", ctypes.c_uint64),
-                ("radix_judge", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("radix_judge", ctypes.c_float), ("flags", ctypes.c_int32)]
 
 
 class _Column(ctypes.Structure):
@@ -227,7 +229,7 @@ def join_inner(keys_r, ids_r, keys_s, ids_s, mem_budget_bytes: int = 0, out=None
                stream=None, router: str | None = None, partitions: int = 0,
                sample_stride: int = 0, pla_segments: int = 0, mlp_steps: int = 0,
                mlp_batch: int = 0, mlp_lr: float = 0.0, seed: int = 0,
-               radix_judge: float = 0.0):
+               radix_judge: float = 0.0, fused: bool = True):
     """Inner equi-join (paper Sec. 4.1) -> (count, 2) tensor of (r_id, s_id)
     ordered by key, then S position, then R position.
 
@@ -236,13 +238,14 @@ def join_inner(keys_r, ids_r, keys_s, ids_s, mem_budget_bytes: int = 0, out=None
     larger, the join is run again into a buffer of the exact size.  `router`
     ('auto', 'single', 'radix', 'pla', 'mlp') and the other keywords fill
     tj_join_opts (0 = library default; radix_judge < 0 keeps a learned model
-    whatever the radix judge finds)."""
+    whatever the radix judge finds; fused=False sorts every batch by LSD
+    passes instead of the partition-resident phase)."""
     opts = None
     if router is not None or partitions or sample_stride or pla_segments or mlp_steps or \
-            mlp_batch or mlp_lr or seed or radix_judge:
+            mlp_batch or mlp_lr or seed or radix_judge or not fused:
         opts = _Opts(ROUTERS[router or "auto"], int(partitions), int(sample_stride),
                      int(pla_segments), int(mlp_steps), int(mlp_batch), float(mlp_lr), int(seed),
-                     float(radix_judge), 0)
+                     float(radix_judge), 0 if fused else TJ_JOIN_NO_FUSED)
     lib = _load()
     dev = keys_r.device
     dt = _dt(keys_r)

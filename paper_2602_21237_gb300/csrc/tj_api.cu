@@ -188,6 +188,7 @@ tj_status ensure_device() {
   TJ_CUDA(radix_init_attributes());
   TJ_CUDA(join_init_attributes());
   TJ_CUDA(mlp_init_attributes());
+  TJ_CUDA(fused_init_attributes());
   g_inited[dev] = true;
   return TJ_OK;
 }
@@ -510,7 +511,7 @@ void set_job_buffers(RadixJob<K>& j, const K* in_k, const K* in_v, K* ak, K* av,
 // ---- inner join -------------------------------------------------------------------
 struct Opts {
   int router = TJ_ROUTE_AUTO;
-  int partitions = 128;
+  int partitions = 0;  // 0: chosen from the key range (auto_parts)
   int stride = 100;
   int segments = 4096;
   int mlp_steps = 600;
@@ -518,6 +519,7 @@ struct Opts {
   float mlp_lr = 3e-3f;
   uint64_t seed = 20260221ull;
   double radix_judge = 1.25;  // < 0: the learned model is always kept
+  bool fused = true;          // the partition-resident phase for narrow batches
   bool exact_route = false;  // size the batch regions by a histogram, not the sample
 };
 
@@ -537,6 +539,7 @@ Opts make_opts(const tj_join_opts* o) {
   if (o->mlp_lr > 0.f) x.mlp_lr = o->mlp_lr;
   if (o->seed) x.seed = o->seed;
   if (o->radix_judge != 0.f) x.radix_judge = o->radix_judge;
+  x.fused = (o->flags & TJ_JOIN_NO_FUSED) == 0;
   return x;
 }
 
@@ -754,6 +757,17 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
 //    buffers, histograms, look-back, join state) fits the budget, and every
 //    group is sorted and aligned by one batched launch sequence, its output
 //    written after the previous group's (device-side running offset).
+// Batches of a partitioned join when the caller leaves the number open: the
+// partition-resident phase joins batches of at most kFKeyBits + kFMaxMsdBits
+// key bits and costs less with an MSD digit of at most 9 bits (measured: a
+// 10-bit pass takes 1.45x a 9-bit one); 256 batches give that for key ranges
+// of 27 to 30 bits, 128 (fewer, larger batches, best for the LSD path: 128
+// and 256 batches measured within 3% there) do for narrower ranges, and wider
+// ones are sorted by LSD passes anyway.
+int auto_parts(int key_bits) {
+  return key_bits >= kFKeyBits + 9 + 8 && key_bits <= kFKeyBits + kFMaxMsdBits + 8 ? 256 : 128;
+}
+
 // Cuts of 2^plog equal-width batches over [lo, hi]: lo + p 2^(b - plog), b =
 // significant bits of hi - lo (every key of the range its own batch when
 // b <= plog).  The batch of a key is then (key - lo) >> (b - plog).
@@ -823,7 +837,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
                          cudaStream_t st) {
   const double w = (double)sizeof(K);
   const int maxd = max_digit_bits<K>();
-  int parts = std::max(2, std::min(o.partitions, kMaxCuts));
+  // batches: as asked, else from the key range (the sample's when the range
+  // is not known yet)
+  int parts = o.partitions > 0 ? std::max(2, std::min(o.partitions, kMaxCuts))
+                               : (range_known ? auto_parts(bitlen(range_of<K>(lo, hi))) : 128);
   std::vector<K> cuts;
   int router = o.router;
   std::vector<uint32_t> sample_cnt;  // per side and batch, when regions are sized by the sample
@@ -837,10 +854,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     const int64_t off_s = (int64_t)((o.seed * 0xBF58476D1CE4E5B9ull) >> 33) % std::min<int64_t>(stride, ns);
     const int64_t m_r = (nr - off_r + stride - 1) / stride, m_s = (ns - off_s + stride - 1) / stride;
     const int64_t m = m_r + m_s;
-    int G = std::max(o.segments, parts);
-    G = (G / parts) * parts;  // boundaries fall on knots
     Carve c;
-    const size_t o_k = c.add<K>((size_t)m), o_v = c.add<K>((size_t)m), o_b = c.add<K>((size_t)parts);
+    const size_t o_k = c.add<K>((size_t)m), o_v = c.add<K>((size_t)m), o_b = c.add<K>(kMaxCuts);
     const size_t o_th = c.add<float>(kMlpParams), o_tab = c.add<float>(kMlpTable + 1);
     const size_t o_edges = c.add<int64_t>(kMaxCuts + 2);
     const size_t o_scuts = c.add<K>(kMaxCuts), o_scnt = c.add<uint32_t>(2 * kMaxBins);
@@ -856,7 +871,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       TJ_CUDA(get_small(&lo, sb.at<K>(o_k), sizeof(K), st));
       TJ_CUDA(get_small(&hi, sb.at<K>(o_k) + (m - 1), sizeof(K), st));
       TJ_CUDA(sync_stream(st));
+      if (o.partitions <= 0) parts = auto_parts(bitlen(range_of<K>(lo, hi)));
     }
+    int G = std::max(o.segments, parts);
+    G = (G / parts) * parts;  // boundaries fall on knots
     std::vector<K> bnd((size_t)(parts - 1));
     if (router == TJ_ROUTE_PLA) {
       // boundaries of the piecewise-linear CDF: knots t_{(G / parts) p}
@@ -1354,19 +1372,38 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     stats.balance = (double)maxrows * nparts / (double)std::max<int64_t>(1, nr + ns);
   }
 
-  // ---- 4. batches and groups ----
+  // ---- 4. batches: a plan per batch ----
+  // A batch whose key range spans kFKeyBits to kFKeyBits + kFMaxMsdBits bits
+  // is joined by the partition-resident phase: one MSD pass cuts it into
+  // sub-batches of kFKeys key values, which are sorted and aligned on chip
+  // (tj_fused.cu) -- unless one of them holds more R rows than fit on chip
+  // (many duplicate R keys), which the key counts show after the MSD
+  // histogram.  Other batches are sorted by LSD passes and aligned by k_join.
   struct Part {
     int64_t r0, nr, s0, ns;
     K lo, hi;
-    Plan plan;
-    int64_t ws;  // working set without the look-back words
-    int64_t lb;  // look-back bytes of one pass
-    int np;      // passes (at least 1)
+    Plan plan;    // LSD plan (or, fused, the MSD pass: its only digit)
+    Plan lsd;     // the LSD plan, kept for a fused batch that falls back
+    bool fused;
+    int m;        // fused: MSD digit bits
+    int64_t items, kbt, kbs;  // fused: items, multi-tile tiles and sub-batches
+    int64_t ws;   // working set without the look-back words
+    int64_t lb;   // look-back bytes of one pass
+    int np;       // passes (at least 1)
+    size_t hist_at;  // its histograms in the tables block (R side, then S side)
+    int fj;          // fused: index of its FusedJob
   };
   std::vector<Part> P;
   size_t hist_words_all = 0;
+  int n_fused = 0;
+  // histogram words of one side of a batch: room for either plan's (the R
+  // side's at hist_at, the S side's after it)
+  auto hist_half = [](const Part& q) {
+    return std::max((size_t)std::max(1, q.lsd.passes) << q.lsd.max_bits,
+                    q.fj >= 0 ? (size_t)1 << q.m : (size_t)0);
+  };
   for (int j = 0; j < nparts; ++j) {
-    Part q;
+    Part q = {};
     q.nr = pcount[(size_t)j];
     q.ns = pcount[(size_t)nparts + j];
     q.r0 = rstart[(size_t)j];
@@ -1374,26 +1411,69 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     if (q.nr == 0 || q.ns == 0) continue;
     q.lo = j == 0 ? lo : std::max(lo, cuts[(size_t)j - 1]);
     q.hi = j == ncuts ? hi : std::min(hi, (K)(cuts[(size_t)j] - 1));
-    q.plan = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd, -1, q.nr + q.ns);
-    // one sort buffer (the passes alternate between it and the batch's routed
-    // copy), one look-back region per pass (a group keeps as many as its
-    // deepest batch), join tile state (tile descriptors, chained words, tile map), the
-    // radix tile map, alignment
-    const int np = std::max(1, q.plan.passes);
-    const int64_t bins = (int64_t)1 << q.plan.max_bits;
-    const int64_t rtiles = ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile);
-    q.lb = rtiles * bins * 4;
-    q.np = np;
-    q.ws = (int64_t)std::min(q.plan.passes, 1) * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
-           ceil_div(q.ns, kJTile) * (int64_t)(sizeof(JTile<K>) + 12) + rtiles * 4 + 4096;
-    hist_words_all += 2 * (size_t)np * (size_t)bins;
+    q.lsd = make_plan(lo_bits<K>(q.lo), range_of<K>(q.lo, q.hi), false, maxd, -1, q.nr + q.ns);
+    const int bits = q.lsd.key_bits;
+    // (narrower batches -- a heavy key's own batch above all -- need no sort
+    // or few passes: k_join aligns them directly)
+    q.fused = o.fused && bits >= kFKeyBits && bits <= kFKeyBits + kFMaxMsdBits;
+    q.m = q.fused ? std::max(0, bits - kFKeyBits) : 0;
+    q.fj = q.fused ? n_fused++ : -1;
+    if (q.fused) {
+      q.plan = Plan();
+      q.plan.lo = lo_bits<K>(q.lo);
+      q.plan.key_bits = bits;
+      if (q.m > 0) {
+        q.plan.passes = 1;
+        q.plan.shift[0] = kFKeyBits;
+        q.plan.bits[0] = q.m;
+        q.plan.max_bits = q.m;
+      }
+    } else {
+      q.plan = q.lsd;
+    }
+    q.hist_at = hist_words_all;
+    hist_words_all += 2 * hist_half(q);
     P.push_back(q);
   }
-  // tables: histogram-pass jobs and group jobs (radix), join jobs, histograms,
-  // output bases (one more than groups; at most one group per batch)
+  // working set of a batch on the LSD path: one sort buffer (the passes
+  // alternate between it and the batch's routed copy), one look-back region
+  // per pass (a group keeps as many as its deepest batch), join tile state
+  // (tile descriptors, chained words, tile map), the radix tile map
+  auto plan_lsd = [&](Part& q) {
+    q.fused = false;
+    q.plan = q.lsd;
+    const int64_t bins = (int64_t)1 << q.plan.max_bits;
+    const int64_t rtiles = ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile);
+    q.np = std::max(1, q.plan.passes);
+    q.lb = rtiles * bins * 4;
+    q.ws = (int64_t)std::min(q.plan.passes, 1) * (q.nr + q.ns) * 2 * (int64_t)sizeof(K) +
+           ceil_div(q.ns, kJTile) * (int64_t)(sizeof(JTile<K>) + 12) + rtiles * 4 + 4096;
+  };
+  // ... and on the fused path: the MSD pass's output, its look-back words and
+  // tile map, the items (descriptor and chained word), the multi-tile count
+  // vectors and totals, the job descriptor
+  auto plan_fused = [&](Part& q) {
+    const int64_t rtiles = ceil_div(q.nr, kTile) + ceil_div(q.ns, kTile);
+    q.np = 1;
+    q.lb = q.m > 0 ? rtiles * ((int64_t)1 << q.m) * 4 : 0;
+    // (+ the layout's minimum of one count vector and one totals slot and its
+    // 256-byte alignment of each of about a dozen arrays)
+    q.ws = (q.m > 0 ? (q.nr + q.ns) * 2 * (int64_t)sizeof(K) + rtiles * 4 : 0) +
+           q.items * (int64_t)(sizeof(FItem) + 8) +
+           (q.kbt + q.kbs + 2) * (int64_t)kFKeys * 4 + (int64_t)sizeof(FusedJob<K>) + 8192;
+  };
+  for (auto& q : P)
+    if (!q.fused) plan_lsd(q);
+  // tables: histogram-pass jobs and group jobs (radix), join jobs, fused jobs
+  // and their counts, histograms, output bases (one more than groups; at most
+  // one group per batch)
   const size_t rj1 = P.size() * 2 * sizeof(RadixJob<K>);
   const size_t t_rj = 0, t_rjh = t_rj + rj1, t_jj = t_rjh + rj1;
-  const size_t t_hist = (t_jj + P.size() * sizeof(JoinJob<K>) + 255) & ~(size_t)255;
+  const size_t t_fj = (t_jj + P.size() * sizeof(JoinJob<K>) + 255) & ~(size_t)255;
+  const size_t t_info = (t_fj + std::max<size_t>(1, (size_t)n_fused) * sizeof(FusedJob<K>) + 255) &
+                        ~(size_t)255;
+  const size_t t_hist = (t_info + std::max<size_t>(1, (size_t)n_fused) * 4 * sizeof(int64_t) + 255) &
+                        ~(size_t)255;
   const size_t t_base = (t_hist + hist_words_all * 4 + 255) & ~(size_t)255;
   const size_t tbl_bytes = t_base + (P.size() + 1) * sizeof(int64_t);
   const int64_t fixed = control + (int64_t)tbl_bytes + 4096;
@@ -1401,9 +1481,121 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   if (room <= 0)
     return set_err(TJ_ERR_BUDGET, "budget %zu below the join's tables and control (%lld bytes)",
                    budget, (long long)fixed);
-  // Consecutive batches form a group while the group's working set fits `lim`.
-  // When the budget needs more than one group, groups are planned against half
-  // of it and alternate between two streams (lanes), each with its own half.
+  rlb.release();
+  Block tbl;
+  TJ_CUDA(tbl.alloc(tbl_bytes + 256, st));
+  uint32_t* d_hist_all = reinterpret_cast<uint32_t*>(tbl.p + t_hist);
+  RadixJob<K>* d_rj_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rj);
+  RadixJob<K>* d_rjh_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rjh);
+  JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + t_jj);
+  FusedJob<K>* d_fj_all = reinterpret_cast<FusedJob<K>*>(tbl.p + t_fj);
+  int64_t* d_info = reinterpret_cast<int64_t*>(tbl.p + t_info);
+  int64_t* d_gbase = reinterpret_cast<int64_t*>(tbl.p + t_base);
+  TJ_CUDA(cudaMemsetAsync(tbl.p + t_hist, 0, tbl_bytes - t_hist, st));
+
+  // ---- 5. digit histograms of every batch in one launch ----
+  // (the routed copies: LSD digits, or the MSD digit of a fused batch)
+  auto batch_side = [&](const Part& q, int side, K** k0, K** v0) {
+    *k0 = side ? stg.at<K>(o_sk) + q.s0 : stg.at<K>(o_rk) + q.r0;
+    *v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
+    return side ? q.ns : q.nr;
+  };
+  auto hist_jobs = [&](bool fused_only_lsd, std::vector<RadixJob<K>>& out, int64_t* tiles) {
+    out.clear();
+    *tiles = 0;
+    for (auto& q : P) {
+      if (fused_only_lsd && (q.fused || q.fj < 0)) continue;  // demoted fused batches only
+      if (q.plan.passes == 0) continue;
+      for (int side = 0; side < 2; ++side) {
+        RadixJob<K> x;
+        memset(&x, 0, sizeof(x));
+        K* k0;
+        K* v0;
+        x.n = batch_side(q, side, &k0, &v0);
+        x.keys = k0;
+        set_job_plan(x, q.plan);
+        x.hist_stride = 1 << q.plan.max_bits;
+        x.hist = d_hist_all + q.hist_at + (side ? hist_half(q) : 0);
+        x.tile0 = *tiles;
+        *tiles += ceil_div(x.n, kTile);
+        out.push_back(x);
+      }
+    }
+  };
+  int maxp = 0;
+  for (auto& q : P) maxp = std::max(maxp, q.plan.passes);
+  std::vector<RadixJob<K>> all_rjh;
+  int64_t htiles = 0;
+  hist_jobs(false, all_rjh, &htiles);
+  if (!all_rjh.empty()) {
+    TJ_CUDA(put_small(d_rjh_all, all_rjh.data(), all_rjh.size() * sizeof(RadixJob<K>), st));
+    tr.begin("histogram", w * (double)(nr + ns));
+    TJ_CUDA(launch_histogram<K>(d_rjh_all, (int)all_rjh.size(), htiles, st));
+    tr.end();
+    TJ_CUDA(launch_digit_scan<K>(d_rjh_all, (int)all_rjh.size(), maxp, st));
+  }
+  // fused batches: items and sub-batch sizes from the MSD counts (one read)
+  std::vector<FusedJob<K>> fj((size_t)n_fused);
+  if (n_fused > 0) {
+    for (auto& q : P) {
+      if (q.fj < 0) continue;
+      FusedJob<K>& f = fj[(size_t)q.fj];
+      memset(&f, 0, sizeof(f));
+      f.hr = q.m > 0 ? d_hist_all + q.hist_at : nullptr;
+      f.hs = q.m > 0 ? d_hist_all + q.hist_at + hist_half(q) : nullptr;
+      f.nr = q.nr;
+      f.ns = q.ns;
+      f.lo = lo_bits<K>(q.lo);
+      f.m = q.m;
+    }
+    TJ_CUDA(put_small(d_fj_all, fj.data(), fj.size() * sizeof(FusedJob<K>), st));
+    TJ_CUDA(launch_fused_info<K>(d_fj_all, n_fused, d_info, st));
+    std::vector<int64_t> info((size_t)n_fused * 4);
+    TJ_CUDA(get_small(info.data(), d_info, info.size() * sizeof(int64_t), st));
+    TJ_CUDA(sync_stream(st));
+    bool demoted = false;
+    for (auto& q : P) {
+      if (q.fj < 0) continue;
+      const int64_t* in = info.data() + (size_t)q.fj * 4;
+      if (in[3] > kFCapR) {  // an R sub-batch does not fit on chip: LSD path
+        plan_lsd(q);
+        demoted = true;
+        continue;
+      }
+      q.items = in[0];
+      q.kbt = in[1];
+      q.kbs = in[2];
+      plan_fused(q);
+    }
+    if (demoted) {  // their LSD digit histograms
+      std::vector<RadixJob<K>> dj;
+      int64_t dt = 0;
+      hist_jobs(true, dj, &dt);
+      for (auto& q : P)
+        if (!q.fused && q.fj >= 0)
+          TJ_CUDA(cudaMemsetAsync(d_hist_all + q.hist_at, 0, 2 * hist_half(q) * 4, st));
+      if (!dj.empty()) {
+        RadixJob<K>* d_dj = d_rj_all;  // the group jobs are written later
+        int dmaxp = 0;
+        for (auto& q : P)
+          if (!q.fused && q.fj >= 0) dmaxp = std::max(dmaxp, q.plan.passes);
+        TJ_CUDA(put_small(d_dj, dj.data(), dj.size() * sizeof(RadixJob<K>), st));
+        TJ_CUDA(launch_histogram<K>(d_dj, (int)dj.size(), dt, st));
+        TJ_CUDA(launch_digit_scan<K>(d_dj, (int)dj.size(), dmaxp, st));
+        maxp = std::max(maxp, dmaxp);
+      }
+    }
+  }
+  {
+    int nf = 0;
+    for (auto& q : P) nf += q.fused;
+    stats.fused_batches = nf;
+  }
+
+  // ---- 6. groups: consecutive batches of one kind whose working set fits ----
+  // When the budget needs more than one group, groups are planned against
+  // half of it and alternate between two streams (lanes), each with its own
+  // half.
   std::vector<std::pair<size_t, size_t>> groups;  // [first, last) into P
   int64_t ws_max = 0;
   auto need_of = [&](size_t i) { return P[i].ws + P[i].lb * P[i].np; };
@@ -1415,7 +1607,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       size_t j = i;
       int64_t ws = 0, lb = 0, acc = 0;
       int np = 1;
-      while (j < P.size()) {
+      while (j < P.size() && P[j].fused == P[i].fused) {
         const int np2 = std::max(np, P[j].np);
         const int64_t acc2 = ws + P[j].ws + (lb + P[j].lb) * np2;
         if (acc2 > lim) break;
@@ -1452,34 +1644,35 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   const size_t lane_bytes = ((size_t)std::max<int64_t>(ws_max, 256) + 255) & ~(size_t)255;
   const int64_t wk_bytes = (int64_t)(lane_bytes * (size_t)lanes);
   stats.scratch_peak = control + std::max<int64_t>(lb_max, wk_bytes + (int64_t)tbl_bytes);
-  rlb.release();
   Block wk;
   TJ_CUDA(wk.alloc((size_t)wk_bytes, st));
 
-  // ---- 5. group plans: job tables, digit histograms of every batch in one launch ----
-  // Group layout in the working block: the sort buffer of every batch | one
-  // zeroed region (tile counters, one look-back region per pass, chained join
-  // words) | join tile descriptors | tile maps.
+  // ---- 7. group plans: job tables ----
+  // Group layout in the working block: LSD groups: the sort buffer of every
+  // batch | one zeroed region (tile counters, one look-back region per pass,
+  // chained join words) | join tile descriptors | tile maps.  Fused groups:
+  // the MSD output of every batch | one zeroed region (tile and item
+  // counters, MSD look-back, chained item words, count vectors, totals) |
+  // items | tile map.
   struct GroupPlan {
+    bool fused;
     size_t first, nj;
-    size_t rj_at, jj_at;  // offsets into the uploaded tables
+    size_t rj_at, jj_at, fj_at;  // offsets into the uploaded tables
     size_t o_zero, zero_bytes, o_cnt, o_lb, o_jt, o_jlb, o_tmap, o_jmap;
+    size_t o_items, o_ilb, o_kbl, o_kbt;
     size_t lb_words;
-    int64_t tiles, jtiles;
-    int P, maxbits, items, lane;
-    double rows, prow[kMaxPasses];
+    int64_t tiles, jtiles, items;
+    int nrj;  // radix jobs of the group
+    bool any_multi;
+    int P, maxbits, items_per_thread, lane;
+    double rows, msd_rows, prow[kMaxPasses];
   };
-  Block tbl;
-  TJ_CUDA(tbl.alloc(tbl_bytes + 256, st));
-  uint32_t* d_hist_all = reinterpret_cast<uint32_t*>(tbl.p + t_hist);
-  std::vector<RadixJob<K>> all_rj, all_rjh;
+  std::vector<RadixJob<K>> all_rj;
   std::vector<JoinJob<K>> all_jj;
   std::vector<GroupPlan> plans;
-  int maxp = 0;
-  size_t hist_at = 0;
-  int64_t htiles = 0;
   for (auto& g : groups) {
     GroupPlan gp = {};
+    gp.fused = P[g.first].fused;
     gp.lane = (int)(plans.size() % (size_t)lanes);
     const View lw{wk.p + (size_t)gp.lane * lane_bytes};  // the group's lane of wk
     gp.first = g.first;
@@ -1498,109 +1691,138 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     }
     // onesweep tile of the group: the wider one when every digit is narrow
     for (size_t i = 0; i < nj; ++i) gp.maxbits = std::max(gp.maxbits, P[g.first + i].plan.max_bits);
-    gp.items = gp.maxbits <= kWideBits ? kItemsWide : kItems;
-    const int64_t otile = (int64_t)kSortThreads * gp.items;
+    gp.items_per_thread = gp.maxbits <= kWideBits ? kItemsWide : kItems;
+    const int64_t otile = (int64_t)kSortThreads * gp.items_per_thread;
     std::vector<size_t> lb_at(nj * 2);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
       const size_t bins = (size_t)1 << q.plan.max_bits;
       for (int side = 0; side < 2; ++side) {
         lb_at[i * 2 + side] = gp.lb_words;
-        gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, otile) * bins;
+        if (q.plan.passes > 0) gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, otile) * bins;
       }
       gp.P = std::max(gp.P, q.plan.passes);
       for (int p = 0; p < q.plan.passes; ++p) gp.prow[p] += (double)(q.nr + q.ns);
+      gp.rows += (double)(q.nr + q.ns);
+      if (gp.fused) {
+        if (q.plan.passes > 0) gp.msd_rows += (double)(q.nr + q.ns);
+        gp.items += q.items;
+        gp.any_multi |= q.kbt > 0;
+      }
     }
-    for (size_t i = 0; i < nj; ++i) gp.jtiles += ceil_div(P[g.first + i].ns, kJTile);
-    gp.o_cnt = gc.add<uint32_t>(kMaxPasses + 1);
+    if (!gp.fused)
+      for (size_t i = 0; i < nj; ++i) gp.jtiles += ceil_div(P[g.first + i].ns, kJTile);
+    gp.o_cnt = gc.add<uint32_t>(kMaxPasses + 2);  // tile counters, item counter
     gp.o_zero = gp.o_cnt;
     gp.o_lb = gc.add<uint32_t>(std::max<size_t>(gp.lb_words, 1) * (size_t)std::max(1, gp.P));
-    gp.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
+    if (gp.fused) {
+      int64_t kbt = 0, kbs = 0;
+      for (size_t i = 0; i < nj; ++i) {
+        kbt += P[g.first + i].kbt;
+        kbs += P[g.first + i].kbs;
+      }
+      gp.o_ilb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.items, 1));
+      gp.o_kbl = gc.add<uint32_t>((size_t)std::max<int64_t>(kbt, 1) * kFKeys);
+      gp.o_kbt = gc.add<uint32_t>((size_t)std::max<int64_t>(kbs, 1) * kFKeys);
+    } else {
+      gp.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
+    }
     gp.zero_bytes = gc.off - gp.o_zero;
     gp.rj_at = all_rj.size();
     gp.jj_at = all_jj.size();
-    int64_t jt = 0;
+    gp.fj_at = gp.fused ? (size_t)P[g.first].fj : 0;
+    int64_t jt = 0, item0 = 0, kbt0 = 0, kbs0 = 0;
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
-      gp.rows += (double)(q.nr + q.ns);
       const K* res[4];
       for (int side = 0; side < 2; ++side) {
+        K* k0;
+        K* v0;
+        const int64_t n = batch_side(q, side, &k0, &v0);
+        res[2 * side] = k0;
+        res[2 * side + 1] = v0;
+        if (q.plan.passes == 0) continue;
         RadixJob<K> x;
         memset(&x, 0, sizeof(x));
-        const int64_t n = side ? q.ns : q.nr;
-        K* k0 = side ? stg.at<K>(o_sk) + q.s0 : stg.at<K>(o_rk) + q.r0;
-        K* v0 = side ? stg.at<K>(o_sv) + q.s0 : stg.at<K>(o_rv) + q.r0;
         x.keys = k0;
         x.n = n;
         set_job_plan(x, q.plan);
         x.hist_stride = 1 << q.plan.max_bits;
-        x.hist = d_hist_all + hist_at;
-        hist_at += (size_t)std::max(1, q.plan.passes) << q.plan.max_bits;
+        x.hist = d_hist_all + q.hist_at + (side ? hist_half(q) : 0);
         x.lookback = lw.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
         x.lb_stride = (int64_t)gp.lb_words;
-        // passes alternate: routed copy -> buffer -> routed copy -> ...
-        K* ak = q.plan.passes > 0 ? lw.at<K>(o_buf[i * 4 + 2 * side]) : nullptr;
-        K* av = q.plan.passes > 0 ? lw.at<K>(o_buf[i * 4 + 2 * side + 1]) : nullptr;
-        set_job_buffers(x, k0, v0, ak, av, k0, v0, &res[2 * side], &res[2 * side + 1]);
-        x.tile0 = htiles;  // the histogram launch numbers tiles over all groups
-        htiles += ceil_div(n, kTile);
-        all_rjh.push_back(x);
+        K* ak = lw.at<K>(o_buf[i * 4 + 2 * side]);
+        K* av = lw.at<K>(o_buf[i * 4 + 2 * side + 1]);
+        if (gp.fused) {
+          // the MSD pass: routed copy -> the batch's MSD output
+          set_job_buffers(x, k0, v0, ak, av, ak, av, &res[2 * side], &res[2 * side + 1]);
+        } else {
+          // LSD passes alternate: routed copy -> buffer -> routed copy -> ...
+          set_job_buffers(x, k0, v0, ak, av, k0, v0, &res[2 * side], &res[2 * side + 1]);
+        }
         x.tile0 = gp.tiles;
         gp.tiles += ceil_div(n, otile);
         all_rj.push_back(x);
+        ++gp.nrj;
       }
-      JoinJob<K> y;
-      y.rk = res[0];
-      y.rv = res[1];
-      y.nr = q.nr;
-      y.sk = res[2];
-      y.sv = res[3];
-      y.ns = q.ns;
-      y.tile0 = jt;
-      jt += ceil_div(q.ns, kJTile);
-      all_jj.push_back(y);
+      if (gp.fused) {
+        FusedJob<K>& f = fj[(size_t)q.fj];
+        f.rk = res[0];
+        f.rv = res[1];
+        f.sk = res[2];
+        f.sv = res[3];
+        f.item0 = item0;
+        f.kbt0 = kbt0;
+        f.kbs0 = kbs0;
+        item0 += q.items;
+        kbt0 += q.kbt;
+        kbs0 += q.kbs;
+      } else {
+        JoinJob<K> y;
+        y.rk = res[0];
+        y.rv = res[1];
+        y.nr = q.nr;
+        y.sk = res[2];
+        y.sv = res[3];
+        y.ns = q.ns;
+        y.tile0 = jt;
+        jt += ceil_div(q.ns, kJTile);
+        all_jj.push_back(y);
+      }
     }
-    gp.o_jt = gc.add<JTile<K>>((size_t)gp.jtiles);
+    if (gp.fused) {
+      gp.o_items = gc.add<FItem>((size_t)std::max<int64_t>(gp.items, 1));
+    } else {
+      gp.o_jt = gc.add<JTile<K>>((size_t)gp.jtiles);
+      gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
+    }
     gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
-    gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     if (gc.off > lane_bytes)
       return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, its lane has %zu", gc.off,
                      lane_bytes);
-    maxp = std::max(maxp, gp.P);
     stats.digit_bits = std::max(stats.digit_bits, gp.maxbits);
     plans.push_back(gp);
   }
-  // (tables were sized for every planned batch; batches found empty after a
-  // sampled route take no room)
-  const size_t rj_used = all_rj.size() * sizeof(RadixJob<K>);
-  if (hist_at > hist_words_all || rj_used > rj1)
+  if (all_rj.size() * sizeof(RadixJob<K>) > rj1)
     return set_err(TJ_ERR_INTERNAL, "group tables do not add up");
-  // one upload of every table (group g writes from base[g] on and its last
-  // join tile sets base[g + 1]), then all digit histograms in one launch
+  // one upload of the group tables (group g writes from base[g] on and its
+  // last join tile or item sets base[g + 1])
   {
     unsigned char* h = nullptr;
     TJ_CUDA(pinned_staging(t_hist, &h));
-    memcpy(h + t_rj, all_rj.data(), rj_used);
-    memcpy(h + t_rjh, all_rjh.data(), rj_used);
+    memcpy(h + t_rj, all_rj.data(), all_rj.size() * sizeof(RadixJob<K>));
     memcpy(h + t_jj, all_jj.data(), all_jj.size() * sizeof(JoinJob<K>));
-    TJ_CUDA(put_small(tbl.p, h, t_hist, st));
+    if (n_fused > 0) memcpy(h + t_fj, fj.data(), fj.size() * sizeof(FusedJob<K>));
+    TJ_CUDA(put_small(tbl.p + t_rj, h + t_rj, t_rjh - t_rj, st));
+    TJ_CUDA(put_small(tbl.p + t_jj, h + t_jj, t_info - t_jj, st));
     TJ_CUDA(cudaEventRecord(pinned_event(), st));  // the staging buffer is busy until here
-    TJ_CUDA(cudaMemsetAsync(tbl.p + t_hist, 0, tbl_bytes - t_hist, st));
-  }
-  RadixJob<K>* d_rj_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rj);
-  RadixJob<K>* d_rjh_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rjh);
-  JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + t_jj);
-  int64_t* d_gbase = reinterpret_cast<int64_t*>(tbl.p + t_base);
-  if (maxp > 0) {
-    tr.begin("histogram", w * (double)(nr + ns));
-    TJ_CUDA(launch_histogram<K>(d_rjh_all, (int)all_rjh.size(), htiles, st));
-    tr.end();
-    TJ_CUDA(launch_digit_scan<K>(d_rjh_all, (int)all_rjh.size(), maxp, st));
+    TJ_CUDA(cudaMemsetAsync(d_gbase, 0, (P.size() + 1) * sizeof(int64_t), st));
   }
 
-  // ---- 6. one batched sort + align per group: a memset and five kernels ----
-  // With two lanes, group g runs on lane g % 2's stream; a group's join waits
-  // for the previous group's join (it writes from the base that join leaves).
+  // ---- 8. per group: LSD sort + align (a memset and five kernels), or the
+  //         MSD pass + the partition-resident join (a memset and four) ----
+  // With two lanes, group g runs on lane g % 2's stream; a group's last kernel
+  // waits for the previous group's (it writes from the base that one leaves).
   cudaStream_t lane_st[2] = {st, st};
   SideStream* side = nullptr;
   JoinBack back;
@@ -1619,10 +1841,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     const cudaStream_t gs = lane_st[gp.lane];
     const View lw{wk.p + (size_t)gp.lane * lane_bytes};
     RadixJob<K>* d_gj = d_rj_all + gp.rj_at;
-    JoinJob<K>* d_gjj = d_jj_all + gp.jj_at;
     uint32_t* d_gcnt = lw.at<uint32_t>(gp.o_cnt);
     int32_t* d_tmap = lw.at<int32_t>(gp.o_tmap);
-    int32_t* d_jmap = lw.at<int32_t>(gp.o_jmap);
     // One lane: every kernel traced.  Two lanes: the launches of the lanes
     // overlap, so a group is traced as a whole ("group/lanes": its sort
     // passes and join, launches counted) with two events instead of two per
@@ -1631,25 +1851,53 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     if (whole) {
       double by = 2.0 * w * gp.rows;  // join input (the output is added at the end)
       for (int p = 0; p < gp.P; ++p) by += 4.0 * w * gp.prow[p];
-      tr.begin("group/lanes", by, gs, gp.P + 3);
+      tr.begin("group/lanes", by, gs, gp.P + 3 + (gp.any_multi ? 1 : 0));
     }
     TJ_CUDA(cudaMemsetAsync(lw.p + gp.o_zero, 0, gp.zero_bytes, gs));
-    TJ_CUDA(launch_group_maps<K>(d_gj, (int)(2 * nj), d_tmap, d_gjj, (int)nj, d_jmap, gs,
-                                 kSortThreads * gp.items));
-    for (int p = 0; p < gp.P; ++p) {
-      if (!whole) tr.begin("onesweep", 4.0 * w * gp.prow[p], gs);
-      TJ_CUDA(launch_onesweep<K>(d_gj, (int)(2 * nj), gp.tiles, p, gp.maxbits, false,
-                                 d_gcnt + p, d_err, gs, d_tmap, gp.items));
-      if (!whole) tr.end();
+    if (gp.fused) {
+      FusedJob<K>* d_gfj = d_fj_all + gp.fj_at;
+      FItem* d_items = lw.at<FItem>(gp.o_items);
+      if (gp.nrj > 0) {
+        TJ_CUDA(launch_group_maps<K>(d_gj, gp.nrj, d_tmap, nullptr, 0, nullptr, gs,
+                                     kSortThreads * gp.items_per_thread));
+        if (!whole) tr.begin("msd", 4.0 * w * gp.msd_rows, gs);
+        TJ_CUDA(launch_onesweep<K>(d_gj, gp.nrj, gp.tiles, 0, gp.maxbits, kModeSort, d_gcnt,
+                                   d_err, gs, d_tmap, gp.items_per_thread));
+        if (!whole) tr.end();
+      }
+      TJ_CUDA(launch_fused_prep<K>(d_gfj, (int)nj, d_items, gp.items, gp.any_multi,
+                                   lw.at<uint32_t>(gp.o_kbt), gs));
+      if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
+      if (!whole) tr.begin("fused", 2.0 * w * gp.rows, gs);
+      if (gp.items > 0) {
+        TJ_CUDA(launch_fused_join<K>(d_gfj, d_items, gp.items, d_gcnt + kMaxPasses + 1,
+                                     lw.at<uint64_t>(gp.o_ilb), lw.at<uint32_t>(gp.o_kbl),
+                                     lw.at<uint32_t>(gp.o_kbt), out, cap, d_gbase + g,
+                                     d_gbase + g + 1, d_err, gs));
+      } else {  // no pairs in this group: the next one starts where it did
+        TJ_CUDA(launch_copy_bytes(d_gbase + g + 1, d_gbase + g, sizeof(int64_t), gs));
+      }
+      tr.end();
+    } else {
+      JoinJob<K>* d_gjj = d_jj_all + gp.jj_at;
+      int32_t* d_jmap = lw.at<int32_t>(gp.o_jmap);
+      TJ_CUDA(launch_group_maps<K>(d_gj, gp.nrj, d_tmap, d_gjj, (int)nj, d_jmap, gs,
+                                   kSortThreads * gp.items_per_thread));
+      for (int p = 0; p < gp.P; ++p) {
+        if (!whole) tr.begin("onesweep", 4.0 * w * gp.prow[p], gs);
+        TJ_CUDA(launch_onesweep<K>(d_gj, gp.nrj, gp.tiles, p, gp.maxbits, kModeSort, d_gcnt + p,
+                                   d_err, gs, d_tmap, gp.items_per_thread));
+        if (!whole) tr.end();
+      }
+      TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, lw.at<JTile<K>>(gp.o_jt), gs,
+                                    d_jmap));
+      if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
+      if (!whole) tr.begin("join", 2.0 * w * gp.rows, gs);
+      TJ_CUDA(launch_join<K>(gp.jtiles, lw.at<JTile<K>>(gp.o_jt), lw.at<uint64_t>(gp.o_jlb),
+                             d_gcnt + kMaxPasses, out, cap, d_gbase + g, nullptr,
+                             d_gbase + g + 1, d_err, gs));
+      tr.end();
     }
-    TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, lw.at<JTile<K>>(gp.o_jt), gs,
-                                  d_jmap));
-    if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
-    if (!whole) tr.begin("join", 2.0 * w * gp.rows, gs);
-    TJ_CUDA(launch_join<K>(gp.jtiles, lw.at<JTile<K>>(gp.o_jt), lw.at<uint64_t>(gp.o_jlb),
-                           d_gcnt + kMaxPasses, out, cap, d_gbase + g, nullptr, d_gbase + g + 1,
-                           d_err, gs));
-    tr.end();
     // (the next group's wait is enqueued before this event is recorded again)
     if (lanes > 1) TJ_CUDA(cudaEventRecord(side->ev[1], gs));
   }
@@ -1660,7 +1908,9 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   TJ_CUDA(get_small(&h_total, d_gbase + plans.size(), sizeof(int64_t), st));
   TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
   TJ_CUDA(sync_stream(st));
-  if (h_total <= cap) tr.add_bytes(lanes > 1 ? "group/lanes" : "join", 2.0 * w * (double)h_total);
+  if (h_total <= cap && !plans.empty())
+    tr.add_bytes(lanes > 1 ? "group/lanes" : (plans.back().fused ? "fused" : "join"),
+                 2.0 * w * (double)h_total);
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);
   *out_count = h_total;

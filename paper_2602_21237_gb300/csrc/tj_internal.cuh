@@ -173,6 +173,65 @@ struct alignas(16) JTile {
 };
 static_assert(sizeof(JTile<int64_t>) == 64 && sizeof(JTile<int32_t>) == 64, "64-byte tiles");
 
+template <typename K> struct PairOf;
+template <> struct PairOf<int32_t> { using type = int2; };
+template <> struct PairOf<int64_t> { using type = longlong2; };
+
+// ---- partition-resident join (tj_fused.cu) ------------------------------------
+// A batch of the partitioned join, cut by one MSD pass into 2^m sub-batches of
+// kFKeys consecutive key values; one item = one tile (<= kFCapS S rows) of a
+// sub-batch, joined on chip.
+constexpr int kFKeyBits = 10;               // key offsets within a sub-batch
+constexpr int kFKeys = 1 << kFKeyBits;
+constexpr int kFThreads = 512;              // threads of a fused CTA
+constexpr int kFCapS = 4608;                // S rows of one item (9 per thread)
+constexpr int kFCapR = 2048;                // R rows of a sub-batch (on chip)
+constexpr int kFMaxMsdBits = 10;            // widest MSD digit
+
+template <typename K>
+struct FusedJob {
+  const K* rk;          // R rows of the batch, sub-batches back to back (MSD order)
+  const K* rv;
+  const K* sk;          // S rows likewise
+  const K* sv;
+  const uint32_t* hr;   // first R row of each sub-batch (2^m), nullptr when m == 0
+  const uint32_t* hs;   // first S row of each sub-batch
+  int64_t nr, ns;
+  uint64_t lo;          // the batch's first key (bits of K); sub-batch d starts at lo + d 2^10
+  int32_t m;            // MSD digit bits (0: the batch is one sub-batch)
+  int32_t pad;
+  int64_t item0;        // first item of the batch in its group's item list
+  int64_t kbt0;         // first count-vector slot of its multi-tile sub-batches' tiles
+  int64_t kbs0;         // first totals slot of its multi-tile sub-batches
+};
+
+struct FItem {
+  int32_t job;   // FusedJob of the group
+  uint32_t dt;   // sub-batch (low 11 bits) | tile << 11
+  int32_t kbt;   // count-vector slot of the tile (-1: the sub-batch is one tile)
+  int32_t kbs;   // totals slot of the sub-batch (-1: one tile)
+};
+
+cudaError_t fused_init_attributes();
+// info[4 j + 0..3]: items, multi-tile tiles, multi-tile sub-batches, largest
+// R sub-batch with pairs
+template <typename K>
+cudaError_t launch_fused_info(const FusedJob<K>* d_jobs, int nj, int64_t* d_info,
+                              cudaStream_t st);
+// the group's item list and (any_multi) the totals of its multi-tile
+// sub-batches (d_kb_tot zeroed beforehand)
+template <typename K>
+cudaError_t launch_fused_prep(const FusedJob<K>* d_jobs, int nj, FItem* d_items, int64_t n_items,
+                              bool any_multi, uint32_t* d_kb_tot, cudaStream_t st);
+// the joins of the group's items (item and count-vector look-back zeroed);
+// pairs from *d_out_base on, *d_total = the end of the group's pairs
+template <typename K>
+cudaError_t launch_fused_join(const FusedJob<K>* d_jobs, const FItem* d_items, int64_t n_items,
+                              uint32_t* d_item_counter, uint64_t* d_item_lb, uint32_t* d_kb_lb,
+                              const uint32_t* d_kb_tot, K* out, int64_t capacity,
+                              const int64_t* d_out_base, int64_t* d_total, int* d_err,
+                              cudaStream_t st);
+
 // ---- late materialisation (tj_gather.cu) ------------------------------------
 constexpr int kGatherCols = 16;  // columns per gather launch
 struct GatherCol {

@@ -182,10 +182,6 @@ __device__ __forceinline__ K* join_copy_async(K* dst, const K* __restrict__ src,
   return d;
 }
 
-template <typename K> struct PairOf;
-template <> struct PairOf<int32_t> { using type = int2; };
-template <> struct PairOf<int64_t> { using type = longlong2; };
-
 // One join tile: kJTile consecutive rows of sorted S against the range [a, b)
 // of sorted R whose keys lie between the tile's first and last key.
 //   1. S keys and ids and the first chunk of the R range go to shared memory

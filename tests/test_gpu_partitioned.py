@@ -91,16 +91,20 @@ def test_sampled_regions_fall_back_to_exact_routing(dtype):
 def test_pla_budgeted_fk_zipf(s):
     kr, ir, ks, is_ = datagen.fk_zipf(200_000, 800_000, s, 41)
     budget = 6 << 20
-    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256)
+    # the LSD path: every batch needs a sort buffer, so the budget makes groups
+    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256,
+               fused=False)
     assert st["groups"] > 1
     assert st["scratch_peak"] <= budget
+    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256)
+    assert st["fused_batches"] > 0 and st["scratch_peak"] <= budget
     if s > 1.0:
         assert st["heavy_keys"] >= 1  # the hottest keys get batches of their own
 
 
 def test_auto_switches_to_partitioned_under_budget():
     kr, ir, ks, is_ = datagen.fk_zipf(300_000, 900_000, 0.8, 43)
-    st = check(kr, ir, ks, is_, mem_budget_bytes=8 << 20)
+    st = check(kr, ir, ks, is_, mem_budget_bytes=8 << 20, fused=False)
     assert st["learned"] % 100 == api.ROUTERS["pla"] and st["groups"] > 1
     assert st["scratch_peak"] <= 8 << 20
     st = check(kr, ir, ks, is_)  # unbounded: single pass
@@ -150,10 +154,11 @@ def test_groups_alternate_between_two_lanes():
     # the previous group's, whichever stream ran it
     kr, ir, ks, is_ = datagen.fk_zipf(200_000, 800_000, 0.8, 47)
     budget = 6 << 20
-    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256)
+    st = check(kr, ir, ks, is_, mem_budget_bytes=budget, router="pla", partitions=256,
+               fused=False)
     assert st["groups"] >= 4 and st["lanes"] == 2
     assert st["scratch_peak"] <= budget
-    st = check(kr, ir, ks, is_, router="pla", partitions=256)  # unbounded: one group
+    st = check(kr, ir, ks, is_, router="pla", partitions=256, fused=False)  # one group
     assert st["groups"] == 1 and st["lanes"] == 1
 
 
@@ -173,7 +178,8 @@ def test_two_lanes_many_to_many_on_a_side_stream():
         d = [torch.empty_like(t, device=DEV) for t in h]
         for dst, src in zip(d, h):
             dst.copy_(src, non_blocking=True)
-        got = api.join_inner(*d, mem_budget_bytes=6 << 20, router="pla", partitions=128)
+        got = api.join_inner(*d, mem_budget_bytes=6 << 20, router="pla", partitions=128,
+                             fused=False)
         st = api.stats()
     s.synchronize()
     assert st["groups"] > 1 and st["lanes"] == 2
@@ -201,9 +207,11 @@ def test_keys_outside_the_sample_range_without_key_statistics(dtype):
         side_k[off + 4] = far
     ir = torch.arange(n, dtype=dtype)
     is_ = torch.arange(n, dtype=dtype)
-    st = check(kr, ir, ks, is_, mem_budget_bytes=4 << 20, router="pla", partitions=64,
-               sample_stride=stride, seed=seed)
-    assert st["groups"] > 1 and st["scratch_peak"] <= 4 << 20
+    for fused in (False, True):
+        st = check(kr, ir, ks, is_, mem_budget_bytes=4 << 20, router="pla", partitions=64,
+                   sample_stride=stride, seed=seed, fused=fused)
+        assert st["scratch_peak"] <= 4 << 20
+        assert st["groups"] > 1 or fused
     assert st["key_bits"] == (64 if dtype == torch.int64 else 32)
 
 
@@ -214,7 +222,7 @@ def test_radix_judge_on_a_sample_range_plans_batches_by_their_width():
     # range must come from the last non-empty batch, so every batch is sorted
     # over its own 13 bits (two passes), not over 64
     kr, ir, ks, is_ = datagen.fk_zipf(600_000, 2_400_000, 0.0, 57)
-    st = check(kr, ir, ks, is_, mem_budget_bytes=16 << 20)
+    st = check(kr, ir, ks, is_, mem_budget_bytes=16 << 20, fused=False)
     assert st["learned"] == api.ROUTERS["pla"] + 100
     assert st["partitions"] == 128 and st["groups"] > 1
     assert st["radix_passes"] == 2 and st["digit_bits"] <= 7
