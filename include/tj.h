@@ -105,7 +105,7 @@ typedef enum {
 typedef struct {
   int32_t router;        /* tj_router */
   int32_t partitions;    /* key-range batches requested, 2..1024 (0 = from the key range:
-                            256 for ranges of 27..30 bits, else 128) */
+                            256 for ranges of 27 bits, else 128) */
   int32_t sample_stride; /* sample one row in this many (0 = 100, a 1% sample) */
   int32_t pla_segments;  /* segments of the piecewise-linear CDF (0 = 4096) */
   int32_t mlp_steps;     /* Adam steps of the MLP (0 = 600) */
@@ -120,7 +120,7 @@ typedef struct {
 
 /* tj_join_opts.flags: sort every batch of the partitioned join by LSD passes
  * and align it with the sorted-merge join, instead of the partition-resident
- * phase (the default for batches whose key range spans 10 to 20 bits: one
+ * phase (the default for batches whose key range spans 10 to 19 bits: one
  * MSD pass into sub-batches of 1024 key values, each sorted and aligned on
  * chip).  The result is the same. */
 #define TJ_JOIN_NO_FUSED 1

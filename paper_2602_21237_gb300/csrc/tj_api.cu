@@ -757,15 +757,13 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
 //    buffers, histograms, look-back, join state) fits the budget, and every
 //    group is sorted and aligned by one batched launch sequence, its output
 //    written after the previous group's (device-side running offset).
-// Batches of a partitioned join when the caller leaves the number open: the
-// partition-resident phase joins batches of at most kFKeyBits + kFMaxMsdBits
-// key bits and costs less with an MSD digit of at most 9 bits (measured: a
-// 10-bit pass takes 1.45x a 9-bit one); 256 batches give that for key ranges
-// of 27 to 30 bits, 128 (fewer, larger batches, best for the LSD path: 128
-// and 256 batches measured within 3% there) do for narrower ranges, and wider
-// ones are sorted by LSD passes anyway.
+// Batches of a partitioned join when the caller leaves the number open: 128
+// (fewer, larger batches: best for the LSD path, where 128 and 256 measured
+// within 3%), or 256 when that, and not 128, brings the batches within the
+// partition-resident phase's reach (kFKeyBits + kFMaxMsdBits key bits): key
+// ranges of 27 bits, such as 10^8 keys.
 int auto_parts(int key_bits) {
-  return key_bits >= kFKeyBits + 9 + 8 && key_bits <= kFKeyBits + kFMaxMsdBits + 8 ? 256 : 128;
+  return key_bits == kFKeyBits + kFMaxMsdBits + 8 ? 256 : 128;
 }
 
 // Cuts of 2^plog equal-width batches over [lo, hi]: lo + p 2^(b - plog), b =
@@ -1592,7 +1590,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     stats.fused_batches = nf;
   }
 
-  // ---- 6. groups: consecutive batches of one kind whose working set fits ----
+  // ---- 6. groups: consecutive batches whose working set fits ----
+  // A group holds runs of LSD and fused batches in key order.  Its working
+  // set: every batch's buffers and tables, the LSD batches' look-back words
+  // once per pass of the deepest one, the fused batches' MSD look-back words.
   // When the budget needs more than one group, groups are planned against
   // half of it and alternate between two streams (lanes), each with its own
   // half.
@@ -1605,13 +1606,15 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     for (size_t i = 0; i < P.size();) {
       if (need_of(i) > lim) return (int64_t)i;
       size_t j = i;
-      int64_t ws = 0, lb = 0, acc = 0;
+      int64_t ws = 0, lb_lsd = 0, lb_msd = 0, acc = 0;
       int np = 1;
-      while (j < P.size() && P[j].fused == P[i].fused) {
-        const int np2 = std::max(np, P[j].np);
-        const int64_t acc2 = ws + P[j].ws + (lb + P[j].lb) * np2;
+      while (j < P.size()) {
+        const Part& q = P[j];
+        const int np2 = q.fused ? np : std::max(np, q.np);
+        const int64_t l2 = lb_lsd + (q.fused ? 0 : q.lb), m2 = lb_msd + (q.fused ? q.lb : 0);
+        const int64_t acc2 = ws + q.ws + l2 * np2 + m2;
         if (acc2 > lim) break;
-        ws += P[j].ws, lb += P[j].lb, np = np2, acc = acc2, ++j;
+        ws += q.ws, lb_lsd = l2, lb_msd = m2, np = np2, acc = acc2, ++j;
       }
       groups.push_back({i, j});
       ws_max = std::max(ws_max, acc);
@@ -1648,36 +1651,57 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   TJ_CUDA(wk.alloc((size_t)wk_bytes, st));
 
   // ---- 7. group plans: job tables ----
-  // Group layout in the working block: LSD groups: the sort buffer of every
-  // batch | one zeroed region (tile counters, one look-back region per pass,
-  // chained join words) | join tile descriptors | tile maps.  Fused groups:
-  // the MSD output of every batch | one zeroed region (tile and item
-  // counters, MSD look-back, chained item words, count vectors, totals) |
-  // items | tile map.
-  struct GroupPlan {
+  // Group layout in the working block: the sort buffer (LSD) or MSD output
+  // (fused) of every batch | one zeroed region (tile and item counters, the
+  // LSD passes' look-back words, the MSD pass's, per run: chained join or
+  // item words, count vectors, totals) | per run: join tile descriptors and
+  // tile map, or items | the tile maps of the LSD passes and the MSD pass.
+  // Runs: maximal stretches of batches of one kind; their last kernels run in
+  // key order, each from the output index the one before it left.
+  struct RunPlan {
     bool fused;
-    size_t first, nj;
-    size_t rj_at, jj_at, fj_at;  // offsets into the uploaded tables
-    size_t o_zero, zero_bytes, o_cnt, o_lb, o_jt, o_jlb, o_tmap, o_jmap;
-    size_t o_items, o_ilb, o_kbl, o_kbt;
-    size_t lb_words;
-    int64_t tiles, jtiles, items;
-    int nrj;  // radix jobs of the group
+    size_t first, nj;  // batches [first, first + nj) of P
+    size_t jj_at;      // LSD: join jobs in the table; fused: first FusedJob
+    int64_t jt0, jtiles;  // LSD: its join tiles within the group's
+    int64_t items;        // fused
     bool any_multi;
-    int P, maxbits, items_per_thread, lane;
+    double rows;
+    size_t o_jlb, o_ilb, o_kbl, o_kbt, o_items;
+    int base;  // index of its first output index in d_gbase
+  };
+  struct GroupPlan {
+    size_t first, nj;
+    size_t rj_lsd_at, rj_msd_at;  // radix jobs in the table
+    int nrj_lsd, nrj_msd;
+    size_t o_zero, zero_bytes, o_cnt, o_lb, o_lbm, o_jt, o_jmap, o_tmap, o_tmapm;
+    size_t lb_words, lbm_words;
+    int64_t tiles, tilesm, jtiles;
+    int P, maxbits, maxbitsm, ipt, iptm, lane;
     double rows, msd_rows, prow[kMaxPasses];
+    std::vector<RunPlan> runs;
   };
   std::vector<RadixJob<K>> all_rj;
   std::vector<JoinJob<K>> all_jj;
   std::vector<GroupPlan> plans;
+  int n_bases = 0;
   for (auto& g : groups) {
     GroupPlan gp = {};
-    gp.fused = P[g.first].fused;
     gp.lane = (int)(plans.size() % (size_t)lanes);
     const View lw{wk.p + (size_t)gp.lane * lane_bytes};  // the group's lane of wk
     gp.first = g.first;
     gp.nj = g.second - g.first;
     const size_t nj = gp.nj;
+    for (size_t i = 0; i < nj;) {  // runs
+      RunPlan r = {};
+      r.fused = P[g.first + i].fused;
+      r.first = g.first + i;
+      size_t j = i;
+      while (j < nj && P[g.first + j].fused == r.fused) ++j;
+      r.nj = j - i;
+      r.base = n_bases++;
+      gp.runs.push_back(r);
+      i = j;
+    }
     Carve gc;
     std::vector<size_t> o_buf(nj * 4, 0);
     for (size_t i = 0; i < nj; ++i) {
@@ -1689,58 +1713,88 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         o_buf[i * 4 + 3] = gc.add<K>((size_t)q.ns);
       }
     }
-    // onesweep tile of the group: the wider one when every digit is narrow
-    for (size_t i = 0; i < nj; ++i) gp.maxbits = std::max(gp.maxbits, P[g.first + i].plan.max_bits);
-    gp.items_per_thread = gp.maxbits <= kWideBits ? kItemsWide : kItems;
-    const int64_t otile = (int64_t)kSortThreads * gp.items_per_thread;
+    // onesweep tiles of the LSD passes and of the MSD pass: the wider one
+    // when every digit of the launch is narrow
+    for (size_t i = 0; i < nj; ++i) {
+      const Part& q = P[g.first + i];
+      if (q.fused)
+        gp.maxbitsm = std::max(gp.maxbitsm, q.plan.max_bits);
+      else
+        gp.maxbits = std::max(gp.maxbits, q.plan.max_bits);
+    }
+    gp.ipt = gp.maxbits <= kWideBits ? kItemsWide : kItems;
+    gp.iptm = gp.maxbitsm <= kWideBits ? kItemsWide : kItems;
+    const int64_t otile = (int64_t)kSortThreads * gp.ipt, otilem = (int64_t)kSortThreads * gp.iptm;
     std::vector<size_t> lb_at(nj * 2);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
       const size_t bins = (size_t)1 << q.plan.max_bits;
       for (int side = 0; side < 2; ++side) {
-        lb_at[i * 2 + side] = gp.lb_words;
-        if (q.plan.passes > 0) gp.lb_words += (size_t)ceil_div(side ? q.ns : q.nr, otile) * bins;
+        const int64_t n = side ? q.ns : q.nr;
+        if (q.plan.passes == 0) continue;
+        if (q.fused) {
+          lb_at[i * 2 + side] = gp.lbm_words;
+          gp.lbm_words += (size_t)ceil_div(n, otilem) * bins;
+        } else {
+          lb_at[i * 2 + side] = gp.lb_words;
+          gp.lb_words += (size_t)ceil_div(n, otile) * bins;
+        }
       }
-      gp.P = std::max(gp.P, q.plan.passes);
-      for (int p = 0; p < q.plan.passes; ++p) gp.prow[p] += (double)(q.nr + q.ns);
       gp.rows += (double)(q.nr + q.ns);
-      if (gp.fused) {
+      if (q.fused) {
         if (q.plan.passes > 0) gp.msd_rows += (double)(q.nr + q.ns);
-        gp.items += q.items;
-        gp.any_multi |= q.kbt > 0;
+      } else {
+        gp.P = std::max(gp.P, q.plan.passes);
+        for (int p = 0; p < q.plan.passes; ++p) gp.prow[p] += (double)(q.nr + q.ns);
       }
     }
-    if (!gp.fused)
-      for (size_t i = 0; i < nj; ++i) gp.jtiles += ceil_div(P[g.first + i].ns, kJTile);
-    gp.o_cnt = gc.add<uint32_t>(kMaxPasses + 2);  // tile counters, item counter
+    for (auto& r : gp.runs) {
+      for (size_t i = 0; i < r.nj; ++i) {
+        const Part& q = P[r.first + i];
+        r.rows += (double)(q.nr + q.ns);
+        if (r.fused) {
+          r.items += q.items;
+          r.any_multi |= q.kbt > 0;
+        }
+      }
+      if (!r.fused) {
+        r.jt0 = gp.jtiles;
+        for (size_t i = 0; i < r.nj; ++i) r.jtiles += ceil_div(P[r.first + i].ns, kJTile);
+        gp.jtiles += r.jtiles;
+      }
+    }
+    // zeroed region: counters (LSD passes, the MSD pass, one per run), the
+    // look-back words, per run its chained words and count vectors
+    gp.o_cnt = gc.add<uint32_t>(kMaxPasses + 1 + gp.runs.size());
     gp.o_zero = gp.o_cnt;
     gp.o_lb = gc.add<uint32_t>(std::max<size_t>(gp.lb_words, 1) * (size_t)std::max(1, gp.P));
-    if (gp.fused) {
-      int64_t kbt = 0, kbs = 0;
-      for (size_t i = 0; i < nj; ++i) {
-        kbt += P[g.first + i].kbt;
-        kbs += P[g.first + i].kbs;
+    gp.o_lbm = gc.add<uint32_t>(std::max<size_t>(gp.lbm_words, 1));
+    for (auto& r : gp.runs) {
+      if (r.fused) {
+        int64_t kbt = 0, kbs = 0;
+        for (size_t i = 0; i < r.nj; ++i) {
+          kbt += P[r.first + i].kbt;
+          kbs += P[r.first + i].kbs;
+        }
+        r.o_ilb = gc.add<uint64_t>((size_t)std::max<int64_t>(r.items, 1));
+        r.o_kbl = gc.add<uint32_t>((size_t)std::max<int64_t>(kbt, 1) * kFKeys);
+        r.o_kbt = gc.add<uint32_t>((size_t)std::max<int64_t>(kbs, 1) * kFKeys);
+      } else {
+        r.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(r.jtiles, 1));
       }
-      gp.o_ilb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.items, 1));
-      gp.o_kbl = gc.add<uint32_t>((size_t)std::max<int64_t>(kbt, 1) * kFKeys);
-      gp.o_kbt = gc.add<uint32_t>((size_t)std::max<int64_t>(kbs, 1) * kFKeys);
-    } else {
-      gp.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     }
     gp.zero_bytes = gc.off - gp.o_zero;
-    gp.rj_at = all_rj.size();
-    gp.jj_at = all_jj.size();
-    gp.fj_at = gp.fused ? (size_t)P[g.first].fj : 0;
-    int64_t jt = 0, item0 = 0, kbt0 = 0, kbs0 = 0;
+    // radix jobs (LSD passes, then the MSD pass), join jobs, fused jobs
+    std::vector<RadixJob<K>> rj_lsd, rj_msd;
+    std::vector<const K*> res(nj * 4);
     for (size_t i = 0; i < nj; ++i) {
       const Part& q = P[g.first + i];
-      const K* res[4];
       for (int side = 0; side < 2; ++side) {
         K* k0;
         K* v0;
         const int64_t n = batch_side(q, side, &k0, &v0);
-        res[2 * side] = k0;
-        res[2 * side + 1] = v0;
+        res[i * 4 + 2 * side] = k0;
+        res[i * 4 + 2 * side + 1] = v0;
         if (q.plan.passes == 0) continue;
         RadixJob<K> x;
         memset(&x, 0, sizeof(x));
@@ -1749,64 +1803,88 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         set_job_plan(x, q.plan);
         x.hist_stride = 1 << q.plan.max_bits;
         x.hist = d_hist_all + q.hist_at + (side ? hist_half(q) : 0);
-        x.lookback = lw.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
-        x.lb_stride = (int64_t)gp.lb_words;
         K* ak = lw.at<K>(o_buf[i * 4 + 2 * side]);
         K* av = lw.at<K>(o_buf[i * 4 + 2 * side + 1]);
-        if (gp.fused) {
+        const K** rk = &res[i * 4 + 2 * side];
+        const K** rv = &res[i * 4 + 2 * side + 1];
+        if (q.fused) {
           // the MSD pass: routed copy -> the batch's MSD output
-          set_job_buffers(x, k0, v0, ak, av, ak, av, &res[2 * side], &res[2 * side + 1]);
+          x.lookback = lw.at<uint32_t>(gp.o_lbm) + lb_at[i * 2 + side];
+          x.lb_stride = (int64_t)gp.lbm_words;
+          set_job_buffers(x, k0, v0, ak, av, ak, av, rk, rv);
+          x.tile0 = gp.tilesm;
+          gp.tilesm += ceil_div(n, otilem);
+          rj_msd.push_back(x);
         } else {
           // LSD passes alternate: routed copy -> buffer -> routed copy -> ...
-          set_job_buffers(x, k0, v0, ak, av, k0, v0, &res[2 * side], &res[2 * side + 1]);
+          x.lookback = lw.at<uint32_t>(gp.o_lb) + lb_at[i * 2 + side];
+          x.lb_stride = (int64_t)gp.lb_words;
+          set_job_buffers(x, k0, v0, ak, av, k0, v0, rk, rv);
+          x.tile0 = gp.tiles;
+          gp.tiles += ceil_div(n, otile);
+          rj_lsd.push_back(x);
         }
-        x.tile0 = gp.tiles;
-        gp.tiles += ceil_div(n, otile);
-        all_rj.push_back(x);
-        ++gp.nrj;
       }
-      if (gp.fused) {
-        FusedJob<K>& f = fj[(size_t)q.fj];
-        f.rk = res[0];
-        f.rv = res[1];
-        f.sk = res[2];
-        f.sv = res[3];
-        f.item0 = item0;
-        f.kbt0 = kbt0;
-        f.kbs0 = kbs0;
-        item0 += q.items;
-        kbt0 += q.kbt;
-        kbs0 += q.kbs;
+    }
+    gp.rj_lsd_at = all_rj.size();
+    gp.nrj_lsd = (int)rj_lsd.size();
+    all_rj.insert(all_rj.end(), rj_lsd.begin(), rj_lsd.end());
+    gp.rj_msd_at = all_rj.size();
+    gp.nrj_msd = (int)rj_msd.size();
+    all_rj.insert(all_rj.end(), rj_msd.begin(), rj_msd.end());
+    for (auto& r : gp.runs) {
+      if (r.fused) {
+        r.jj_at = (size_t)P[r.first].fj;
+        int64_t item0 = 0, kbt0 = 0, kbs0 = 0;
+        for (size_t i = 0; i < r.nj; ++i) {
+          const Part& q = P[r.first + i];
+          const size_t li = r.first + i - g.first;
+          FusedJob<K>& f = fj[(size_t)q.fj];
+          f.rk = res[li * 4 + 0];
+          f.rv = res[li * 4 + 1];
+          f.sk = res[li * 4 + 2];
+          f.sv = res[li * 4 + 3];
+          f.item0 = item0;
+          f.kbt0 = kbt0;
+          f.kbs0 = kbs0;
+          item0 += q.items;
+          kbt0 += q.kbt;
+          kbs0 += q.kbs;
+        }
+        r.o_items = gc.add<FItem>((size_t)std::max<int64_t>(r.items, 1));
       } else {
-        JoinJob<K> y;
-        y.rk = res[0];
-        y.rv = res[1];
-        y.nr = q.nr;
-        y.sk = res[2];
-        y.sv = res[3];
-        y.ns = q.ns;
-        y.tile0 = jt;
-        jt += ceil_div(q.ns, kJTile);
-        all_jj.push_back(y);
+        r.jj_at = all_jj.size();
+        int64_t jt = r.jt0;
+        for (size_t i = 0; i < r.nj; ++i) {
+          const Part& q = P[r.first + i];
+          const size_t li = r.first + i - g.first;
+          JoinJob<K> y;
+          y.rk = res[li * 4 + 0];
+          y.rv = res[li * 4 + 1];
+          y.nr = q.nr;
+          y.sk = res[li * 4 + 2];
+          y.sv = res[li * 4 + 3];
+          y.ns = q.ns;
+          y.tile0 = jt;
+          jt += ceil_div(q.ns, kJTile);
+          all_jj.push_back(y);
+        }
       }
     }
-    if (gp.fused) {
-      gp.o_items = gc.add<FItem>((size_t)std::max<int64_t>(gp.items, 1));
-    } else {
-      gp.o_jt = gc.add<JTile<K>>((size_t)gp.jtiles);
-      gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
-    }
+    gp.o_jt = gc.add<JTile<K>>((size_t)std::max<int64_t>(gp.jtiles, 1));
+    gp.o_jmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.jtiles, 1));
     gp.o_tmap = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tiles, 1));
+    gp.o_tmapm = gc.add<int32_t>((size_t)std::max<int64_t>(gp.tilesm, 1));
     if (gc.off > lane_bytes)
       return set_err(TJ_ERR_INTERNAL, "group needs %zu bytes, its lane has %zu", gc.off,
                      lane_bytes);
-    stats.digit_bits = std::max(stats.digit_bits, gp.maxbits);
-    plans.push_back(gp);
+    stats.digit_bits = std::max(stats.digit_bits, std::max(gp.maxbits, gp.maxbitsm));
+    plans.push_back(std::move(gp));
   }
-  if (all_rj.size() * sizeof(RadixJob<K>) > rj1)
+  if (all_rj.size() * sizeof(RadixJob<K>) > rj1 || (size_t)n_bases > P.size())
     return set_err(TJ_ERR_INTERNAL, "group tables do not add up");
-  // one upload of the group tables (group g writes from base[g] on and its
-  // last join tile or item sets base[g + 1])
+  // one upload of the group tables (run r writes from base[r] on and its
+  // last join tile or item sets base[r + 1])
   {
     unsigned char* h = nullptr;
     TJ_CUDA(pinned_staging(t_hist, &h));
@@ -1819,10 +1897,12 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     TJ_CUDA(cudaMemsetAsync(d_gbase, 0, (P.size() + 1) * sizeof(int64_t), st));
   }
 
-  // ---- 8. per group: LSD sort + align (a memset and five kernels), or the
-  //         MSD pass + the partition-resident join (a memset and four) ----
-  // With two lanes, group g runs on lane g % 2's stream; a group's last kernel
-  // waits for the previous group's (it writes from the base that one leaves).
+  // ---- 8. per group: the LSD passes and the MSD pass of its batches, the
+  //         LSD runs' tile ranges and fused runs' items, then each run's
+  //         join (k_join or k_fused_join) in key order ----
+  // With two lanes, group g runs on lane g % 2's stream; a group's first join
+  // waits for the previous group's last (it writes from the base that one
+  // leaves).
   cudaStream_t lane_st[2] = {st, st};
   SideStream* side = nullptr;
   JoinBack back;
@@ -1837,67 +1917,83 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   }
   for (size_t g = 0; g < plans.size(); ++g) {
     const GroupPlan& gp = plans[g];
-    const size_t nj = gp.nj;
     const cudaStream_t gs = lane_st[gp.lane];
     const View lw{wk.p + (size_t)gp.lane * lane_bytes};
-    RadixJob<K>* d_gj = d_rj_all + gp.rj_at;
     uint32_t* d_gcnt = lw.at<uint32_t>(gp.o_cnt);
-    int32_t* d_tmap = lw.at<int32_t>(gp.o_tmap);
     // One lane: every kernel traced.  Two lanes: the launches of the lanes
-    // overlap, so a group is traced as a whole ("group/lanes": its sort
-    // passes and join, launches counted) with two events instead of two per
-    // kernel.
+    // overlap, so a group is traced as a whole ("group/lanes": its passes and
+    // joins, launches counted) with two events instead of two per kernel.
     const bool whole = lanes > 1;
     if (whole) {
-      double by = 2.0 * w * gp.rows;  // join input (the output is added at the end)
+      double by = 2.0 * w * gp.rows + 4.0 * w * gp.msd_rows;  // join input, MSD pass
       for (int p = 0; p < gp.P; ++p) by += 4.0 * w * gp.prow[p];
-      tr.begin("group/lanes", by, gs, gp.P + 3 + (gp.any_multi ? 1 : 0));
+      tr.begin("group/lanes", by, gs, gp.P + 2 + 2 * (int)gp.runs.size());
     }
     TJ_CUDA(cudaMemsetAsync(lw.p + gp.o_zero, 0, gp.zero_bytes, gs));
-    if (gp.fused) {
-      FusedJob<K>* d_gfj = d_fj_all + gp.fj_at;
-      FItem* d_items = lw.at<FItem>(gp.o_items);
-      if (gp.nrj > 0) {
-        TJ_CUDA(launch_group_maps<K>(d_gj, gp.nrj, d_tmap, nullptr, 0, nullptr, gs,
-                                     kSortThreads * gp.items_per_thread));
-        if (!whole) tr.begin("msd", 4.0 * w * gp.msd_rows, gs);
-        TJ_CUDA(launch_onesweep<K>(d_gj, gp.nrj, gp.tiles, 0, gp.maxbits, kModeSort, d_gcnt,
-                                   d_err, gs, d_tmap, gp.items_per_thread));
-        if (!whole) tr.end();
+    // the join jobs of the LSD runs are consecutive in the table
+    size_t jj0 = 0;
+    int lsd_jobs = 0;
+    for (auto& r : gp.runs)
+      if (!r.fused) {
+        if (lsd_jobs == 0) jj0 = r.jj_at;
+        lsd_jobs += (int)r.nj;
       }
-      TJ_CUDA(launch_fused_prep<K>(d_gfj, (int)nj, d_items, gp.items, gp.any_multi,
-                                   lw.at<uint32_t>(gp.o_kbt), gs));
-      if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
-      if (!whole) tr.begin("fused", 2.0 * w * gp.rows, gs);
-      if (gp.items > 0) {
-        TJ_CUDA(launch_fused_join<K>(d_gfj, d_items, gp.items, d_gcnt + kMaxPasses + 1,
-                                     lw.at<uint64_t>(gp.o_ilb), lw.at<uint32_t>(gp.o_kbl),
-                                     lw.at<uint32_t>(gp.o_kbt), out, cap, d_gbase + g,
-                                     d_gbase + g + 1, d_err, gs));
-      } else {  // no pairs in this group: the next one starts where it did
-        TJ_CUDA(launch_copy_bytes(d_gbase + g + 1, d_gbase + g, sizeof(int64_t), gs));
-      }
-      tr.end();
-    } else {
-      JoinJob<K>* d_gjj = d_jj_all + gp.jj_at;
-      int32_t* d_jmap = lw.at<int32_t>(gp.o_jmap);
-      TJ_CUDA(launch_group_maps<K>(d_gj, gp.nrj, d_tmap, d_gjj, (int)nj, d_jmap, gs,
-                                   kSortThreads * gp.items_per_thread));
+    JoinJob<K>* d_gjj = d_jj_all + jj0;
+    if (gp.nrj_lsd > 0) {
+      RadixJob<K>* d_gj = d_rj_all + gp.rj_lsd_at;
+      TJ_CUDA(launch_group_maps<K>(d_gj, gp.nrj_lsd, lw.at<int32_t>(gp.o_tmap), d_gjj, lsd_jobs,
+                                   lw.at<int32_t>(gp.o_jmap), gs, kSortThreads * gp.ipt));
       for (int p = 0; p < gp.P; ++p) {
         if (!whole) tr.begin("onesweep", 4.0 * w * gp.prow[p], gs);
-        TJ_CUDA(launch_onesweep<K>(d_gj, gp.nrj, gp.tiles, p, gp.maxbits, kModeSort, d_gcnt + p,
-                                   d_err, gs, d_tmap, gp.items_per_thread));
+        TJ_CUDA(launch_onesweep<K>(d_gj, gp.nrj_lsd, gp.tiles, p, gp.maxbits, kModeSort,
+                                   d_gcnt + p, d_err, gs, lw.at<int32_t>(gp.o_tmap), gp.ipt));
         if (!whole) tr.end();
       }
-      TJ_CUDA(launch_tile_ranges<K>(d_gjj, (int)nj, gp.jtiles, lw.at<JTile<K>>(gp.o_jt), gs,
-                                    d_jmap));
-      if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
-      if (!whole) tr.begin("join", 2.0 * w * gp.rows, gs);
-      TJ_CUDA(launch_join<K>(gp.jtiles, lw.at<JTile<K>>(gp.o_jt), lw.at<uint64_t>(gp.o_jlb),
-                             d_gcnt + kMaxPasses, out, cap, d_gbase + g, nullptr,
-                             d_gbase + g + 1, d_err, gs));
-      tr.end();
+    } else if (gp.jtiles > 0) {  // LSD runs of single-key batches only: the join map
+      TJ_CUDA(launch_group_maps<K>(nullptr, 0, nullptr, d_gjj, lsd_jobs,
+                                   lw.at<int32_t>(gp.o_jmap), gs));
     }
+    if (gp.nrj_msd > 0) {
+      RadixJob<K>* d_gm = d_rj_all + gp.rj_msd_at;
+      TJ_CUDA(launch_group_maps<K>(d_gm, gp.nrj_msd, lw.at<int32_t>(gp.o_tmapm), nullptr, 0,
+                                   nullptr, gs, kSortThreads * gp.iptm));
+      if (!whole) tr.begin("msd", 4.0 * w * gp.msd_rows, gs);
+      TJ_CUDA(launch_onesweep<K>(d_gm, gp.nrj_msd, gp.tilesm, 0, gp.maxbitsm, kModeSort,
+                                 d_gcnt + kMaxPasses, d_err, gs, lw.at<int32_t>(gp.o_tmapm),
+                                 gp.iptm));
+      if (!whole) tr.end();
+    }
+    if (gp.jtiles > 0)
+      TJ_CUDA(launch_tile_ranges<K>(d_gjj, lsd_jobs, gp.jtiles, lw.at<JTile<K>>(gp.o_jt), gs,
+                                    lw.at<int32_t>(gp.o_jmap)));
+    for (auto& r : gp.runs)
+      if (r.fused)
+        TJ_CUDA(launch_fused_prep<K>(d_fj_all + r.jj_at, (int)r.nj, lw.at<FItem>(r.o_items),
+                                     r.items, r.any_multi, lw.at<uint32_t>(r.o_kbt), gs));
+    if (lanes > 1 && g > 0) TJ_CUDA(cudaStreamWaitEvent(gs, side->ev[1], 0));
+    for (size_t ri = 0; ri < gp.runs.size(); ++ri) {
+      const RunPlan& r = gp.runs[ri];
+      uint32_t* cnt = d_gcnt + kMaxPasses + 1 + ri;
+      if (r.fused) {
+        if (!whole) tr.begin("fused", 2.0 * w * r.rows, gs);
+        if (r.items > 0) {
+          TJ_CUDA(launch_fused_join<K>(d_fj_all + r.jj_at, lw.at<FItem>(r.o_items), r.items, cnt,
+                                       lw.at<uint64_t>(r.o_ilb), lw.at<uint32_t>(r.o_kbl),
+                                       lw.at<uint32_t>(r.o_kbt), out, cap, d_gbase + r.base,
+                                       d_gbase + r.base + 1, d_err, gs));
+        } else {  // no pairs in this run: the next one starts where it did
+          TJ_CUDA(launch_copy_bytes(d_gbase + r.base + 1, d_gbase + r.base, sizeof(int64_t), gs));
+        }
+        if (!whole) tr.end();
+      } else {
+        if (!whole) tr.begin("join", 2.0 * w * r.rows, gs);
+        TJ_CUDA(launch_join<K>(r.jtiles, lw.at<JTile<K>>(gp.o_jt) + r.jt0,
+                               lw.at<uint64_t>(r.o_jlb), cnt, out, cap, d_gbase + r.base, nullptr,
+                               d_gbase + r.base + 1, d_err, gs));
+        if (!whole) tr.end();
+      }
+    }
+    if (whole) tr.end();
     // (the next group's wait is enqueued before this event is recorded again)
     if (lanes > 1) TJ_CUDA(cudaEventRecord(side->ev[1], gs));
   }
@@ -1905,11 +2001,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   stats.radix_passes = maxp;
   int64_t h_total = 0;
   int h_err = 0;
-  TJ_CUDA(get_small(&h_total, d_gbase + plans.size(), sizeof(int64_t), st));
+  TJ_CUDA(get_small(&h_total, d_gbase + n_bases, sizeof(int64_t), st));
   TJ_CUDA(get_small(&h_err, d_err, sizeof(int), st));
   TJ_CUDA(sync_stream(st));
   if (h_total <= cap && !plans.empty())
-    tr.add_bytes(lanes > 1 ? "group/lanes" : (plans.back().fused ? "fused" : "join"),
+    tr.add_bytes(lanes > 1 ? "group/lanes" : (plans.back().runs.back().fused ? "fused" : "join"),
                  2.0 * w * (double)h_total);
   tr.flush();
   if (h_err) return set_err((tj_status)h_err, "device reported %d", h_err);

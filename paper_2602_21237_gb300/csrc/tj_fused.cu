@@ -444,31 +444,52 @@ __global__ void __launch_bounds__(kFThreads, 2)
   }
   uint32_t pr[2] = {0u, 0u};
   if (multi_tile && t > 0) {
-    // decoupled look-back over the earlier tiles of the sub-batch (bounded)
+    // decoupled look-back over the earlier tiles of the sub-batch (a window
+    // of kLB predecessors per round trip, both key offsets together; tile 0
+    // publishes inclusive counts, so the walk ends there at the latest;
+    // bounded wait)
+    constexpr int kLB = 8;
+    const int64_t first = it.kbt - t;  // a sub-batch's tiles have consecutive slots
+    int64_t p[2] = {it.kbt - 1, it.kbt - 1};
+    bool done[2] = {false, false};
+    int spins = 0;
+    while (!(done[0] && done[1])) {
+      uint32_t v[2][kLB];
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int k = k0 + e;
-      uint32_t prefix = 0;
-      int64_t p = it.kbt - 1;  // a sub-batch's tiles have consecutive slots
-      int spins = 0;
-      while (true) {
-        const uint32_t v = ld_vol_u32(kb_lb + (size_t)p * kFKeys + k);
-        const uint32_t f = v & ~kValMask;
-        if (f == 0u) {
-          if (++spins > kSpinLimit) {
-            atomicExch(err, (int)TJ_ERR_TIMEOUT);
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int q = 0; q < kLB; ++q)
+          v[e][q] = (!done[e] && p[e] - q >= first)
+                        ? ld_vol_u32(kb_lb + (size_t)(p[e] - q) * kFKeys + k0 + e)
+                        : kFlagInc;
+      bool progress = false;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (done[e]) continue;
+#pragma unroll
+        for (int q = 0; q < kLB; ++q) {
+          const uint32_t f = v[e][q] & ~kValMask;
+          if (f == 0u) break;  // not published yet: wait for it
+          pr[e] += v[e][q] & kValMask;
+          --p[e];
+          progress = true;
+          if (f == kFlagInc) {
+            done[e] = true;
             break;
           }
-          __nanosleep(32);
-          continue;
         }
-        prefix += v & kValMask;
-        if (f == kFlagInc) break;
-        --p;
       }
-      pr[e] = prefix;
-      st_vol_u32(lb_mine + k, kFlagInc | ((prefix + S.cS[k]) & kValMask));
+      if (!progress) {
+        if (++spins > kSpinLimit) {
+          atomicExch(err, (int)TJ_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
     }
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      st_vol_u32(lb_mine + k0 + e, kFlagInc | ((pr[e] + S.cS[k0 + e]) & kValMask));
   }
   uint32_t cs[2], cr[2];
   uint64_t tot[2];
