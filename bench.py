@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the learned / batched / serving measurements")
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
+                    help="seconds of Poisson arrivals per serving rate (at most)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests per serving rate (at most)")
     return ap.parse_args()
 
 
@@ -550,7 +554,8 @@ def run_tj(args, ws, rank, local):
                   "regime_shift": extra_regime(args.scale),
                   "late_materialisation": extra_payload(args.scale),
                   "sort_single_vs_multi_key": extra_sort_multi(args.scale),
-                  "serving": extra_serving(args.scale)}
+                  "serving": extra_serving(args.scale, args.serving_seconds,
+                                           args.serving_requests)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step_max,
@@ -807,44 +812,73 @@ def extra_batched(scale):
     return res
 
 
-def extra_serving(scale, rates=(10.0, 100.0, 1000.0, 10000.0), budget_gb=64, workers=8):
-    """Poisson arrivals of join requests, |R|, |S| log-uniform in [1e4, 1e8],
-    int64 foreign keys Zipf(1.0), admitted against a 64 GB budget."""
+def extra_serving(scale, seconds=60.0, max_requests=2000,
+                  rates=(10.0, 30.0, 100.0, 300.0, 1000.0, 3000.0, 10000.0), budget_gb=64,
+                  workers=8):
+    """Serving (the P50/P99 framing of the paper's Sec. 5.2 and Sec. 6): Poisson
+    arrivals of foreign-key join requests at each rate, 2000 requests or 60 s
+    of arrivals per rate, admitted against a 64 GB device budget.  |R| and |S|
+    are log-uniform in [1e4, 1e8]: R takes one of nine log-spaced sizes (the
+    first |R| keys of one random permutation of [0, 1e8), so R keys are
+    unique), S is a slice of a pool of Zipf(1.0) draws over that R's keys
+    (so |J| = |S|), int64 keys and ids."""
+    import math
+
     import torch
 
     from paper_2602_21237_gb300 import api, datagen
 
     top = max(20_000, int(1e8 * scale))
-    kr, ir, ks, is_ = datagen.fk_zipf(top, top, 1.0, 20260225, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(20260225)
+    kr = torch.randperm(top, generator=g, device="cuda", dtype=torch.int64)  # R pool
+    ir = torch.arange(top, device="cuda", dtype=torch.int64)
+    classes = sorted({max(10_000, min(top, int(round(10 ** (4 + 0.5 * i))))) for i in range(9)})
+    pools = {}
+    for c in classes:  # Zipf(1.0) over R[:c], through an independent permutation
+        perm = torch.randperm(c, generator=g, device="cuda", dtype=torch.int64)
+        ranks = datagen.zipf_ranks(top, c, 1.0, g, "cuda")
+        pools[c] = kr[:c][perm[ranks]]
+        del perm, ranks
+    # the workers' own streams do not wait for this one: inputs complete first
+    torch.cuda.synchronize()
     srv = api.Server(mem_budget_bytes=int(budget_gb * (1 << 30)), workers=workers)
     out = []
     for i, lam in enumerate(rates):
-        n_req = int(min(200, max(20, lam * 2.0)))
+        n_req = int(min(max_requests, max(20, lam * seconds)))
         nr = datagen.log_uniform_sizes(n_req, 1e4, top, 20260300 + i)
         ns = datagen.log_uniform_sizes(n_req, 1e4, top, 20260400 + i)
-        g = torch.Generator().manual_seed(20260500 + i)
+        gh = torch.Generator().manual_seed(20260500 + i)
         reqs = []
         for a, b in zip(nr, ns):
-            off = int(torch.randint(0, top - b + 1, (1,), generator=g))
-            # R: the first a keys of R's permutation; S: a slice of S's Zipf draws
-            reqs.append(api.Server.join_request(kr[:a], ir[:a], ks[off:off + b],
-                                                is_[off:off + b], None, b))
+            # the class nearest |R| in log scale
+            c = min(classes, key=lambda x: abs(math.log(x) - math.log(a)))
+            off = int(torch.randint(0, top - b + 1, (1,), generator=gh))
+            reqs.append(api.Server.join_request(kr[:c], ir[:c], pools[c][off:off + b],
+                                                ir[off:off + b], None, b))
         arr = datagen.poisson_arrivals(lam, n_req, 20260600 + i)
         srv.reset_stats()
         tickets = srv.replay(reqs, arr)
         res = [srv.wait(t) for t in tickets]
         rep = srv.report()
         assert all(r["status"] == 0 for r in res), res[:3]
-        out.append({"rate_per_s": lam, "requests": n_req, "p50_ms": rep["p50_ms"],
-                    "p99_ms": rep["p99_ms"], "max_ms": rep["max_ms"],
+        # foreign keys: every S row has exactly one partner
+        assert all(r["out_count"] == q.n_s for r, q in zip(res, reqs))
+        out.append({"rate_per_s": lam, "requests": n_req, "completed": rep["completed"],
+                    "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "max_ms": rep["max_ms"],
+                    "mean_ms": rep["mean_ms"], "arrival_span_s": float(arr[-1]),
                     "throughput_tuples_per_s": rep["tuples"] / max(rep["makespan_s"], 1e-9),
-                    "peak_inflight": rep["peak_inflight"],
+                    "peak_inflight": rep["peak_inflight"], "bypasses": rep["bypasses"],
                     "peak_reserved_gb": rep["peak_reserved"] / 2**30})
+        del reqs
     srv.close()
-    del kr, ir, ks, is_
+    del kr, ir, pools
     torch.cuda.empty_cache()
-    return {"budget_gb": budget_gb, "workers": workers, "sizes": f"log-uniform [1e4, {top:.0e}]",
-            "keys": "int64 foreign keys, Zipf(1.0)", "rates": out}
+    return {"budget_gb": budget_gb, "workers": workers,
+            "sizes": f"|R| in 9 log-spaced sizes of [1e4, {top:.0e}] (log-uniform draws "
+                     f"rounded), |S| log-uniform in [1e4, {top:.0e}]",
+            "keys": "int64, R unique, S Zipf(1.0) over the request's R keys (|J| = |S|)",
+            "per_rate": f"min({max_requests} requests, {seconds:g} s of arrivals)",
+            "rates": out}
 
 
 def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort, ws):

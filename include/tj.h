@@ -304,15 +304,20 @@ tj_status tj_mlp_table(const float* theta, int T, float* table, int parts, tj_dt
  *
  * A server owns `workers` host threads, each with its own CUDA stream on the
  * device that was current at tj_server_create.  Submitted requests wait in
- * one FIFO queue; the head is admitted as soon as a worker is free and its
- * footprint fits in what mem_budget_bytes has left (footprint = the scratch
- * its library call may hold + its output buffer, out_capacity pairs).  Admitted
- * requests run concurrently on their workers' streams; a completion releases
- * its reservation and admits the next request (continuous batching).  A
- * request whose footprint exceeds the whole budget completes at once with
- * TJ_ERR_BUDGET.  Inputs and outputs are caller-owned device arrays that must
- * stay valid until the request completes; results are the same as those of
- * the direct calls.
+ * one queue in arrival order; the oldest is admitted as soon as a worker is
+ * free and its footprint fits in what mem_budget_bytes has left (footprint =
+ * the scratch its library call may hold + its output buffer, out_capacity
+ * pairs).  While the oldest does not fit, a later request that does may go
+ * first, but no request is passed more than 8 times (the queue then waits
+ * for it).  Admitted requests run concurrently on their workers' streams; a
+ * completion releases its reservation and admits the next request
+ * (continuous batching).  A request whose footprint exceeds the whole budget
+ * completes at once with TJ_ERR_BUDGET.  Inputs and outputs are caller-owned
+ * device arrays that must stay valid until the request completes; results
+ * are the same as those of the direct calls.  The workers' streams are
+ * non-blocking and do not wait for any other stream: work that produces a
+ * request's inputs must be complete (synchronised) before the request is
+ * submitted.
  */
 typedef enum { TJ_OP_JOIN = 0, TJ_OP_SORT = 1 } tj_op;
 
@@ -344,6 +349,7 @@ typedef struct {
   double makespan_s;                       /* first arrival -> last completion */
   int64_t peak_reserved;                   /* bytes reserved at once, <= budget */
   int32_t peak_inflight;                   /* requests running at once */
+  int64_t bypasses;                        /* times a request was passed by a later one */
 } tj_server_stats;
 
 typedef struct tj_server tj_server;
@@ -355,7 +361,9 @@ tj_status tj_server_submit(tj_server* s, const tj_request* req, int64_t* ticket)
  * from the calling thread; returns once all are submitted. */
 tj_status tj_server_replay(tj_server* s, const tj_request* reqs, const double* arrival_s,
                            int64_t n, int64_t* tickets);
-/* Block until the request completes; *res receives its outcome. */
+/* Block until the request completes; *res receives its outcome.  Each
+ * ticket is collected once (the server keeps no result after that); waiting
+ * on it again, or on an unknown ticket, returns TJ_ERR_INVALID. */
 tj_status tj_server_wait(tj_server* s, int64_t ticket, tj_result* res);
 /* Block until nothing is queued or running. */
 tj_status tj_server_drain(tj_server* s);

@@ -429,7 +429,7 @@ class _SStats(ctypes.Structure):
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("tuples", ctypes.c_int64),
                 ("makespan_s", ctypes.c_double), ("peak_reserved", ctypes.c_int64),
-                ("peak_inflight", ctypes.c_int32)]
+                ("peak_inflight", ctypes.c_int32), ("bypasses", ctypes.c_int64)]
 
 
 def _server_lib():

@@ -2,13 +2,16 @@
 // Sec. 6 it measures): continuous batching of join and sort requests under a
 // device-memory budget.
 //
-// Requests wait in one FIFO queue.  A request is admitted as soon as a worker
-// is free and its footprint (the library scratch its call may hold plus its
-// output buffer) fits in what the budget has left; it then runs on its
-// worker's own CUDA stream, so admitted requests overlap on the device.  When
-// it completes, its reservation is released and the next queued request is
-// admitted immediately -- requests that arrive while others run join the mix
-// as slots and memory free up.  Latency = completion - arrival.
+// Requests wait in one queue in arrival order.  A request is admitted as soon
+// as a worker is free and its footprint (the library scratch its call may
+// hold plus its output buffer) fits in what the budget has left; it then runs
+// on its worker's own CUDA stream, so admitted requests overlap on the
+// device.  When the oldest request does not fit yet, a later one that does
+// may go first, but no request is passed more than kMaxBypass times (then the
+// queue waits for it), so none starves.  When a request completes, its
+// reservation is released and the next one is admitted immediately --
+// requests that arrive while others run join the mix as slots and memory
+// free up.  Latency = completion - arrival.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -16,6 +19,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "tj_internal.cuh"
@@ -24,11 +28,19 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// times a queued request may be passed by later ones that fit the budget
+constexpr int kMaxBypass = 8;
+// requests of the queue's front looked at for one that fits
+constexpr size_t kScan = 64;
+// latencies kept for the percentiles (a uniform sample beyond this many)
+constexpr size_t kLatCap = 1 << 20;
+
 struct Pending {
   int64_t ticket;
   tj_request req;
   size_t footprint;
   Clock::time_point arrival;
+  int bypassed;
 };
 
 }  // namespace
@@ -39,8 +51,12 @@ struct tj_server {
   std::mutex mu;
   std::condition_variable cv;  // queue / completion changes
   std::deque<Pending> queue;
-  std::unordered_map<int64_t, tj_result> done;
-  std::vector<double> lat_ms;
+  std::unordered_map<int64_t, tj_result> done;  // completed, not yet waited on
+  std::unordered_set<int64_t> open;             // submitted, not yet waited on
+  std::vector<double> lat_ms;                   // this stats window's latencies (sampled)
+  int64_t lat_seen = 0;                         // latencies the window has seen
+  uint64_t lat_rng = 0x9E3779B97F4A7C15ull;
+  int64_t bypasses = 0;
   size_t reserved = 0;
   size_t peak_reserved = 0;
   int inflight = 0;
@@ -66,6 +82,19 @@ size_t footprint_of(const tj_request& r) {
   return rows * (4 * w + 2) + (size_t)r.out_capacity * 2 * w + (2u << 20);
 }
 
+// The queued request to admit now (index into the queue), or -1: the first
+// one of the front kScan that fits what the budget has left, unless a request
+// before it has been passed kMaxBypass times already.
+long pick(const tj_server* S) {
+  const size_t n = std::min(S->queue.size(), kScan);
+  for (size_t i = 0; i < n; ++i) {
+    const Pending& q = S->queue[i];
+    if (S->reserved + q.footprint <= S->budget) return (long)i;
+    if (q.bypassed >= kMaxBypass) return -1;  // it goes next: wait for room
+  }
+  return -1;
+}
+
 void worker_main(tj_server* S) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
@@ -74,14 +103,14 @@ void worker_main(tj_server* S) {
     Pending p;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv.wait(lk, [&] {
-        return S->stop ||
-               (!S->queue.empty() && S->reserved + S->queue.front().footprint <= S->budget);
-      });
+      S->cv.wait(lk, [&] { return S->stop || pick(S) >= 0; });
       if (S->stop && S->queue.empty()) break;
-      if (S->queue.empty() || S->reserved + S->queue.front().footprint > S->budget) continue;
-      p = S->queue.front();
-      S->queue.pop_front();
+      const long i = pick(S);
+      if (i < 0) continue;
+      for (long j = 0; j < i; ++j) S->queue[(size_t)j].bypassed += 1;
+      S->bypasses += i;
+      p = S->queue[(size_t)i];
+      S->queue.erase(S->queue.begin() + i);
       S->reserved += p.footprint;
       S->peak_reserved = std::max(S->peak_reserved, S->reserved);
       S->inflight += 1;
@@ -116,7 +145,15 @@ void worker_main(tj_server* S) {
       S->reserved -= p.footprint;
       S->inflight -= 1;
       S->done[p.ticket] = res;
-      S->lat_ms.push_back(res.latency_ms);
+      // reservoir sample of the window's latencies (all of them up to kLatCap)
+      S->lat_seen += 1;
+      if (S->lat_ms.size() < kLatCap) {
+        S->lat_ms.push_back(res.latency_ms);
+      } else {
+        S->lat_rng = S->lat_rng * 6364136223846793005ull + 1442695040888963407ull;
+        const uint64_t k = (S->lat_rng >> 11) % (uint64_t)S->lat_seen;
+        if (k < kLatCap) S->lat_ms[(size_t)k] = res.latency_ms;
+      }
       S->tuples += r.op == TJ_OP_SORT ? r.n_r : r.n_r + r.n_s;
       if (t1 > S->last_done) S->last_done = t1;
     }
@@ -125,9 +162,9 @@ void worker_main(tj_server* S) {
   cudaStreamDestroy(st);
 }
 
-double pct(std::vector<double> v, double q) {
+// q-quantile of sorted v (linear between neighbours)
+double pct(const std::vector<double>& v, double q) {
   if (v.empty()) return 0.0;
-  std::sort(v.begin(), v.end());
   const double pos = q * (double)(v.size() - 1);
   const size_t i = (size_t)pos;
   const double f = pos - (double)i;
@@ -166,6 +203,7 @@ tj_status tj_server_submit(tj_server* S, const tj_request* r, int64_t* ticket) {
       S->first_arrival = p.arrival;
       S->any = true;
     }
+    S->open.insert(p.ticket);
     if (p.footprint > S->budget) {  // can never be admitted
       tj_result res = {};
       res.status = TJ_ERR_BUDGET;
@@ -173,6 +211,7 @@ tj_status tj_server_submit(tj_server* S, const tj_request* r, int64_t* ticket) {
       S->cv.notify_all();
       return TJ_OK;
     }
+    p.bypassed = 0;
     S->queue.push_back(p);
   }
   S->cv.notify_all();
@@ -182,9 +221,12 @@ tj_status tj_server_submit(tj_server* S, const tj_request* r, int64_t* ticket) {
 tj_status tj_server_wait(tj_server* S, int64_t ticket, tj_result* res) {
   if (!S || !res) return TJ_ERR_INVALID;
   std::unique_lock<std::mutex> lk(S->mu);
-  if (ticket < 0 || ticket >= S->next) return TJ_ERR_INVALID;
+  if (S->open.count(ticket) == 0) return TJ_ERR_INVALID;  // unknown, or waited on already
   S->cv.wait(lk, [&] { return S->done.count(ticket) > 0; });
-  *res = S->done[ticket];
+  auto it = S->done.find(ticket);
+  *res = it->second;
+  S->done.erase(it);  // each result is collected once: the server keeps no history
+  S->open.erase(ticket);
   return TJ_OK;
 }
 
@@ -211,20 +253,26 @@ tj_status tj_server_drain(tj_server* S) {
 
 tj_status tj_server_report(tj_server* S, tj_server_stats* out) {
   if (!S || !out) return TJ_ERR_INVALID;
-  std::lock_guard<std::mutex> lk(S->mu);
   tj_server_stats r = {};
-  r.completed = (int64_t)S->lat_ms.size();
-  r.p50_ms = pct(S->lat_ms, 0.50);
-  r.p99_ms = pct(S->lat_ms, 0.99);
-  r.max_ms = S->lat_ms.empty() ? 0.0 : *std::max_element(S->lat_ms.begin(), S->lat_ms.end());
+  std::vector<double> lat;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    lat = S->lat_ms;  // sorted outside the lock
+    r.completed = S->lat_seen;
+    r.tuples = S->tuples;
+    r.makespan_s = S->any ? std::chrono::duration<double>(S->last_done - S->first_arrival).count()
+                          : 0.0;
+    r.peak_reserved = (int64_t)S->peak_reserved;
+    r.peak_inflight = S->peak_inflight;
+    r.bypasses = S->bypasses;
+  }
+  std::sort(lat.begin(), lat.end());
+  r.p50_ms = pct(lat, 0.50);
+  r.p99_ms = pct(lat, 0.99);
+  r.max_ms = lat.empty() ? 0.0 : lat.back();
   double sum = 0;
-  for (double x : S->lat_ms) sum += x;
-  r.mean_ms = S->lat_ms.empty() ? 0.0 : sum / (double)S->lat_ms.size();
-  r.tuples = S->tuples;
-  r.makespan_s = S->any ? std::chrono::duration<double>(S->last_done - S->first_arrival).count()
-                        : 0.0;
-  r.peak_reserved = (int64_t)S->peak_reserved;
-  r.peak_inflight = S->peak_inflight;
+  for (double x : lat) sum += x;
+  r.mean_ms = lat.empty() ? 0.0 : sum / (double)lat.size();
   *out = r;
   return TJ_OK;
 }
@@ -233,6 +281,8 @@ tj_status tj_server_reset_stats(tj_server* S) {
   if (!S) return TJ_ERR_INVALID;
   std::lock_guard<std::mutex> lk(S->mu);
   S->lat_ms.clear();
+  S->lat_seen = 0;
+  S->bypasses = 0;
   S->tuples = 0;
   S->any = false;
   S->peak_reserved = S->reserved;
