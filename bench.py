@@ -551,6 +551,7 @@ def run_tj(args, ws, rank, local):
         extras = {"small_int32_1e6": extra_small(),
                   "learned_vs_radix": extra_learned(args.scale),
                   "batched_vs_one_at_a_time": extra_batched(args.scale),
+                  "path_selection_fk_join": extra_paths(args.scale),
                   "regime_shift": extra_regime(args.scale),
                   "late_materialisation": extra_payload(args.scale),
                   "sort_single_vs_multi_key": extra_sort_multi(args.scale),
@@ -607,6 +608,44 @@ def extra_small():
     return {"workload": "uniform_int32_1e6x1e6_keys_2^20", "pairs": int(r.shape[0]),
             "join_us": 1e3 * ms_join, "join_tuples_per_s": 2e6 / (ms_join / 1e3),
             "sort_us": 1e3 * ms_sort, "sort_keys_per_s": 1e6 / (ms_sort / 1e3)}
+
+
+def extra_paths(scale):
+    """Execution-time path selection (paper Sec. 3.3) against the forced
+    paths (Sec. 5.4) on the benchmark's FK join at Zipf 0.8 (R = 10^8, S =
+    4x10^8 int64), without a budget and under the 256 MiB one: the single
+    pass, the partitioned join with equal-width, PLA and MLP batches, and
+    router AUTO's choice."""
+    import torch
+
+    from paper_2602_21237_gb300 import api, datagen
+
+    n_r, n_s = max(1000, int(10**8 * scale)), max(4000, int(4 * 10**8 * scale))
+    kr, ir, ks, is_ = datagen.fk_zipf(n_r, n_s, 0.8, 20260221 + 1, device="cuda")
+    out = torch.empty((n_s, 2), dtype=torch.int64, device="cuda")
+    res = {"workload": "fk_join_1e8x4e8_zipf0.8_int64"}
+    for label, budget in (("unbounded", 0), ("budget_256MiB", 256 << 20)):
+        row = {}
+        for name in ("single", "radix", "pla", "mlp", "auto"):
+            try:
+                ms, r = _events_ms(lambda: api.join_inner(kr, ir, ks, is_, out=out, router=name,
+                                                          mem_budget_bytes=budget), reps=3, warm=1)
+            except api.TjError as e:
+                row[name] = {"status": f"{e.name}: {e.detail}"}
+                continue
+            assert r.shape[0] == n_s
+            st = api.stats()
+            row[name] = {"ms": ms, "tuples_per_s": (n_r + n_s) / (ms / 1e3),
+                         "path": "single_pass" if st["partitions"] == 0 else
+                         ("radix (judge) for " if st["learned"] >= 100 else "") +
+                         {2: "radix", 3: "pla", 4: "mlp"}.get(st["learned"] % 100, "?"),
+                         "fused_batches": st["fused_batches"], "groups": st["groups"]}
+        best = min(v["ms"] for v in row.values() if "ms" in v)
+        row["auto_over_best_forced"] = row["auto"]["ms"] / best if "ms" in row["auto"] else None
+        res[label] = row
+    del kr, ir, ks, is_, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def extra_regime(scale, budget_mb=256):

@@ -90,7 +90,10 @@ typedef struct {
  * leaves the execution design open).
  */
 typedef enum {
-  TJ_ROUTE_AUTO = 0,   /* single pass if its scratch fits the budget, else TJ_ROUTE_PLA */
+  TJ_ROUTE_AUTO = 0,   /* chosen from the inputs (Sec. 3.3): TJ_ROUTE_PLA (judged by radix)
+                          when one pass does not fit the budget, or when n_r + n_s >= 2^26
+                          and the key range's batches reach the partition-resident phase
+                          (10 to 19 key bits each); else TJ_ROUTE_SINGLE */
   TJ_ROUTE_SINGLE = 1, /* sort both relations whole, then align (TJ_ERR_BUDGET if too big) */
   TJ_ROUTE_RADIX = 2,  /* key-range batches of equal width (top bits of key - min) */
   TJ_ROUTE_PLA = 3,    /* batches from a piecewise-linear CDF on a sample's quantiles */

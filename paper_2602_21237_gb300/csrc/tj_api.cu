@@ -543,6 +543,19 @@ Opts make_opts(const tj_join_opts* o) {
   return x;
 }
 
+// Batches of a partitioned join when the caller leaves the number open: 128
+// (fewer, larger batches: best for the LSD path, where 128 and 256 measured
+// within 3%), or 256 when that, and not 128, brings the batches within the
+// partition-resident phase's reach (kFKeyBits + kFMaxMsdBits key bits): key
+// ranges of 27 bits, such as 10^8 keys.
+int auto_parts(int key_bits) {
+  return key_bits == kFKeyBits + kFMaxMsdBits + 8 ? 256 : 128;
+}
+
+// Inputs (n_r + n_s) from which router AUTO partitions a join whose batches
+// the partition-resident phase can join, even when one pass fits the budget.
+constexpr int64_t kAutoPartitionRows = int64_t(1) << 26;
+
 template <typename K>
 tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* is,
                          int64_t ns, K lo, K hi, bool range_known, size_t budget, const Opts& o,
@@ -660,8 +673,26 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
   const size_t o_jlb = bc.add<uint64_t>(jtiles);
   const size_t need = bc.off + cc.off;
   int router = opts.router;
-  if (router == TJ_ROUTE_AUTO)
-    router = (budget == 0 || need <= budget) ? TJ_ROUTE_SINGLE : TJ_ROUTE_PLA;
+  if (router == TJ_ROUTE_AUTO) {
+    // Execution-time choice of the path (Sec. 3.3: from the input's scale and
+    // the extent of the key axis; Sec. 5.4 compares it with the forced
+    // paths): partitioned when the budget requires it, or when the inputs
+    // are large and the batches of this key range reach the
+    // partition-resident phase, which then costs less than sorting both
+    // relations whole (measured on FK joins: 0.88-0.93x the single pass from
+    // 10^8 rows on, break-even near 5x10^7, up to 2x slower below); else
+    // one pass.
+    const int parts_bits = bitlen((uint64_t)auto_parts(plan.key_bits)) - 1;
+    const int batch_bits = plan.key_bits - parts_bits;
+    const bool fusable =
+        opts.fused && batch_bits >= kFKeyBits && batch_bits <= kFKeyBits + kFMaxMsdBits;
+    if (budget != 0 && need > budget)
+      router = TJ_ROUTE_PLA;
+    else if (fusable && nr + ns >= kAutoPartitionRows)
+      router = TJ_ROUTE_PLA;
+    else
+      router = TJ_ROUTE_SINGLE;
+  }
   if (router != TJ_ROUTE_SINGLE) return partitioned(router, lo, hi, true);
   if (budget != 0 && need > budget)
     return set_err(TJ_ERR_BUDGET,
@@ -757,14 +788,6 @@ tj_status join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, const K* 
 //    buffers, histograms, look-back, join state) fits the budget, and every
 //    group is sorted and aligned by one batched launch sequence, its output
 //    written after the previous group's (device-side running offset).
-// Batches of a partitioned join when the caller leaves the number open: 128
-// (fewer, larger batches: best for the LSD path, where 128 and 256 measured
-// within 3%), or 256 when that, and not 128, brings the batches within the
-// partition-resident phase's reach (kFKeyBits + kFMaxMsdBits key bits): key
-// ranges of 27 bits, such as 10^8 keys.
-int auto_parts(int key_bits) {
-  return key_bits == kFKeyBits + kFMaxMsdBits + 8 ? 256 : 128;
-}
 
 // Cuts of 2^plog equal-width batches over [lo, hi]: lo + p 2^(b - plog), b =
 // significant bits of hi - lo (every key of the range its own batch when

@@ -227,3 +227,21 @@ def test_radix_judge_on_a_sample_range_plans_batches_by_their_width():
     assert st["partitions"] == 128 and st["groups"] > 1
     assert st["radix_passes"] == 2 and st["digit_bits"] <= 7
     assert st["key_bits"] == 20  # keys 0 .. 599_999
+
+
+def test_auto_chooses_the_path_from_scale_and_key_range():
+    # no budget: 7e7 rows whose 24-bit key range gives batches the
+    # partition-resident phase joins -> partitioned; the same scale with
+    # 40-bit log-normal keys -> one pass.  Either way the bytes equal the
+    # single pass's (itself checked against the oracle elsewhere).
+    kr, ir, ks, is_ = datagen.fk_zipf(14_000_000, 56_000_000, 0.8, 59, device="cuda")
+    auto = api.join_inner(kr, ir, ks, is_)
+    st = api.stats()
+    assert st["partitions"] > 0 and st["fused_batches"] > 0
+    assert torch.equal(auto, api.join_inner(kr, ir, ks, is_, router="single"))
+    del kr, ir, ks, is_, auto
+    kr, ir = datagen.lognormal_mix(1 << 25, 61, device="cuda")
+    ks, is_ = datagen.lognormal_mix(1 << 25, 62, device="cuda")
+    auto = api.join_inner(kr, ir, ks, is_)
+    assert api.stats()["partitions"] == 0
+    assert torch.equal(auto, api.join_inner(kr, ir, ks, is_, router="single"))
