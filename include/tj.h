@@ -80,7 +80,9 @@ typedef struct {
   int32_t packed_keys;     /* tj_sort_multi: 1 if the key columns were folded into one
                               key (their significant bits fit it), 0 if sorted per column */
   double learned_balance;  /* the learned model's batches on the sample: largest / mean,
-                              batches of a single key left out (0 if no model) */
+                              batches of a single key left out (0 if no model was
+                              fitted: equal-width ranges already within the judge's
+                              factor of perfect balance) */
   int32_t fused_batches;   /* batches joined by the partition-resident phase */
   int32_t reserved;
 } tj_stats;

@@ -894,44 +894,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       TJ_CUDA(sync_stream(st));
       if (o.partitions <= 0) parts = auto_parts(bitlen(range_of<K>(lo, hi)));
     }
-    int G = std::max(o.segments, parts);
-    G = (G / parts) * parts;  // boundaries fall on knots
-    std::vector<K> bnd((size_t)(parts - 1));
-    if (router == TJ_ROUTE_PLA) {
-      // boundaries of the piecewise-linear CDF: knots t_{(G / parts) p}
-      const int step = G / parts;
-      tr.begin("pla_fit", w * (double)m);
-      TJ_CUDA(launch_quantiles<K>(sb.at<K>(o_k), m, G, step, step * (parts - 1), step,
-                                  sb.at<K>(o_b), st));
-      tr.end();
-    } else {
-      // MLP: seeded uniform initialisation on the host, training and the
-      // monotone tabulation on the device
-      std::vector<float> th(kMlpParams, 0.f);
-      uint64_t z = o.seed;
-      auto uni = [&](float a) {
-        z += 0x9E3779B97F4A7C15ull;
-        uint64_t x = z;
-        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-        x ^= x >> 31;
-        return a * (2.f * (float)((x >> 40) * (1.0 / 16777216.0)) - 1.f);
-      };
-      for (int i = 0; i < 32; ++i) th[1 + i] = uni(2.45f);          // w1
-      for (int i = 0; i < 32; ++i) th[33 + i] = uni(1.0f);          // b1
-      for (int i = 0; i < 1024; ++i) th[65 + i] = uni(0.433f);      // W2
-      for (int i = 0; i < 32; ++i) th[1121 + i] = uni(0.433f);      // w3
-      TJ_CUDA(put_small(sb.at<float>(o_th), th.data(), th.size() * 4, st));
-      tr.begin("mlp_train", 0.0);
-      TJ_CUDA(launch_mlp_train<K>(sb.at<K>(o_k), m, sb.at<float>(o_th), o.mlp_steps, o.mlp_lr,
-                                  o.seed, st));
-      tr.end();
-      tr.begin("mlp_route_table", 0.0);
-      TJ_CUDA(launch_mlp_boundaries<K>(sb.at<float>(o_th), kMlpTable, sb.at<float>(o_tab), parts,
-                                       sb.at<K>(o_k), m, sb.at<K>(o_b), st));
-      tr.end();
-    }
-    TJ_CUDA(get_small(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K), st));
     // per-side sample counts of the batches a set of cuts makes
     auto sample_counts = [&](const std::vector<K>& cv, std::vector<uint32_t>& cnt) -> tj_status {
       std::vector<K> hc(kMaxCuts, std::numeric_limits<K>::max());
@@ -952,11 +914,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     // batches of a single key (a heavy key isolated by its cuts needs no
     // sort).  Radix replaces the model whenever it is within o.radix_judge
     // (1.25 by default) of it, allowing for the sample's noise (the model is
-    // judged on the sample it was fitted to), and its largest batch fits the
-    // budget
-    // -- its route pass is a plain digit pass, no cut-table search -- so a
-    // model that fits the keys no better than equal-width ranges (uniform
-    // keys, or a network that failed to fit) falls back to radix.
+    // judged on the sample it was fitted to) and its largest batch fits the
+    // budget.  Its route pass is a plain digit pass with no cut-table search,
+    // so a model that fits the keys no better than equal-width ranges
+    // (uniform keys, or a network that failed to fit) falls back to radix.
     const int b_all = bitlen(range_of<K>(lo, hi));
     int plog = 0;
     while ((2 << plog) <= parts) ++plog;
@@ -985,21 +946,6 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
       // deviations (Poisson: the square root of the mean) above their mean
       radix_noise = 3.0 / std::sqrt(std::max(1.0, (double)m / std::max(used, 1)));
     }
-    cuts = make_cuts<K>(bnd);
-    std::vector<uint32_t> cnt;
-    tj_status js = sample_counts(cuts, cnt);
-    if (js != TJ_OK) return js;
-    {
-      const int np = (int)cuts.size() + 1;
-      int64_t mx = 0;
-      for (int p2 = 0; p2 < np; ++p2) {
-        const bool single = p2 > 0 && p2 < np - 1 &&
-                            (uint64_t)cuts[(size_t)p2] - (uint64_t)cuts[(size_t)p2 - 1] == 1;
-        if (!single)
-          mx = std::max<int64_t>(mx, (int64_t)cnt[(size_t)p2] + cnt[(size_t)kMaxBins + p2]);
-      }
-      stats.learned_balance = (double)mx * (double)np / (double)std::max<int64_t>(1, m);
-    }
     // Under a budget, the largest equal-width batch (its sample share of all
     // rows plus 10%) must also fit one lane's half of the working set: about
     // 2w + 2 bytes per row (one sort buffer, look-back words).
@@ -1007,13 +953,82 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         1.1 * (double)radix_max / (double)std::max<int64_t>(1, m) * (double)(nr + ns) + 4096.0;
     const bool radix_fits =
         budget == 0 || radix_rows * (2.0 * sizeof(K) + 2.0) <= 0.45 * (double)budget;
-    if (o.radix_judge >= 0 && radix_fits &&
-        stats.radix_balance <= o.radix_judge * stats.learned_balance + radix_noise) {
+    // A model's batches balance no better than perfectly (1, up to the heavy
+    // keys it isolates, and a key heavy enough to matter would have pushed
+    // the equal-width balance up too), so when equal-width ranges are within
+    // the judge's factor of perfect, radix wins whatever the model: the fit
+    // is skipped.
+    std::vector<uint32_t> cnt;
+    tj_status js = TJ_OK;
+    if (o.radix_judge >= 0 && radix_fits && stats.radix_balance <= o.radix_judge + radix_noise) {
       radix_route = true;
       fell_back = true;
+      stats.learned_balance = 0;
       cuts = radix_cuts<K>(lo, hi, plog);
       js = sample_counts(cuts, cnt);
       if (js != TJ_OK) return js;
+    } else {
+      int G = std::max(o.segments, parts);
+      G = (G / parts) * parts;  // boundaries fall on knots
+      std::vector<K> bnd((size_t)(parts - 1));
+      if (router == TJ_ROUTE_PLA) {
+        // boundaries of the piecewise-linear CDF: knots t_{(G / parts) p}
+        const int step = G / parts;
+        tr.begin("pla_fit", w * (double)m);
+        TJ_CUDA(launch_quantiles<K>(sb.at<K>(o_k), m, G, step, step * (parts - 1), step,
+                                    sb.at<K>(o_b), st));
+        tr.end();
+      } else {
+        // MLP: seeded uniform initialisation on the host, training and the
+        // monotone tabulation on the device
+        std::vector<float> th(kMlpParams, 0.f);
+        uint64_t z = o.seed;
+        auto uni = [&](float a) {
+          z += 0x9E3779B97F4A7C15ull;
+          uint64_t x = z;
+          x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+          x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+          x ^= x >> 31;
+          return a * (2.f * (float)((x >> 40) * (1.0 / 16777216.0)) - 1.f);
+        };
+        for (int i = 0; i < 32; ++i) th[1 + i] = uni(2.45f);          // w1
+        for (int i = 0; i < 32; ++i) th[33 + i] = uni(1.0f);          // b1
+        for (int i = 0; i < 1024; ++i) th[65 + i] = uni(0.433f);      // W2
+        for (int i = 0; i < 32; ++i) th[1121 + i] = uni(0.433f);      // w3
+        TJ_CUDA(put_small(sb.at<float>(o_th), th.data(), th.size() * 4, st));
+        tr.begin("mlp_train", 0.0);
+        TJ_CUDA(launch_mlp_train<K>(sb.at<K>(o_k), m, sb.at<float>(o_th), o.mlp_steps, o.mlp_lr,
+                                    o.seed, st));
+        tr.end();
+        tr.begin("mlp_route_table", 0.0);
+        TJ_CUDA(launch_mlp_boundaries<K>(sb.at<float>(o_th), kMlpTable, sb.at<float>(o_tab), parts,
+                                         sb.at<K>(o_k), m, sb.at<K>(o_b), st));
+        tr.end();
+      }
+      TJ_CUDA(get_small(bnd.data(), sb.at<K>(o_b), bnd.size() * sizeof(K), st));
+      TJ_CUDA(sync_stream(st));  // bnd is filled at the sync
+      cuts = make_cuts<K>(bnd);
+      js = sample_counts(cuts, cnt);
+      if (js != TJ_OK) return js;
+      {
+        const int np = (int)cuts.size() + 1;
+        int64_t mx = 0;
+        for (int p2 = 0; p2 < np; ++p2) {
+          const bool single = p2 > 0 && p2 < np - 1 &&
+                              (uint64_t)cuts[(size_t)p2] - (uint64_t)cuts[(size_t)p2 - 1] == 1;
+          if (!single)
+            mx = std::max<int64_t>(mx, (int64_t)cnt[(size_t)p2] + cnt[(size_t)kMaxBins + p2]);
+        }
+        stats.learned_balance = (double)mx * (double)np / (double)std::max<int64_t>(1, m);
+      }
+      if (o.radix_judge >= 0 && radix_fits &&
+          stats.radix_balance <= o.radix_judge * stats.learned_balance + radix_noise) {
+        radix_route = true;
+        fell_back = true;
+        cuts = radix_cuts<K>(lo, hi, plog);
+        js = sample_counts(cuts, cnt);
+        if (js != TJ_OK) return js;
+      }
     }
     // batch sizes per side estimated from the sample (regions sized ahead of
     // the route pass, so it needs no histogram of its own)

@@ -33,16 +33,23 @@ def test_router_unbounded(router, dtype):
 
 
 def test_radix_judge_replaces_a_model_no_better_than_equal_ranges():
-    # uniform keys: equal-width ranges balance as well as the PLA; an MLP
-    # trained for one step fits nothing.  Both fall back to radix (+100), and
-    # the result is the same.
+    # uniform keys: equal-width ranges are within the judge's factor of
+    # perfect balance, so no model is fitted (learned_balance 0) and both
+    # routers fall back to radix (+100); the result is the same.
     kr, ir, ks, is_ = datagen.uniform_pair(150_000, 250_007, -(1 << 40), 1 << 40, 37, torch.int64)
+    m = (150_000 + 250_007) // 100  # the 1% sample; 128 ranges, 3-sigma allowance
+    noise = 3 / np.sqrt(m / 128)
     for router in ("pla", "mlp"):
-        st = check(kr, ir, ks, is_, router=router, partitions=128, mlp_steps=1)
+        st = check(kr, ir, ks, is_, router=router, partitions=128)
         assert st["learned"] == api.ROUTERS[router] + 100
-        m = (150_000 + 250_007) // 100  # the 1% sample; 128 ranges, 3-sigma allowance
-        assert st["radix_balance"] <= 1.25 * st["learned_balance"] + 3 / np.sqrt(m / 128)
+        assert st["learned_balance"] == 0 and st["radix_balance"] <= 1.25 + noise
         assert st["heavy_keys"] == 0 and st["partitions"] == 128
+    # a judge factor below the uniform keys' sampled balance makes the model
+    # fit; an MLP trained for one step fits nothing and still falls back
+    st = check(kr, ir, ks, is_, router="mlp", partitions=128, mlp_steps=1, radix_judge=0.5)
+    assert st["learned_balance"] > 0
+    assert st["learned"] == api.ROUTERS["mlp"] + 100
+    assert st["radix_balance"] <= 0.5 * st["learned_balance"] + noise
 
 
 def test_radix_judge_keeps_a_model_that_balances_better():
