@@ -84,7 +84,8 @@ typedef struct {
                               fitted: equal-width ranges already within the judge's
                               factor of perfect balance) */
   int32_t fused_batches;   /* batches joined by the partition-resident phase */
-  int32_t reserved;
+  int32_t mlp_steps;       /* Adam steps the MLP router trained for (its loss levelled
+                              off, or tj_join_opts.mlp_steps); 0 if none */
 } tj_stats;
 
 /*
@@ -113,8 +114,11 @@ typedef struct {
                             256 for ranges of 27 bits, else 128) */
   int32_t sample_stride; /* sample one row in this many (0 = 100, a 1% sample) */
   int32_t pla_segments;  /* segments of the piecewise-linear CDF (0 = 4096) */
-  int32_t mlp_steps;     /* Adam steps of the MLP (0 = 600) */
-  int32_t mlp_batch;     /* sample rows per step (0 = 512) */
+  int32_t mlp_steps;     /* Adam steps of the MLP, at most (0 = 600); training stops
+                            earlier once its loss levels off: the moving average
+                            of the batch loss improved by less than 2% over the
+                            last 100 steps (checked every 50, from step 150) */
+  int32_t mlp_batch;     /* sample rows per step, 1..256 (0 = 256) */
   float mlp_lr;          /* Adam learning rate (0 = 3e-3) */
   uint64_t seed;         /* sample offsets, MLP initialisation and batches (0 = 20260221) */
   float radix_judge;     /* equal-width ranges replace a learned model whose sampled

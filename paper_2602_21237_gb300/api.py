@@ -43,7 +43,7 @@ class _Stats(ctypes.Structure):
                 ("tile_rows", ctypes.c_int32), ("digit_cap", ctypes.c_int32),
                 ("lanes", ctypes.c_int32), ("packed_keys", ctypes.c_int32),
                 ("learned_balance", ctypes.c_double), ("fused_batches", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("mlp_steps", ctypes.c_int32)]
 
 
 class _Opts(ctypes.Structure):

@@ -289,10 +289,11 @@ __device__ __forceinline__ void sort_offsets(const uint16_t* __restrict__ koff, 
 // k_fused_join: one CTA per item
 // ---------------------------------------------------------------------------
 // Shared memory: per-warp counters of the key offsets (two 16-bit counters a
-// word) and lane-mask tables of the ranking | per key offset: the tile's S
-// rows, the sub-batch's R rows, the entry a row reads to write its pairs,
-// the R id of a unique key | R rows staged for keys with several R rows
-// (sorted by key offset, stably, only then).
+// word) and lane-mask tables of the ranking | per key offset: the
+// sub-batch's R rows (two 16-bit counters a word) and the entry a row reads
+// to write its pairs | the R rows' key offsets, sorted by key offset
+// (stably) when a key has several R rows.  About 75 KB: three CTAs a
+// multiprocessor.
 // What a row of key offset k needs to write its pairs, in one 16-byte load:
 // the position of the key's first pair for this tile's rows within the
 // sub-batch's output (~0: no R row has the key), and the key's R id (one R
@@ -307,14 +308,11 @@ template <typename K>
 struct FusedSmem {
   uint32_t wh[kFWarps][kFKeys / 2];
   uint32_t wm[kFWarps][128];
-  uint32_t cS[kFKeys];
-  uint32_t cR[kFKeys];
+  uint32_t cR[kFKeys / 2];
   KeyEnt<K> ent[kFKeys];
-  K rid[kFKeys];
   uint16_t r_koff[kFCapR];
   uint16_t r_pa[kFCapR];
   uint16_t r_pb[kFCapR];
-  K r_ids[kFCapR];
   uint32_t wcnt[kFWarps * (kFBins / 2)];
   uint16_t wexcl[kFWarps * kFBins];
   uint32_t dbase[kFBins];
@@ -343,8 +341,11 @@ size_t fused_smem_bytes() {
 //      vectors), and the key's first pair, Sum_{k' < k} |S_k'| |R_k'|;
 //   4. the chained scan over the group's items gives the tile's first pair;
 //   5. each S row's pairs go to their final position straight from registers.
+#ifndef TJ_FUSED_MINB
+#define TJ_FUSED_MINB 2
+#endif
 template <typename K>
-__global__ void __launch_bounds__(kFThreads, 2)
+__global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
     k_fused_join(const FusedJob<K>* __restrict__ jobs, const FItem* __restrict__ items,
                  int64_t n_items, uint32_t* __restrict__ item_counter,
                  uint64_t* __restrict__ item_lb, uint32_t* __restrict__ kb_lb,
@@ -359,10 +360,7 @@ __global__ void __launch_bounds__(kFThreads, 2)
   // counters and tables start at zero
   for (int i = tid; i < kFWarps * (kFKeys / 2); i += kFThreads) (&S.wh[0][0])[i] = 0u;
   for (int i = tid; i < kFWarps * 128; i += kFThreads) (&S.wm[0][0])[i] = 0u;
-  for (int i = tid; i < kFKeys; i += kFThreads) {
-    S.cS[i] = 0u;
-    S.cR[i] = 0u;
-  }
+  for (int i = tid; i < kFKeys / 2; i += kFThreads) S.cR[i] = 0u;
   __syncthreads();
   const int64_t ii = S.s_item;
   if (ii >= n_items) return;
@@ -404,9 +402,9 @@ __global__ void __launch_bounds__(kFThreads, 2)
     if (i < nr) {
       const uint32_t o = (uint32_t)((U)rkey[u] - sublo) & (kFKeys - 1);
       S.r_koff[i] = (uint16_t)o;
-      S.r_ids[i] = rid_v[u];
-      if (atomicAdd(&S.cR[o], 1u) == 0u)
-        S.rid[o] = rid_v[u];
+      const uint32_t sh = (o & 1u) * 16u;  // counts <= kFCapR: the halves never carry
+      if (((atomicAdd(&S.cR[o >> 1], 1u << sh) >> sh) & 0xFFFFu) == 0u)
+        S.ent[o].r = rid_v[u];  // the key's R id, kept unless the key has several
       else
         dup = true;
     }
@@ -414,25 +412,14 @@ __global__ void __launch_bounds__(kFThreads, 2)
   // 2. S rows counted and ranked
   uint32_t dr[kFItemsS];
 #pragma unroll
-  for (int u = 0; u < kFItemsS; ++u) {
-    const int row = wrow + u * 32 + lane;
-    dr[u] = (uint32_t)((U)skey[u] - sublo) & (kFKeys - 1);
-    if (row < ns) atomicAdd(&S.cS[dr[u]], 1u);
-  }
+  for (int u = 0; u < kFItemsS; ++u) dr[u] = (uint32_t)((U)skey[u] - sublo) & (kFKeys - 1);
   rank_items_or<kFKeyBits - 7, kFItemsS>(dr, ns - wrow, &S.wh[warp][0], &S.wm[warp][0]);
   dup = __syncthreads_or(dup) != 0;  // also: counts complete, ranks done
 
-  // multi-tile sub-batches: publish this tile's counts (look-back over the
-  // sub-batch's tiles, one word per key offset)
-  uint32_t* lb_mine = multi_tile ? kb_lb + (size_t)it.kbt * kFKeys : nullptr;
-  if (multi_tile)
-    for (int k = tid; k < kFKeys; k += kFThreads)
-      st_vol_u32(lb_mine + k, (t == 0 ? kFlagInc : kFlagAgg) | S.cS[k]);
-  // keys with several R rows: their R rows sorted by key offset
-  if (dup) sort_offsets<kFItemsR>(S.r_koff, nr, S.r_pa, S.r_pb, S.wcnt, S.wexcl, S.dbase);
-
-  // 3. per key offset (two per thread: word tid of the warps' counters)
+  // 3. per key offset (two per thread: word tid of the warps' counters):
+  //    the S rows of earlier warps, and the tile's count
   const int k0 = 2 * tid;
+  uint32_t cs[2];
   {
     uint32_t run = 0;  // the two 16-bit halves never carry (counts <= kFCapS)
 #pragma unroll
@@ -441,7 +428,17 @@ __global__ void __launch_bounds__(kFThreads, 2)
       S.wh[w][tid] = run;
       run += c;
     }
+    cs[0] = run & 0xFFFFu;
+    cs[1] = run >> 16;
   }
+  // multi-tile sub-batches: publish this tile's counts (look-back over the
+  // sub-batch's tiles, one word per key offset)
+  uint32_t* lb_mine = multi_tile ? kb_lb + (size_t)it.kbt * kFKeys : nullptr;
+  if (multi_tile)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) st_vol_u32(lb_mine + k0 + e, (t == 0 ? kFlagInc : kFlagAgg) | cs[e]);
+  // keys with several R rows: their R rows sorted by key offset
+  if (dup) sort_offsets<kFItemsR>(S.r_koff, nr, S.r_pa, S.r_pb, S.wcnt, S.wexcl, S.dbase);
   uint32_t pr[2] = {0u, 0u};
   if (multi_tile && t > 0) {
     // decoupled look-back over the earlier tiles of the sub-batch (a window
@@ -489,14 +486,17 @@ __global__ void __launch_bounds__(kFThreads, 2)
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e)
-      st_vol_u32(lb_mine + k0 + e, kFlagInc | ((pr[e] + S.cS[k0 + e]) & kValMask));
+      st_vol_u32(lb_mine + k0 + e, kFlagInc | ((pr[e] + cs[e]) & kValMask));
   }
-  uint32_t cs[2], cr[2];
+  uint32_t cr[2];
   uint64_t tot[2];
+  {
+    const uint32_t c2 = S.cR[tid];
+    cr[0] = c2 & 0xFFFFu;
+    cr[1] = c2 >> 16;
+  }
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    cs[e] = S.cS[k0 + e];
-    cr[e] = S.cR[k0 + e];
     tot[e] = multi_tile ? (uint64_t)kb_tot[(size_t)it.kbs * kFKeys + k0 + e] : (uint64_t)cs[e];
   }
   // one pass over the key offsets: the exclusive scan of the keys' pairs in
@@ -553,11 +553,10 @@ __global__ void __launch_bounds__(kFThreads, 2)
     const uint32_t rstart[2] = {er, er + cr[0]};
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-      KeyEnt<K> en;
-      // the key's first pair for this tile's rows: after the earlier tiles'
-      en.a = cr[e] ? first[e] + (uint64_t)pr[e] * cr[e] : ~0ull;
-      en.r = dup ? (K)rstart[e] : S.rid[k0 + e];
-      S.ent[k0 + e] = en;
+      // the key's first pair for this tile's rows: after the earlier tiles';
+      // with several R rows a key's run start replaces its R id
+      S.ent[k0 + e].a = cr[e] ? first[e] + (uint64_t)pr[e] * cr[e] : ~0ull;
+      if (dup) S.ent[k0 + e].r = (K)rstart[e];
     }
     total_sub = ta;
     cnt_tile = tb;
@@ -648,11 +647,12 @@ __global__ void __launch_bounds__(kFThreads, 2)
         out[2 * pos + 1] = sid[u];
       }
     } else {
-      const uint32_t c = S.cR[k];
+      const uint32_t c = (S.cR[k >> 1] >> ((k & 1u) * 16u)) & 0xFFFFu;
       const uint64_t pos = base + en.a + (uint64_t)within * c;
       const uint32_t r0 = (uint32_t)en.r;
+      const K* __restrict__ rv = J.rv + x.r0;  // R ids in the order of the key's run
       for (uint32_t j = 0; j < c; ++j) {
-        out[2 * (pos + j)] = S.r_ids[S.r_pb[r0 + j]];
+        out[2 * (pos + j)] = rv[S.r_pb[r0 + j]];
         out[2 * (pos + j) + 1] = sid[u];
       }
     }

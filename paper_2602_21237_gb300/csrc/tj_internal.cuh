@@ -339,8 +339,8 @@ cudaError_t launch_fix_job_out(const JoinJob<K>* d_jobs, int num_jobs, int64_t t
 constexpr int kMlpParams = 1153;
 cudaError_t mlp_init_attributes();
 template <typename K>
-cudaError_t launch_mlp_train(const K* sorted, int64_t m, float* theta, int steps, float lr,
-                             uint64_t seed, cudaStream_t st);
+cudaError_t launch_mlp_train(const K* sorted, int64_t m, float* theta, int steps, int batch,
+                             float lr, uint64_t seed, int* steps_run, cudaStream_t st);
 cudaError_t launch_mlp_grad(const float* theta, const float* x, const float* y, int n,
                             float* grad, cudaStream_t st);
 cudaError_t launch_adam(float* theta, float* m, float* v, const float* g, int n, int t, float lr,

@@ -81,6 +81,8 @@ def test_trained_network_gains_over_radix_and_untrained():
     api.join_inner(*d, router="mlp", partitions=256, radix_judge=-1)
     trained = api.stats()["balance"]
     assert api.stats()["learned"] == api.ROUTERS["mlp"]
+    # training ran until its loss levelled off: at least 150 steps, at most 600
+    assert 150 <= api.stats()["mlp_steps"] <= 600
     assert trained < radix / 3, (trained, radix)
     assert trained < untrained, (trained, untrained)
 
@@ -172,3 +174,17 @@ def test_mlp_table_and_boundaries_match_oracle(seed, T, parts, span):
         assert abs(k - round(k)) <= 1e-9 * max(1.0, abs(k)) and abs(int(bounds[p - 1]) - int(exp[p - 1])) == 1, \
             (p, bounds[p - 1], exp[p - 1], k)
     assert np.all(np.diff(bounds) >= 0)
+
+
+def test_mlp_batch_option():
+    # a smaller batch per step still routes exactly; more than 256 rows per
+    # step is rejected before any work
+    kr, ir, ks, is_ = _lognormal_pair(1 << 16, 81)
+    d = [x.to(DEV) for x in (kr, ir, ks, is_)]
+    got = api.join_inner(*d, router="mlp", partitions=64, mlp_batch=61, mlp_steps=50,
+                         radix_judge=-1)
+    assert_pairs_equal(got, oracle.join_inner(kr.numpy(), ir.numpy(), ks.numpy(), is_.numpy()))
+    assert api.stats()["mlp_steps"] == 50  # below the first convergence check
+    with pytest.raises(api.TjError) as ei:
+        api.join_inner(*d, router="mlp", mlp_batch=257)
+    assert ei.value.status == api.TJ_ERR_INVALID

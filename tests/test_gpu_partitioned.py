@@ -74,6 +74,15 @@ def test_route_regions_sampled_or_histogram(router):
     assert st["route_regions"] == (2 if router == "pla" else 1)
 
 
+def test_1024_learned_batches_take_a_route_histogram():
+    # beyond 256 batches the regions come from a route histogram, not the sample
+    kr, ir = datagen.lognormal_mix(1 << 18, 35)
+    ks, is_ = datagen.lognormal_mix(1 << 18, 36)
+    st = check(kr, ir, ks, is_, router="pla", partitions=1024)
+    assert st["learned"] == api.ROUTERS["pla"] and st["partitions"] > 900
+    assert st["route_regions"] == 1
+
+
 @pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
 def test_sampled_regions_fall_back_to_exact_routing(dtype):
     # the keys at the sampled positions are all small, the others large: the
