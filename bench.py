@@ -824,15 +824,24 @@ def extra_batched(scale):
     hi = max(2e3, 1e6 * scale)
     r_off, s_off, kr, ir, ks, is_ = datagen.batch_jobs(4096, 1e3, hi, 20260224, device="cuda")
     out = torch.empty((max(1, s_off[-1] * 2), 2), dtype=torch.int32, device="cuda")
+    reps = 3
+
+    def timed():
+        api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out)  # warm
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        for _ in range(reps):
+            p, _o = api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out)
+        torch.cuda.synchronize()
+        return (_t.perf_counter() - t0) / reps, p, api.stats()
+
+    # the default digit width and tile (forced, before any tuning in this
+    # process), then the autotuner's choice (selected, Sec. 5.4)
+    td, pd, sd = timed()
     api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out, autotune=True)
     torch.cuda.synchronize()
-    reps = 3
-    t0 = _t.perf_counter()
-    for _ in range(reps):
-        p, _o = api.join_batch(r_off, s_off, kr, ir, ks, is_, out=out)
-    torch.cuda.synchronize()
-    tb = (_t.perf_counter() - t0) / reps
-    st = api.stats()
+    tb, p, st = timed()
+    assert pd.shape[0] == p.shape[0]
     t0 = _t.perf_counter()
     tot = 0
     for j in range(4096):
@@ -844,7 +853,12 @@ def extra_batched(scale):
     assert tot == p.shape[0]
     res = {"jobs": 4096, "rows": rows, "pairs": tot,
            "batched": {"ms": tb * 1e3, "tuples_per_s": rows / tb, "tile_rows": st["tile_rows"],
-                       "digit_cap": st["digit_cap"], "radix_passes": st["radix_passes"]},
+                       "digit_cap": st["digit_cap"], "radix_passes": st["radix_passes"],
+                       "config": "autotuned (selected)"},
+           "batched_default": {"ms": td * 1e3, "tuples_per_s": rows / td,
+                               "tile_rows": sd["tile_rows"], "digit_cap": sd["digit_cap"],
+                               "radix_passes": sd["radix_passes"],
+                               "config": "default digit width and tile (forced)"},
            "one_at_a_time": {"ms": t1 * 1e3, "tuples_per_s": rows / t1}}
     del kr, ir, ks, is_, out
     torch.cuda.empty_cache()

@@ -129,9 +129,10 @@ typedef struct {
 
 /* tj_join_opts.flags: sort every batch of the partitioned join by LSD passes
  * and align it with the sorted-merge join, instead of the partition-resident
- * phase (the default for batches whose key range spans 10 to 19 bits: one
+ * phase.  By default, batches whose key range spans 10 to 19 bits take one
  * MSD pass into sub-batches of 1024 key values, each sorted and aligned on
- * chip).  The result is the same. */
+ * chip.  A batch of a single key value (a heavy key the cuts isolate) has its
+ * pairs streamed straight from its rows.  The result is the same. */
 #define TJ_JOIN_NO_FUSED 1
 
 /*

@@ -546,10 +546,10 @@ Opts make_opts(const tj_join_opts* o) {
 // Batches of a partitioned join when the caller leaves the number open: 128
 // (fewer, larger batches: best for the LSD path, where 128 and 256 measured
 // within 3%), or 256 when that, and not 128, brings the batches within the
-// partition-resident phase's reach (kFKeyBits + kFMaxMsdBits key bits): key
-// ranges of 27 bits, such as 10^8 keys.
+// partition-resident phase's preferred reach (kFKeyBits + kFPreferMsdBits
+// key bits): key ranges of 27 bits, such as 10^8 keys.
 int auto_parts(int key_bits) {
-  return key_bits == kFKeyBits + kFMaxMsdBits + 8 ? 256 : 128;
+  return key_bits == kFKeyBits + kFPreferMsdBits + 8 ? 256 : 128;
 }
 
 // Inputs (n_r + n_s) from which router AUTO partitions a join whose batches
@@ -1419,13 +1419,16 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   // sub-batches of kFKeys key values, which are sorted and aligned on chip
   // (tj_fused.cu) -- unless one of them holds more R rows than fit on chip
   // (many duplicate R keys), which the key counts show after the MSD
-  // histogram.  Other batches are sorted by LSD passes and aligned by k_join.
+  // histogram.  A batch of a single key value (a heavy key the cuts
+  // isolate) pairs every R row with every S row: k_cross streams its pairs.
+  // Other batches are sorted by LSD passes and aligned by k_join.
   struct Part {
     int64_t r0, nr, s0, ns;
     K lo, hi;
     Plan plan;    // LSD plan (or, fused, the MSD pass: its only digit)
     Plan lsd;     // the LSD plan, kept for a fused batch that falls back
     bool fused;
+    bool cross;   // one key value: pairs streamed by k_cross
     int m;        // fused: MSD digit bits
     int64_t items, kbt, kbs;  // fused: items, multi-tile tiles and sub-batches
     int64_t ws;   // working set without the look-back words
@@ -1456,7 +1459,8 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     const int bits = q.lsd.key_bits;
     // (narrower batches -- a heavy key's own batch above all -- need no sort
     // or few passes: k_join aligns them directly)
-    q.fused = o.fused && bits >= kFKeyBits && bits <= kFKeyBits + kFMaxMsdBits;
+    q.fused = o.fused && bits >= kFMinBits && bits <= kFKeyBits + kFMaxMsdBits;
+    q.cross = o.fused && q.lo == q.hi;
     q.m = q.fused ? std::max(0, bits - kFKeyBits) : 0;
     q.fj = q.fused ? n_fused++ : -1;
     if (q.fused) {
@@ -1505,12 +1509,20 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   };
   for (auto& q : P)
     if (!q.fused) plan_lsd(q);
+  // ... and a single-key batch: no buffers (its job sits in the tables)
+  for (auto& q : P)
+    if (q.cross) {
+      q.ws = 4096;
+      q.lb = 0;
+      q.np = 1;
+    }
   // tables: histogram-pass jobs and group jobs (radix), join jobs, fused jobs
   // and their counts, histograms, output bases (one more than groups; at most
   // one group per batch)
   const size_t rj1 = P.size() * 2 * sizeof(RadixJob<K>);
   const size_t t_rj = 0, t_rjh = t_rj + rj1, t_jj = t_rjh + rj1;
-  const size_t t_fj = (t_jj + P.size() * sizeof(JoinJob<K>) + 255) & ~(size_t)255;
+  const size_t t_cj = (t_jj + P.size() * sizeof(JoinJob<K>) + 255) & ~(size_t)255;
+  const size_t t_fj = (t_cj + P.size() * sizeof(CrossJob<K>) + 255) & ~(size_t)255;
   const size_t t_info = (t_fj + std::max<size_t>(1, (size_t)n_fused) * sizeof(FusedJob<K>) + 255) &
                         ~(size_t)255;
   const size_t t_hist = (t_info + std::max<size_t>(1, (size_t)n_fused) * 4 * sizeof(int64_t) + 255) &
@@ -1529,6 +1541,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   RadixJob<K>* d_rj_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rj);
   RadixJob<K>* d_rjh_all = reinterpret_cast<RadixJob<K>*>(tbl.p + t_rjh);
   JoinJob<K>* d_jj_all = reinterpret_cast<JoinJob<K>*>(tbl.p + t_jj);
+  CrossJob<K>* d_cj_all = reinterpret_cast<CrossJob<K>*>(tbl.p + t_cj);
   FusedJob<K>* d_fj_all = reinterpret_cast<FusedJob<K>*>(tbl.p + t_fj);
   int64_t* d_info = reinterpret_cast<int64_t*>(tbl.p + t_info);
   int64_t* d_gbase = reinterpret_cast<int64_t*>(tbl.p + t_base);
@@ -1699,10 +1712,14 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   // LSD passes' look-back words, the MSD pass's, per run: chained join or
   // item words, count vectors, totals) | per run: join tile descriptors and
   // tile map, or items | the tile maps of the LSD passes and the MSD pass.
-  // Runs: maximal stretches of batches of one kind; their last kernels run in
-  // key order, each from the output index the one before it left.
+  // Runs: maximal stretches of batches of one kind (LSD, fused, single-key);
+  // their last kernels run in key order, each from the output index the one
+  // before it left.
   struct RunPlan {
     bool fused;
+    bool cross;        // single-key batches (k_cross)
+    int64_t pairs;     // cross: the run's pairs
+    int64_t xblocks;   // cross: CTAs of k_cross
     size_t first, nj;  // batches [first, first + nj) of P
     size_t jj_at;      // LSD: join jobs in the table; fused: first FusedJob
     int64_t jt0, jtiles;  // LSD: its join tiles within the group's
@@ -1725,6 +1742,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
   };
   std::vector<RadixJob<K>> all_rj;
   std::vector<JoinJob<K>> all_jj;
+  std::vector<CrossJob<K>> all_cj;
   std::vector<GroupPlan> plans;
   int n_bases = 0;
   for (auto& g : groups) {
@@ -1737,9 +1755,10 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     for (size_t i = 0; i < nj;) {  // runs
       RunPlan r = {};
       r.fused = P[g.first + i].fused;
+      r.cross = P[g.first + i].cross;
       r.first = g.first + i;
       size_t j = i;
-      while (j < nj && P[g.first + j].fused == r.fused) ++j;
+      while (j < nj && P[g.first + j].fused == r.fused && P[g.first + j].cross == r.cross) ++j;
       r.nj = j - i;
       r.base = n_bases++;
       gp.runs.push_back(r);
@@ -1800,7 +1819,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
           r.any_multi |= q.kbt > 0;
         }
       }
-      if (!r.fused) {
+      if (!r.fused && !r.cross) {
         r.jt0 = gp.jtiles;
         for (size_t i = 0; i < r.nj; ++i) r.jtiles += ceil_div(P[r.first + i].ns, kJTile);
         gp.jtiles += r.jtiles;
@@ -1822,7 +1841,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         r.o_ilb = gc.add<uint64_t>((size_t)std::max<int64_t>(r.items, 1));
         r.o_kbl = gc.add<uint32_t>((size_t)std::max<int64_t>(kbt, 1) * kFKeys);
         r.o_kbt = gc.add<uint32_t>((size_t)std::max<int64_t>(kbs, 1) * kFKeys);
-      } else {
+      } else if (!r.cross) {
         r.o_jlb = gc.add<uint64_t>((size_t)std::max<int64_t>(r.jtiles, 1));
       }
     }
@@ -1895,6 +1914,24 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
           kbs0 += q.kbs;
         }
         r.o_items = gc.add<FItem>((size_t)std::max<int64_t>(r.items, 1));
+      } else if (r.cross) {
+        r.jj_at = all_cj.size();
+        for (size_t i = 0; i < r.nj; ++i) {
+          const Part& q = P[r.first + i];
+          const size_t li = r.first + i - g.first;
+          CrossJob<K> x;
+          x.rv = res[li * 4 + 1];
+          x.sv = res[li * 4 + 3];
+          x.nr = q.nr;
+          x.ns = q.ns;
+          x.off = r.pairs;
+          x.blk0 = r.xblocks;
+          r.pairs += q.nr * q.ns;
+          r.xblocks += ceil_div(q.nr * q.ns, kXPairs);
+          all_cj.push_back(x);
+        }
+        // beyond the caller's capacity: one CTA, which only passes the base on
+        if (r.pairs > cap) r.xblocks = 1;
       } else {
         r.jj_at = all_jj.size();
         int64_t jt = r.jt0;
@@ -1933,6 +1970,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     TJ_CUDA(pinned_staging(t_hist, &h));
     memcpy(h + t_rj, all_rj.data(), all_rj.size() * sizeof(RadixJob<K>));
     memcpy(h + t_jj, all_jj.data(), all_jj.size() * sizeof(JoinJob<K>));
+    memcpy(h + t_cj, all_cj.data(), all_cj.size() * sizeof(CrossJob<K>));
     if (n_fused > 0) memcpy(h + t_fj, fj.data(), fj.size() * sizeof(FusedJob<K>));
     TJ_CUDA(put_small(tbl.p + t_rj, h + t_rj, t_rjh - t_rj, st));
     TJ_CUDA(put_small(tbl.p + t_jj, h + t_jj, t_info - t_jj, st));
@@ -1977,7 +2015,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     size_t jj0 = 0;
     int lsd_jobs = 0;
     for (auto& r : gp.runs)
-      if (!r.fused) {
+      if (!r.fused && !r.cross) {
         if (lsd_jobs == 0) jj0 = r.jj_at;
         lsd_jobs += (int)r.nj;
       }
@@ -2027,6 +2065,11 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
         } else {  // no pairs in this run: the next one starts where it did
           TJ_CUDA(launch_copy_bytes(d_gbase + r.base + 1, d_gbase + r.base, sizeof(int64_t), gs));
         }
+        if (!whole) tr.end();
+      } else if (r.cross) {
+        if (!whole) tr.begin("cross", w * (double)r.rows + 2.0 * w * (double)r.pairs, gs);
+        TJ_CUDA(launch_cross<K>(d_cj_all + r.jj_at, (int)r.nj, r.xblocks, out, cap,
+                                d_gbase + r.base, d_gbase + r.base + 1, r.pairs, gs));
         if (!whole) tr.end();
       } else {
         if (!whole) tr.begin("join", 2.0 * w * r.rows, gs);

@@ -157,6 +157,21 @@ struct JoinJob {
   int64_t tile0;        // first global join tile (kJTile S rows per tile)
 };
 
+// A batch of one key value (a heavy key the cuts isolate): every R row pairs
+// with every S row, so its pairs need neither sort nor table.  Pair p of the
+// batch, p = i * nr + j, is (R id j, S id i) at out[base + off + p]: key,
+// then S position, then R position.
+template <typename K>
+struct CrossJob {
+  const K* rv;     // R ids of the batch (routed, so in input order)
+  const K* sv;     // S ids
+  int64_t nr, ns;
+  int64_t off;     // first pair relative to its run's base
+  int64_t blk0;    // first CTA (kXPairs pairs per CTA)
+};
+constexpr int kXPairs = 4096;  // pairs per CTA of k_cross
+constexpr int kXThreads = 256;
+
 // One join tile as k_tile_ranges leaves it for k_join (one 64-byte load): its
 // S rows and the R rows whose keys lie between its first and last key.
 template <typename K>
@@ -182,11 +197,21 @@ template <> struct PairOf<int64_t> { using type = longlong2; };
 // kFKeys consecutive key values; one item = one tile (<= kFCapS S rows) of a
 // sub-batch, joined on chip.
 constexpr int kFKeyBits = 10;               // key offsets within a sub-batch
+#ifndef TJ_FUSED_MIN_BITS
+#define TJ_FUSED_MIN_BITS 10
+#endif
+// narrowest batch key range the resident phase takes (below kFKeyBits: the
+// whole batch is one sub-batch, no MSD pass)
+constexpr int kFMinBits = TJ_FUSED_MIN_BITS;
 constexpr int kFKeys = 1 << kFKeyBits;
 constexpr int kFThreads = 512;              // threads of a fused CTA
 constexpr int kFCapS = 4608;                // S rows of one item (9 per thread)
 constexpr int kFCapR = 2048;                // R rows of a sub-batch (on chip)
-constexpr int kFMaxMsdBits = 9;             // widest MSD digit (a 10-bit pass costs 1.45x)
+#ifndef TJ_FUSED_MAX_MSD
+#define TJ_FUSED_MAX_MSD 9
+#endif
+constexpr int kFMaxMsdBits = TJ_FUSED_MAX_MSD;  // widest MSD digit of the resident phase
+constexpr int kFPreferMsdBits = 9;  // widest MSD digit the batch count aims at (a 10-bit pass costs 1.45x a 9-bit one)
 
 template <typename K>
 struct FusedJob {
@@ -306,6 +331,13 @@ cudaError_t launch_join(int64_t total_tiles, const JTile<K>* d_tiles, uint64_t* 
                         uint32_t* d_tile_counter, K* out, int64_t capacity,
                         const int64_t* d_out_base, int64_t* d_job_out, int64_t* d_total,
                         int* d_err, cudaStream_t st);
+// k_cross over a run of single-key batches: reads the run's base, writes
+// base + run_pairs for the next run (CTA 0), and writes a batch's pairs only
+// if all of them fit `capacity`.
+template <typename K>
+cudaError_t launch_cross(const CrossJob<K>* d_jobs, int num_jobs, int64_t blocks, K* out,
+                         int64_t capacity, const int64_t* d_base, int64_t* d_next,
+                         int64_t run_pairs, cudaStream_t st);
 // tile -> job maps of a group's radix jobs (tile of kTile rows) and join jobs
 template <typename K>
 cudaError_t launch_group_maps(const RadixJob<K>* d_rjobs, int nr, int32_t* d_rmap,

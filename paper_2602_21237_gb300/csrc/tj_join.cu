@@ -647,6 +647,68 @@ cudaError_t launch_fix_job_out(const JoinJob<K>* d_jobs, int num_jobs, int64_t t
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// k_cross: the pairs of single-key batches, streamed (one CTA per kXPairs
+// consecutive pairs of a batch): pair p = i * nr + j of a batch is (R id j,
+// S id i), so for nr = 1 (a foreign key's heavy value) a CTA reads 4096
+// consecutive S ids and writes 4096 consecutive pairs.
+template <typename K>
+__global__ void __launch_bounds__(kXThreads)
+    k_cross(const CrossJob<K>* __restrict__ jobs, int num_jobs, K* __restrict__ out,
+            int64_t capacity, const int64_t* __restrict__ base_in, int64_t* __restrict__ base_out,
+            int64_t run_pairs) {
+  const int64_t b = blockIdx.x;
+  int lo = 0, hi = num_jobs - 1;  // last job whose first CTA is <= b
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].blk0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const CrossJob<K> J = jobs[lo];
+  const int64_t base = *base_in;
+  if (b == 0 && threadIdx.x == 0) *base_out = base + run_pairs;
+  const int64_t np = J.nr * J.ns;
+  const int64_t o = base + J.off;
+  if (o + np > capacity) return;  // the host reports TJ_ERR_CAPACITY
+  const int64_t p0 = (b - J.blk0) * kXPairs;
+  const int64_t p1 = min(np, p0 + kXPairs);
+  using P = typename PairOf<K>::type;
+  const bool vec = (((uintptr_t)out) & (2 * sizeof(K) - 1)) == 0;
+  if (J.nr == 1) {
+    const K r = J.rv[0];
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kXThreads) {
+      const K sid = J.sv[p];
+      if (vec) {
+        P v;
+        v.x = r;
+        v.y = sid;
+        *reinterpret_cast<P*>(out + 2 * (o + p)) = v;
+      } else {
+        out[2 * (o + p)] = r;
+        out[2 * (o + p) + 1] = sid;
+      }
+    }
+  } else {
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kXThreads) {
+      const int64_t i = p / J.nr, j = p - i * J.nr;
+      out[2 * (o + p)] = J.rv[j];
+      out[2 * (o + p) + 1] = J.sv[i];
+    }
+  }
+}
+
+template <typename K>
+cudaError_t launch_cross(const CrossJob<K>* d_jobs, int num_jobs, int64_t blocks, K* out,
+                         int64_t capacity, const int64_t* d_base, int64_t* d_next,
+                         int64_t run_pairs, cudaStream_t st) {
+  if (num_jobs <= 0 || blocks <= 0) return cudaErrorInvalidValue;
+  k_cross<K><<<(unsigned)blocks, kXThreads, 0, st>>>(d_jobs, num_jobs, out, capacity, d_base,
+                                                     d_next, run_pairs);
+  return cudaGetLastError();
+}
+
 cudaError_t join_init_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_join<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)join_smem_bytes<int32_t>());
@@ -663,6 +725,8 @@ cudaError_t join_init_attributes() {
   template cudaError_t launch_join<K>(int64_t, const JTile<K>*, uint64_t*, uint32_t*, K*,        \
                                       int64_t, const int64_t*, int64_t*, int64_t*, int*,          \
                                       cudaStream_t);                                              \
+  template cudaError_t launch_cross<K>(const CrossJob<K>*, int, int64_t, K*, int64_t,            \
+                                       const int64_t*, int64_t*, int64_t, cudaStream_t);        \
   template cudaError_t launch_fix_job_out<K>(const JoinJob<K>*, int, int64_t, int64_t*,          \
                                              const int64_t*, cudaStream_t);                     \
   template cudaError_t launch_group_maps<K>(const RadixJob<K>*, int, int32_t*, const JoinJob<K>*, \

@@ -104,3 +104,36 @@ def test_capacity_error_with_multi_tile_sub_batches():
     with pytest.raises(api.TjError) as ei:
         api.join_inner(*d, out=out, router="radix", partitions=64)
     assert ei.value.status == api.TJ_ERR_CAPACITY
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int64])
+def test_single_key_batches_are_streamed(dtype):
+    # two heavy S keys the PLA cuts isolate: key 777 has four R rows (pairs
+    # in S position, then R position order), key 5000 one; their batches'
+    # pairs are streamed by k_cross, the rest go through the other paths
+    g = torch.Generator().manual_seed(8)
+    kr = torch.cat([torch.randperm(1 << 17, generator=g), torch.full((3,), 777)])
+    kr = kr[torch.randperm(kr.numel(), generator=g)]
+    ks = torch.cat([torch.randint(0, 1 << 17, (400_000,), generator=g),
+                    torch.full((200_000,), 777), torch.full((300_001,), 5000)])
+    ks = ks[torch.randperm(ks.numel(), generator=g)]
+    kr, ks = kr.to(dtype), ks.to(dtype)
+    ir = torch.arange(kr.numel(), dtype=dtype) * 5
+    is_ = torch.arange(ks.numel(), dtype=dtype) + 11
+    api.trace_reset()
+    api.trace_enable(True)
+    try:
+        st = check(kr, ir, ks, is_, router="pla", partitions=64, radix_judge=-1)
+    finally:
+        api.trace_enable(False)
+    assert st["heavy_keys"] >= 2
+    assert api.trace_table()["cross"]["launches"] >= 1
+    a, _ = run(kr, ir, ks, is_, router="pla", partitions=64, radix_judge=-1)
+    b, _ = run(kr, ir, ks, is_, router="pla", partitions=64, radix_judge=-1, fused=False)
+    assert torch.equal(a, b)
+    # a capacity one pair short: nothing is written past it, the count is reported
+    d = [t.to(DEV) for t in (kr, ir, ks, is_)]
+    out = torch.empty((a.shape[0] - 1, 2), dtype=dtype, device=DEV)
+    with pytest.raises(api.TjError) as ei:
+        api.join_inner(*d, out=out, router="pla", partitions=64, radix_judge=-1)
+    assert ei.value.status == api.TJ_ERR_CAPACITY
