@@ -96,7 +96,7 @@ typedef enum {
   TJ_ROUTE_AUTO = 0,   /* chosen from the inputs (Sec. 3.3): TJ_ROUTE_PLA (judged by radix)
                           when one pass does not fit the budget, or when n_r + n_s >= 2^26
                           and the key range's batches reach the partition-resident phase
-                          (10 to 19 key bits each); else TJ_ROUTE_SINGLE */
+                          (10 to 20 key bits each); else TJ_ROUTE_SINGLE */
   TJ_ROUTE_SINGLE = 1, /* sort both relations whole, then align (TJ_ERR_BUDGET if too big) */
   TJ_ROUTE_RADIX = 2,  /* key-range batches of equal width (top bits of key - min) */
   TJ_ROUTE_PLA = 3,    /* batches from a piecewise-linear CDF on a sample's quantiles */
@@ -129,7 +129,7 @@ typedef struct {
 
 /* tj_join_opts.flags: sort every batch of the partitioned join by LSD passes
  * and align it with the sorted-merge join, instead of the partition-resident
- * phase.  By default, batches whose key range spans 10 to 19 bits take one
+ * phase.  By default, batches whose key range spans 10 to 20 bits take one
  * MSD pass into sub-batches of 1024 key values, each sorted and aligned on
  * chip.  A batch of a single key value (a heavy key the cuts isolate) has its
  * pairs streamed straight from its rows.  The result is the same. */

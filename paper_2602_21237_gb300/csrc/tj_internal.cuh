@@ -208,7 +208,7 @@ constexpr int kFThreads = 512;              // threads of a fused CTA
 constexpr int kFCapS = 4608;                // S rows of one item (9 per thread)
 constexpr int kFCapR = 2048;                // R rows of a sub-batch (on chip)
 #ifndef TJ_FUSED_MAX_MSD
-#define TJ_FUSED_MAX_MSD 9
+#define TJ_FUSED_MAX_MSD 10
 #endif
 constexpr int kFMaxMsdBits = TJ_FUSED_MAX_MSD;  // widest MSD digit of the resident phase
 constexpr int kFPreferMsdBits = 9;  // widest MSD digit the batch count aims at (a 10-bit pass costs 1.45x a 9-bit one)

@@ -1,5 +1,5 @@
 """GPU parity of the partition-resident phase of the partitioned join: batches
-whose key range spans 10 to 19 bits are cut by one MSD pass into sub-batches
+whose key range spans 10 to 20 bits are cut by one MSD pass into sub-batches
 of 1024 key values, each sorted and aligned on chip (one CTA per tile of at
 most 4608 S rows; larger sub-batches are split into tiles that share per-key
 counts).  The result must equal the oracle's byte for byte, and the LSD path
