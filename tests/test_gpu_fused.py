@@ -137,3 +137,12 @@ def test_single_key_batches_are_streamed(dtype):
     with pytest.raises(api.TjError) as ei:
         api.join_inner(*d, out=out, router="pla", partitions=64, radix_judge=-1)
     assert ei.value.status == api.TJ_ERR_CAPACITY
+
+
+def test_ten_bit_msd_pass():
+    # 2^22 R keys in 4 equal-width batches of 20 bits, about 2M rows each
+    # (2048 per sub-batch): one 10-bit MSD pass each
+    kr, ir, ks, is_ = datagen.fk_zipf(1 << 22, 1 << 22, 0.5, 77)
+    st = check(kr, ir, ks, is_, router="radix", partitions=4)
+    assert st["partitions"] == 4 and st["fused_batches"] == 4
+    assert st["digit_bits"] == 10
