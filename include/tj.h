@@ -106,7 +106,9 @@ typedef enum {
  * balanced within 1.25x of the model's batches (single-key batches of heavy
  * keys left out) and, under a budget, their largest batch fits half of the
  * working set, the join routes by equal-width ranges instead (their route pass
- * needs no cut-table search) and tj_stats.learned reports router + 100. */
+ * needs no cut-table search) and tj_stats.learned reports router + 100.  When
+ * the equal-width ranges are already within 1.25x of perfect balance, no
+ * model is fitted at all (tj_stats.learned_balance = 0). */
 
 typedef struct {
   int32_t router;        /* tj_router */
