@@ -563,6 +563,17 @@ __global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
     before = tc;
   }
 
+  // the S ids (read when the pairs are written): their loads in flight while
+  // warp 0 runs the chained scan (the S keys' registers are free by now)
+  K sid[kFItemsS];
+  {
+    const K* __restrict__ sv = J.sv + srow0;
+#pragma unroll
+    for (int u = 0; u < kFItemsS; ++u) {
+      const int row = wrow + u * 32 + lane;
+      sid[u] = row < ns ? sv[row] : K(0);
+    }
+  }
   // 4. chained scan over the group's items (warp 0): the tile's first pair
   if (warp == 0) {
     uint64_t* mine = item_lb + ii;
@@ -617,15 +628,6 @@ __global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
   using P = typename PairOf<K>::type;
   const bool vec = (((uintptr_t)out) & (2 * sizeof(K) - 1)) == 0;
   const uint32_t* wx = &S.wh[warp][0];
-  K sid[kFItemsS];
-  {
-    const K* __restrict__ sv = J.sv + srow0;
-#pragma unroll
-    for (int u = 0; u < kFItemsS; ++u) {
-      const int row = wrow + u * 32 + lane;
-      sid[u] = row < ns ? sv[row] : K(0);
-    }
-  }
 #pragma unroll
   for (int u = 0; u < kFItemsS; ++u) {
     if (wrow + u * 32 + lane >= ns) continue;
