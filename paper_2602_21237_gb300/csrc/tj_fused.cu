@@ -184,8 +184,18 @@ __global__ void __launch_bounds__(kFThreads) k_fused_items(const FusedJob<K>* __
     const int64_t ei = block_excl<kFThreads, int64_t>(t, s_w, &ti);
     const int64_t et = block_excl<kFThreads, int64_t>(multi ? t : 0, s_w, &tt);
     const int64_t es = block_excl<kFThreads, int64_t>(multi ? 1 : 0, s_w, &ts);
+    Sub<K> x = {0, 0, 0, 0};
+    if (d < nd) x = sub_of(J, d);
+    using U = typename UnsignedOf<K>::type;
     for (int64_t k = 0; k < t; ++k) {
       FItem it;
+      it.rk = (uint64_t)(uintptr_t)(J.rk + x.r0);
+      it.rv = (uint64_t)(uintptr_t)(J.rv + x.r0);
+      it.sk = (uint64_t)(uintptr_t)(J.sk + x.s0 + k * kFCapS);
+      it.sv = (uint64_t)(uintptr_t)(J.sv + x.s0 + k * kFCapS);
+      it.sublo = (uint64_t)((U)J.lo + ((U)d << kFKeyBits));
+      it.nr = (int32_t)x.nr;
+      it.ns = (int32_t)min((int64_t)kFCapS, x.ns - k * kFCapS);
       it.job = j;
       it.dt = (uint32_t)d | ((uint32_t)k << 11);
       it.kbt = multi ? (int32_t)(base_t + et + k) : -1;
@@ -209,16 +219,12 @@ __global__ void __launch_bounds__(256) k_fused_hist(const FusedJob<K>* __restric
   __shared__ uint32_t h[kFKeys];
   const FItem it = items[blockIdx.x];
   if (it.kbt < 0) return;
-  const FusedJob<K>& J = jobs[it.job];
-  const int d = (int)(it.dt & 2047u), t = (int)(it.dt >> 11);
-  const Sub<K> x = sub_of(J, d);
   using U = typename UnsignedOf<K>::type;
-  const U sublo = (U)J.lo + ((U)d << kFKeyBits);
+  const U sublo = (U)it.sublo;
   for (int i = threadIdx.x; i < kFKeys; i += 256) h[i] = 0u;
   __syncthreads();
-  const int64_t row0 = x.s0 + (int64_t)t * kFCapS;
-  const int n = (int)min((int64_t)kFCapS, x.ns - (int64_t)t * kFCapS);
-  const K* __restrict__ sk = J.sk + row0;
+  const int n = it.ns;
+  const K* __restrict__ sk = reinterpret_cast<const K*>(it.sk);
   for (int i = threadIdx.x; i < n; i += 256)
     atomicAdd(&h[(uint32_t)((U)sk[i] - sublo) & (kFKeys - 1)], 1u);
   __syncthreads();
@@ -346,7 +352,7 @@ size_t fused_smem_bytes() {
 #endif
 template <typename K>
 __global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
-    k_fused_join(const FusedJob<K>* __restrict__ jobs, const FItem* __restrict__ items,
+    k_fused_join(const FItem* __restrict__ items,
                  int64_t n_items, uint32_t* __restrict__ item_counter,
                  uint64_t* __restrict__ item_lb, uint32_t* __restrict__ kb_lb,
                  const uint32_t* __restrict__ kb_tot, K* __restrict__ out, int64_t capacity,
@@ -365,23 +371,22 @@ __global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
   const int64_t ii = S.s_item;
   if (ii >= n_items) return;
   const FItem it = items[ii];
-  const FusedJob<K>& J = jobs[it.job];
-  const int d = (int)(it.dt & 2047u), t = (int)(it.dt >> 11);
-  const Sub<K> x = sub_of(J, d);
+  const int t = (int)(it.dt >> 11);
   const bool multi_tile = it.kbt >= 0;
-  const U sublo = (U)J.lo + ((U)d << kFKeyBits);
-  const int nr = (int)x.nr;  // <= kFCapR (the host checked)
-  const int64_t srow0 = x.s0 + (int64_t)t * kFCapS;
-  const int ns = (int)min((int64_t)kFCapS, x.ns - (int64_t)t * kFCapS);
+  const U sublo = (U)it.sublo;
+  const int nr = it.nr;  // <= kFCapR (the host checked)
+  const int ns = it.ns;
+  const K* __restrict__ g_rv = reinterpret_cast<const K*>(it.rv);
+  const K* __restrict__ g_sv = reinterpret_cast<const K*>(it.sv);
 
   // 1. the tile's global loads in flight at once: S keys, R keys and ids
   //    (the S ids are loaded when the pairs are written)
   const int wrow = warp * 32 * kFItemsS;
   K rkey[kFItemsR], rid_v[kFItemsR], skey[kFItemsS];
   {
-    const K* __restrict__ rk = J.rk + x.r0;
-    const K* __restrict__ rv = J.rv + x.r0;
-    const K* __restrict__ sk = J.sk + srow0;
+    const K* __restrict__ rk = reinterpret_cast<const K*>(it.rk);
+    const K* __restrict__ rv = g_rv;
+    const K* __restrict__ sk = reinterpret_cast<const K*>(it.sk);
 #pragma unroll
     for (int u = 0; u < kFItemsS; ++u) {
       const int row = wrow + u * 32 + lane;
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
   // warp 0 runs the chained scan (the S keys' registers are free by now)
   K sid[kFItemsS];
   {
-    const K* __restrict__ sv = J.sv + srow0;
+    const K* __restrict__ sv = g_sv;
 #pragma unroll
     for (int u = 0; u < kFItemsS; ++u) {
       const int row = wrow + u * 32 + lane;
@@ -652,7 +657,7 @@ __global__ void __launch_bounds__(kFThreads, TJ_FUSED_MINB)
       const uint32_t c = (S.cR[k >> 1] >> ((k & 1u) * 16u)) & 0xFFFFu;
       const uint64_t pos = base + en.a + (uint64_t)within * c;
       const uint32_t r0 = (uint32_t)en.r;
-      const K* __restrict__ rv = J.rv + x.r0;  // R ids in the order of the key's run
+      const K* __restrict__ rv = g_rv;  // R ids in the order of the key's run
       for (uint32_t j = 0; j < c; ++j) {
         out[2 * (pos + j)] = rv[S.r_pb[r0 + j]];
         out[2 * (pos + j) + 1] = sid[u];
@@ -687,9 +692,10 @@ cudaError_t launch_fused_join(const FusedJob<K>* d_jobs, const FItem* d_items, i
                               const uint32_t* d_kb_tot, K* out, int64_t capacity,
                               const int64_t* d_out_base, int64_t* d_total, int* d_err,
                               cudaStream_t st) {
+  (void)d_jobs;  // the items carry what the join needs
   if (n_items <= 0) return cudaSuccess;
   k_fused_join<K><<<(unsigned)n_items, kFThreads, fused_smem_bytes<K>(), st>>>(
-      d_jobs, d_items, n_items, d_item_counter, d_item_lb, d_kb_lb, d_kb_tot, out, capacity,
+      d_items, n_items, d_item_counter, d_item_lb, d_kb_lb, d_kb_tot, out, capacity,
       d_out_base, d_total, d_err);
   return cudaGetLastError();
 }

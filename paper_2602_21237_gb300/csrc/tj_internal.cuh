@@ -230,12 +230,20 @@ struct FusedJob {
   int64_t kbs0;         // first totals slot of its multi-tile sub-batches
 };
 
-struct FItem {
-  int32_t job;   // FusedJob of the group
-  uint32_t dt;   // sub-batch (low 11 bits) | tile << 11
-  int32_t kbt;   // count-vector slot of the tile (-1: the sub-batch is one tile)
-  int32_t kbs;   // totals slot of the sub-batch (-1: one tile)
+// One item, resolved by k_fused_items so that a join CTA starts from one
+// 64-byte load: where its rows are, how many, and its sub-batch's first key.
+struct alignas(16) FItem {
+  uint64_t rk, rv;  // the sub-batch's first R row (keys, ids: const K*)
+  uint64_t sk, sv;  // the tile's first S row
+  uint64_t sublo;   // the sub-batch's first key value (unsigned bits of K)
+  int32_t nr;       // R rows of the sub-batch (<= kFCapR)
+  int32_t ns;       // S rows of the tile (<= kFCapS)
+  int32_t job;      // FusedJob of the group
+  uint32_t dt;      // sub-batch (low 11 bits) | tile << 11
+  int32_t kbt;      // count-vector slot of the tile (-1: the sub-batch is one tile)
+  int32_t kbs;      // totals slot of the sub-batch (-1: one tile)
 };
+static_assert(sizeof(FItem) == 64, "an item is one 64-byte load");
 
 cudaError_t fused_init_attributes();
 // info[4 j + 0..3]: items, multi-tile tiles, multi-tile sub-batches, largest
