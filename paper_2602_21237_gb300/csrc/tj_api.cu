@@ -1034,10 +1034,7 @@ tj_status part_join_impl(const K* kr, const K* ir, int64_t nr, const K* ks, cons
     }
     // batch sizes per side estimated from the sample (regions sized ahead of
     // the route pass, so it needs no histogram of its own)
-    // (up to 256 batches: with more, the guarded route pass of sampled regions,
-    // one chunk a launch, cost more than the route histogram it saves --
-    // measured at 1024 batches of 2^29 rows: 16.8 ms against 10.8 + 1.6 ms)
-    if (!o.exact_route && cuts.size() <= 255) {
+    if (!o.exact_route) {
       sample_cnt = cnt;
       sample_m[0] = m_r;
       sample_m[1] = m_s;

@@ -360,9 +360,9 @@ __host__ __device__ constexpr size_t onesweep_smem_bytes(int bins, int mode, int
                                                          bool guard = false) {
   return 2 * sizeof(K) * (size_t)tile + 2 * 16 + sizeof(uint16_t) * (size_t)tile +
          sizeof(uint32_t) * (size_t)kSortWarps * (size_t)((bins + 1) / 2) +
-         sizeof(uint32_t) * 2 * (size_t)bins + sizeof(long long) * (size_t)bins +
+         sizeof(uint32_t) * 3 * (size_t)bins +
          (mode == kModeCuts ? sizeof(K) * (size_t)bins + sizeof(uint16_t) * (kRouteBuckets + 8) +
-                                  (bins <= 256 ? 1 : 2) * (size_t)tile
+                                  (bins <= 256 ? 1 : (bins <= 512 || !guard) ? 2 : 0) * (size_t)tile
                             : 0) +
          (mode != kModeSort && guard ? sizeof(uint32_t) * (size_t)bins : 0);
 }
@@ -518,14 +518,21 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
   uint32_t* s_whist = reinterpret_cast<uint32_t*>(s_src + TILE);
   uint32_t* s_count = s_whist + kSortWarps * hb;  // contiguous with s_whist
   uint32_t* s_excl = s_count + bins;
-  long long* s_gbase = reinterpret_cast<long long*>(s_excl + bins);
+  // a digit's first output position minus its first slot (positions are
+  // 32-bit, as the digit histograms are: arithmetic modulo 2^32)
+  uint32_t* s_gbase = s_excl + bins;
   K* s_cuts = reinterpret_cast<K*>(s_gbase + bins);
   uint16_t* s_tab = reinterpret_cast<uint16_t*>(s_cuts + bins);
   uint16_t* s_dig = s_tab + (kRouteBuckets + 8);  // u16 slots; u8 when bins <= 256
   uint8_t* s_dig8 = reinterpret_cast<uint8_t*>(s_dig);
+  // slot digits kept, except beyond 512 batches with sized regions: there the
+  // scatter searches the cut table again (their 2 bytes a row, beside the
+  // regions' ends, would cost the multiprocessor a CTA)
+  const bool keep_dig = bins <= 512 || J->route_end == nullptr;
   uint32_t* s_rend =  // end of each batch's region (route passes with sized regions)
-      MODE == kModeCuts ? reinterpret_cast<uint32_t*>(s_dig8 + (bins <= 256 ? 1 : 2) * TILE)
-                        : reinterpret_cast<uint32_t*>(s_gbase + bins);
+      MODE == kModeCuts
+          ? reinterpret_cast<uint32_t*>(s_dig8 + (bins <= 256 ? 1 : keep_dig ? 2 : 0) * TILE)
+          : s_gbase + bins;
   const bool dig8 = bins <= 256;
   constexpr bool route = MODE == kModeCuts;  // digits from the cut table, kept per slot
   constexpr bool radix = MODE == kModeRadix;
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
         if (route) {
           if (dig8)
             s_dig8[pos] = (uint8_t)d;
-          else
+          else if (keep_dig)
             s_dig[pos] = (uint16_t)d;
         }
       }
@@ -685,7 +692,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
       }
       st_volatile_u32(lb_mine + d, kFlagInc | ((prefix + s_count[d]) & kValMask));
     }
-    s_gbase[d] = (long long)hist[d] + (long long)prefix - (long long)s_excl[d];
+    s_gbase[d] = hist[d] + prefix - s_excl[d];
   }
   __syncthreads();
 
@@ -702,9 +709,12 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
         const int q = tid + it * kSortThreads;
         if (q < nvalid) {
           const int r = s_src[q];
-          const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
-          const long long g = s_gbase[d] + q;
-          const bool in = g < (long long)s_rend[d];
+          const uint32_t d = dig8       ? (uint32_t)s_dig8[q]
+                             : keep_dig ? (uint32_t)s_dig[q]
+                                        : route_idx<K>(s_keys[r], lo, s_cuts, s_tab,
+                                                       J->route_steps, J->route_shift);
+          const uint32_t g = s_gbase[d] + (uint32_t)q;
+          const bool in = g < s_rend[d];
           over |= !in;
           if (in) {
             dst_k[g] = s_keys[r];
@@ -720,8 +730,11 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
       const int q = tid + it * kSortThreads;
       if (q < nvalid) {
         const int r = s_src[q];
-        const uint32_t d = dig8 ? (uint32_t)s_dig8[q] : (uint32_t)s_dig[q];
-        const long long g = s_gbase[d] + q;
+        const uint32_t d = dig8       ? (uint32_t)s_dig8[q]
+                           : keep_dig ? (uint32_t)s_dig[q]
+                                      : route_idx<K>(s_keys[r], lo, s_cuts, s_tab,
+                                                     J->route_steps, J->route_shift);
+        const uint32_t g = s_gbase[d] + (uint32_t)q;
         dst_k[g] = s_keys[r];
         dst_v[g] = s_vals[r];
       }
@@ -740,8 +753,8 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
         const K c = k < c_lo ? c_lo : (c_hi < k ? c_hi : k);
         const uint32_t d =
             narrow ? (((uint32_t)c - lo32) >> shift) & mask : digit_of<K>(c, lo, shift, mask);
-        const long long g = s_gbase[d] + q;
-        const bool in = !guard || g < (long long)s_rend[d];
+        const uint32_t g = s_gbase[d] + (uint32_t)q;
+        const bool in = !guard || g < s_rend[d];
         over |= !in;
         if (in) {
           dst_k[g] = k;
@@ -760,7 +773,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
         const int r = s_src[q];
         const K k = s_keys[r];
         const uint32_t d = (((uint32_t)k - lo32) >> shift) & mask;
-        const long long g = s_gbase[d] + q;
+        const uint32_t g = s_gbase[d] + (uint32_t)q;
         dst_k[g] = k;
         dst_v[g] = s_vals[r];
       }
@@ -773,7 +786,7 @@ __global__ void __launch_bounds__(kSortThreads, TJ_SORT_MINB)
         const int r = s_src[q];
         const K k = s_keys[r];
         const uint32_t d = digit_of<K>(k, lo, shift, mask);
-        const long long g = s_gbase[d] + q;
+        const uint32_t g = s_gbase[d] + (uint32_t)q;
         dst_k[g] = k;
         dst_v[g] = s_vals[r];
       }
@@ -894,10 +907,12 @@ cudaError_t launch_onesweep(const RadixJob<K>* d_jobs, int num_jobs, int64_t tot
 // with sized regions need the most).
 template <typename K, int ITEMS, int MODE>
 cudaError_t onesweep_attr() {
+  // the larger of a launch with and without sized regions (a cut-table route
+  // over more than 512 batches keeps slot digits only without them)
+  const size_t a = onesweep_smem_bytes<K>(kMaxBins, MODE, kSortThreads * ITEMS, false);
+  const size_t b = onesweep_smem_bytes<K>(kMaxBins, MODE, kSortThreads * ITEMS, MODE != kModeSort);
   return cudaFuncSetAttribute(k_onesweep<K, ITEMS, MODE>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)onesweep_smem_bytes<K>(kMaxBins, MODE, kSortThreads * ITEMS,
-                                                          MODE != kModeSort));
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(a > b ? a : b));
 }
 
 template <typename K>
