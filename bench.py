@@ -49,6 +49,8 @@ def parse():
                     help="mem_budget_bytes of each join in MiB (0 = unbounded)")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (debug only)")
     ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-buffers", type=int, default=2,
+                    help="device buffers per input and result in the end-to-end pipeline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -938,8 +940,8 @@ def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort
     """Same metric through the public API with host buffers: every step copies
     its inputs from pinned host memory and reads every result back.  The steps
     are pipelined the way a caller streaming batches would: copies in on one
-    stream, the library calls on another, copies out on a third, with two
-    device buffers for R, S, the pairs and the sort input, so the next job's
+    stream, the library calls on another, copies out on a third, with two (or
+    --e2e-buffers) device buffers for R, S, the pairs and the sort input, so the next job's
     inputs arrive while the current job runs and each result leaves while the
     next one runs.  The timed region covers K whole steps, from the first copy
     in to the last copy out."""
@@ -955,12 +957,13 @@ def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort
     h_out = torch.empty((n_s, 2), dtype=torch.int64).pin_memory()
     h_sorted_k = torch.empty_like(h_sk).pin_memory()
     h_sorted_i = torch.empty_like(h_si).pin_memory()
-    two = lambda f: [f() for _ in range(2)]  # noqa: E731
-    d_kr, d_ir = two(lambda: torch.empty_like(kr)), two(lambda: torch.empty_like(ir))
-    d_sk = two(lambda: torch.empty((n_s,), dtype=torch.int64, device=dev))
-    d_si = two(lambda: torch.empty((n_s,), dtype=torch.int64, device=dev))
-    d_out = two(lambda: torch.empty((n_s, 2), dtype=torch.int64, device=dev))
-    d_ok, d_oi = two(lambda: torch.empty_like(sort_src_k)), two(lambda: torch.empty_like(sort_src_i))
+    nb = max(2, int(getattr(args, "e2e_buffers", 2)))  # device buffers per input and result
+    many = lambda f: [f() for _ in range(nb)]  # noqa: E731
+    d_kr, d_ir = many(lambda: torch.empty_like(kr)), many(lambda: torch.empty_like(ir))
+    d_sk = many(lambda: torch.empty((n_s,), dtype=torch.int64, device=dev))
+    d_si = many(lambda: torch.empty((n_s,), dtype=torch.int64, device=dev))
+    d_out = many(lambda: torch.empty((n_s, 2), dtype=torch.int64, device=dev))
+    d_ok, d_oi = many(lambda: torch.empty_like(sort_src_k)), many(lambda: torch.empty_like(sort_src_i))
     s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ev = lambda: torch.cuda.Event()  # noqa: E731
     nj = len(h_s)
@@ -980,47 +983,47 @@ def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort
             k, j = items[i]
             _, a, b = h_s[j]
             with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(done_s[i - 2])
-                d_sk[i % 2].copy_(a, non_blocking=True)
-                d_si[i % 2].copy_(b, non_blocking=True)
+                if i >= nb:
+                    s_in.wait_event(done_s[i - nb])
+                d_sk[i % nb].copy_(a, non_blocking=True)
+                d_si[i % nb].copy_(b, non_blocking=True)
                 e = ev()
                 e.record(s_in)
             return e
 
         def copy_in_r(k):
             with torch.cuda.stream(s_in):
-                if k >= 2:
-                    s_in.wait_event(done_r[k - 2])
-                d_kr[k % 2].copy_(h_kr, non_blocking=True)
-                d_ir[k % 2].copy_(h_ir, non_blocking=True)
+                if k >= nb:
+                    s_in.wait_event(done_r[k - nb])
+                d_kr[k % nb].copy_(h_kr, non_blocking=True)
+                d_ir[k % nb].copy_(h_ir, non_blocking=True)
                 e = ev()
                 e.record(s_in)
             return e
 
         def copy_in_sort(k):
             with torch.cuda.stream(s_in):
-                if k >= 2:
-                    s_in.wait_event(done_sort_read[k - 2])  # read out, free again
-                d_ok[k % 2].copy_(h_sk, non_blocking=True)
-                d_oi[k % 2].copy_(h_si, non_blocking=True)
+                if k >= nb:
+                    s_in.wait_event(done_sort_read[k - nb])  # read out, free again
+                d_ok[k % nb].copy_(h_sk, non_blocking=True)
+                d_oi[k % nb].copy_(h_si, non_blocking=True)
                 e = ev()
                 e.record(s_in)
             return e
 
         done_sort_read = {}
         in_r = {0: copy_in_r(0)}
-        in_s = {0: copy_in(0)}
-        if len(items) > 1:
-            in_s[1] = copy_in(1)
+        in_s = {}
+        for i0 in range(min(nb, len(items))):
+            in_s[i0] = copy_in(i0)
         in_sort = {}
         for i, (k, j) in enumerate(items):
             s_run.wait_event(in_r[k])
             s_run.wait_event(in_s[i])
-            if i >= 2:
-                s_run.wait_event(done_out[i - 2])  # its pair buffer has been read out
-            res = api.join_inner(d_kr[k % 2], d_ir[k % 2], d_sk[i % 2], d_si[i % 2],
-                                 mem_budget_bytes=budget, out=d_out[i % 2], stream=s_run)
+            if i >= nb:
+                s_run.wait_event(done_out[i - nb])  # its pair buffer has been read out
+            res = api.join_inner(d_kr[k % nb], d_ir[k % nb], d_sk[i % nb], d_si[i % nb],
+                                 mem_budget_bytes=budget, out=d_out[i % nb], stream=s_run)
             done_s[i] = ev()
             done_s[i].record(s_run)
             with torch.cuda.stream(s_out):
@@ -1032,22 +1035,22 @@ def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort
                 d2h += res.numel() * 8
             # inputs queued in the order they are needed: S two jobs ahead; after
             # a step's first join, its sort input and the next step's R
-            if i + 2 < len(items):
-                in_s[i + 2] = copy_in(i + 2)
+            if i + nb < len(items):
+                in_s[i + nb] = copy_in(i + nb)
             if j == 0:
                 in_sort[k] = copy_in_sort(k)
                 if k + 1 < steps:
                     in_r[k + 1] = copy_in_r(k + 1)
             if j == nj - 1:
                 s_run.wait_event(in_sort[k])
-                api.sort(d_ok[k % 2], d_oi[k % 2], stream=s_run)
+                api.sort(d_ok[k % nb], d_oi[k % nb], stream=s_run)
                 done_sort[k] = ev()
                 done_sort[k].record(s_run)
                 done_r[k] = done_sort[k]  # the step's joins are done before its sort
                 with torch.cuda.stream(s_out):
                     s_out.wait_event(done_sort[k])
-                    h_sorted_k.copy_(d_ok[k % 2], non_blocking=True)
-                    h_sorted_i.copy_(d_oi[k % 2], non_blocking=True)
+                    h_sorted_k.copy_(d_ok[k % nb], non_blocking=True)
+                    h_sorted_i.copy_(d_oi[k % nb], non_blocking=True)
                     done_sort_read[k] = ev()
                     done_sort_read[k].record(s_out)
                 if k == 0:
@@ -1064,7 +1067,7 @@ def run_e2e(args, kr, ir, rels, sort_src_k, sort_src_i, budget, n_r, n_s, n_sort
     tuples_step = len(rels) * (n_r + n_s) + n_sort
     return {"value": tuples_step * ws / dt, "unit": UNIT, "h2d_bytes_per_step": bytes_in,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": args.e2e_steps,
-            "pipelining": "copies in, library calls and copies out on three streams, two "
+            "pipelining": f"copies in, library calls and copies out on three streams, {nb} "
                           "device buffers per input and result; K steps back to back"}
 
 
